@@ -1,0 +1,529 @@
+/*
+ * lbm_oracle.c -- plain, slow, FP64 CPU oracle of the pore-scale lattice
+ * Boltzmann advection-diffusion(-reaction) update with maximum-entropy
+ * Dirichlet / Neumann boundary conditions.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call, link or
+ * load this file; only the tests, the smoke check and the benchmark's CPU
+ * baseline leg do.  It shares no code, header, table or helper with the CUDA
+ * library: the lattice constants below are typed out here on their own.
+ *
+ * One time step follows the order the paper prints it (Sec. 4.1 and
+ * Algorithm 1): collide every fluid node (Eq. "Collision", with the
+ * equilibrium of Eq. "LBM_feq"), stream by pushing each post-collision
+ * population to its neighbour (Eq. "LBE"), impose the boundary conditions on
+ * the populations that streaming left unknown (Sec. 4.1.1 (a) and (b)), then
+ * take the moments (Eq. "LBM_Macro").
+ *
+ * Readings of points the paper leaves open (each is also listed in the
+ * design notes):
+ *  - the equilibrium's last term is v.v/(2 c_s^2); the printed v.v/c_s^2 would
+ *    make the collision destroy mass, against u = sum_i f_i (Sec. 4.1);
+ *  - D2Q9 uses the textbook velocities and weights 4/9, 1/9, 1/36, c_s^2 = 1/3;
+ *  - boundary nodes are wet nodes on the edge; the unknown populations are the
+ *    ones whose upstream neighbour lies outside the lattice, which on a straight
+ *    edge is exactly the set M^- of Eq. "Boundary_Vel";
+ *  - Dirichlet data that leave no non-negative solution are applied literally
+ *    (unknowns may go negative) and counted; Neumann data with no root are met
+ *    by the gamma -> -infinity limit (unknowns set to zero) and counted;
+ *  - at a corner of two Neumann edges the normal is the normalised sum of the
+ *    two outward normals; unknowns with e_i.n = 0 are filled by halfway
+ *    bounce-back; a corner that touches a Dirichlet edge is Dirichlet over all
+ *    of its unknowns;
+ *  - the reaction is an explicit first-order sink applied after collision,
+ *    f*_i -= w_i k u, at reactive fluid nodes (fluid nodes with a solid D2Q9
+ *    neighbour, or every fluid node in bulk mode);
+ *  - with dissolution on, the mass removed at a fluid node is taken from its
+ *    solid neighbours in proportion to the link weights w_j; a solid node whose
+ *    mineral mass reaches zero or less after a step becomes fluid with all
+ *    populations zero;
+ *  - Dirichlet data inside a run of eta substeps are interpolated linearly in
+ *    time: substep j uses (1 - j/eta) a + (j/eta) b (Eq. "MTS").
+ *
+ * Memory: the oracle owns copies of everything it is given.  Arrays are
+ * row-major [ny][nx]; populations are [9][ny][nx].
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ---- D2Q9 lattice (textbook), c_s^2 = 1/3 -------------------------------- */
+enum { NQ = 9 };
+static const int CX[NQ] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+static const int CY[NQ] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+static const double WT[NQ] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,
+                              1.0 / 9.0,  1.0 / 9.0,  1.0 / 36.0,
+                              1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+static const double CS2 = 1.0 / 3.0;
+
+/* direction pointing the other way: CX[REV[i]] == -CX[i], CY[REV[i]] == -CY[i] */
+static int reverse_of(int i) {
+  for (int j = 0; j < NQ; ++j)
+    if (CX[j] == -CX[i] && CY[j] == -CY[i]) return j;
+  return -1;
+}
+
+enum { EDGE_PERIODIC = 0, EDGE_DIRICHLET = 1, EDGE_NEUMANN = 2 };
+enum { SIDE_W = 0, SIDE_E = 1, SIDE_S = 2, SIDE_N = 3 };
+enum { REACT_NONE = 0, REACT_SURFACE = 1, REACT_BULK = 2 };
+
+typedef struct {
+  int nx, ny;
+  int edge[4];
+  double tau;
+  int react_mode;
+  double k_scalar;
+  int dissolution;
+  double *k;       /* [ny][nx] rate, used where reactive          */
+  double *vel;     /* [2][ny][nx]                                  */
+  uint8_t *solid;  /* [ny][nx] 1 = solid                           */
+  double *mineral; /* [ny][nx] mineral mass of solid nodes         */
+  double *f;       /* [9][ny][nx] populations after BC (state)     */
+  double *fpost;   /* [9][ny][nx] post-collision populations       */
+  double *fnew;    /* [9][ny][nx] streamed populations             */
+  uint8_t *known;  /* [9][ny][nx] 1 = set by streaming             */
+  double *u;       /* [ny][nx] concentration at the current time   */
+  long long steps;
+  long long bc_infeasible;
+  long long flips;
+  long long newton_iters;
+  long long newton_fail;
+  double J;        /* sum over steps of the east-edge fluid concentrations */
+  double reacted;  /* total mass removed by the sink                        */
+} or_lbm;
+
+static size_t nn(const or_lbm *o) { return (size_t)o->nx * (size_t)o->ny; }
+static size_t at(const or_lbm *o, int x, int y) {
+  return (size_t)y * (size_t)o->nx + (size_t)x;
+}
+
+/* Wrap (x, y) through periodic edges.  Returns 0 if the point lies outside
+ * the lattice across a non-periodic edge. */
+static int locate(const or_lbm *o, int x, int y, int *ox, int *oy) {
+  if (x < 0 || x >= o->nx) {
+    if (o->edge[SIDE_W] != EDGE_PERIODIC) return 0;
+    x = ((x % o->nx) + o->nx) % o->nx;
+  }
+  if (y < 0 || y >= o->ny) {
+    if (o->edge[SIDE_S] != EDGE_PERIODIC) return 0;
+    y = ((y % o->ny) + o->ny) % o->ny;
+  }
+  *ox = x;
+  *oy = y;
+  return 1;
+}
+
+static int is_solid(const or_lbm *o, int x, int y) {
+  int a, b;
+  if (!locate(o, x, y, &a, &b)) return 0;
+  return o->solid[at(o, a, b)] != 0;
+}
+
+/* Second-order equilibrium, Eq. "LBM_feq" with the v.v/(2 c_s^2) reading. */
+static double feq(int i, double u, double vx, double vy) {
+  double ev = CX[i] * vx + CY[i] * vy;
+  double vv = vx * vx + vy * vy;
+  return WT[i] * u *
+         (1.0 + ev / CS2 + 0.5 * ev * ev / (CS2 * CS2) - 0.5 * vv / CS2);
+}
+
+/* A fluid node is reactive in surface mode when one of its 8 neighbours is
+ * solid; in bulk mode every fluid node is reactive. */
+static int reactive(const or_lbm *o, int x, int y) {
+  if (o->solid[at(o, x, y)]) return 0;
+  if (o->react_mode == REACT_BULK) return 1;
+  if (o->react_mode != REACT_SURFACE) return 0;
+  for (int i = 1; i < NQ; ++i)
+    if (is_solid(o, x + CX[i], y + CY[i])) return 1;
+  return 0;
+}
+
+/* Sum of the link weights from fluid node (x,y) to its solid neighbours. */
+static double solid_link_weight(const or_lbm *o, int x, int y) {
+  double s = 0.0;
+  for (int i = 1; i < NQ; ++i)
+    if (is_solid(o, x + CX[i], y + CY[i])) s += WT[i];
+  return s;
+}
+
+static void moments(or_lbm *o) {
+  size_t N = nn(o);
+  for (size_t n = 0; n < N; ++n) {
+    double s = 0.0;
+    if (!o->solid[n])
+      for (int i = 0; i < NQ; ++i) s += o->f[(size_t)i * N + n];
+    o->u[n] = s;
+  }
+}
+
+/* ---- single-node maximum-entropy solutions (Sec. 4.1.1) ------------------ */
+
+/* Dirichlet, Sec. 4.1.1 (a): the unknowns (mask unk[i] = 1) that minimise
+ * H = sum f log(f/w) with sum_i f_i = up are f_i = w_i / sum_unk w *
+ * (up - sum_known f).  Returns 1 if the data leave no non-negative solution. */
+int or_maxent_dirichlet(double *f, const int *unk, double up) {
+  double wu = 0.0, known = 0.0;
+  for (int i = 0; i < NQ; ++i) {
+    if (unk[i]) wu += WT[i];
+    else known += f[i];
+  }
+  double rest = up - known;
+  for (int i = 0; i < NQ; ++i)
+    if (unk[i]) f[i] = WT[i] / wu * rest;
+  return rest < 0.0;
+}
+
+/* Neumann, Sec. 4.1.1 (b): unknowns in M^- = {i: unk[i], e_i.n < 0} take
+ * f_i = w_i exp(-1 - gamma e_i.n), with gamma the root of
+ *   sum_{M^-} w_i (e_i.n) exp(-1 - gamma e_i.n) = q - sum_{not M^-} (e_j.n) f_j.
+ * Unknowns with e_i.n >= 0 must already hold a value (the caller fills them).
+ * The left side runs over (-inf, 0) and falls strictly with gamma, so a root
+ * exists iff the right side R < 0; it is found by Newton's method kept inside
+ * a bracket (bisection when a Newton step leaves it).  For R >= 0 the M^-
+ * unknowns are set to 0, the limit gamma -> -inf.  Returns 1 when R > 0
+ * (infeasible data), 0 otherwise; *iters receives the Newton iterations, and
+ * *fail is set if the iteration did not converge. */
+int or_maxent_neumann(double *f, const int *unk, double nxn, double nyn,
+                      double q, long long *iters, int *fail) {
+  double a[NQ];
+  int inm[NQ];
+  double R = q;
+  int any = 0;
+  *fail = 0;
+  for (int i = 0; i < NQ; ++i) {
+    a[i] = CX[i] * nxn + CY[i] * nyn;
+    inm[i] = unk[i] && a[i] < 0.0;
+    if (inm[i]) any = 1;
+    else R -= a[i] * f[i];
+  }
+  if (!any) return 0;
+  if (!(R < 0.0)) {
+    for (int i = 0; i < NQ; ++i)
+      if (inm[i]) f[i] = 0.0;
+    return R > 0.0;
+  }
+  /* g(gamma) = sum_{M^-} w a exp(-1 - gamma a) - R ; g decreasing. */
+  double lo = -1.0, hi = 1.0;
+#define G_OF(gm, gout, dout)                                   \
+  do {                                                         \
+    double s_ = 0.0, d_ = 0.0;                                 \
+    for (int i_ = 0; i_ < NQ; ++i_)                            \
+      if (inm[i_]) {                                           \
+        double e_ = WT[i_] * exp(-1.0 - (gm) * a[i_]);         \
+        s_ += a[i_] * e_;                                      \
+        d_ -= a[i_] * a[i_] * e_;                              \
+      }                                                        \
+    gout = s_ - R;                                             \
+    dout = d_;                                                 \
+  } while (0)
+  double glo, ghi, dd;
+  G_OF(lo, glo, dd);
+  while (glo < 0.0) { lo = 2.0 * lo - 1.0; G_OF(lo, glo, dd); }
+  G_OF(hi, ghi, dd);
+  while (ghi > 0.0) { hi = 2.0 * hi + 1.0; G_OF(hi, ghi, dd); }
+  double gm = 0.5 * (lo + hi);
+  int it = 0, done = 0;
+  for (; it < 200; ++it) {
+    double g, dg;
+    G_OF(gm, g, dg);
+    if (g == 0.0) { done = 1; break; }
+    if (g > 0.0) lo = gm; else hi = gm;
+    double nx_ = gm - g / dg;
+    if (!(nx_ > lo && nx_ < hi)) nx_ = 0.5 * (lo + hi);
+    if (fabs(nx_ - gm) <= 1e-15 * (1.0 + fabs(gm))) { gm = nx_; done = 1; break; }
+    gm = nx_;
+  }
+#undef G_OF
+  *iters += it + 1;
+  if (!done) *fail = 1;
+  for (int i = 0; i < NQ; ++i)
+    if (inm[i]) f[i] = WT[i] * exp(-1.0 - gm * a[i]);
+  return 0;
+}
+
+/* ---- construction -------------------------------------------------------- */
+
+or_lbm *or_lbm_new(int nx, int ny, const int *edge, double tau,
+                   int react_mode, double k_scalar, const double *k_field,
+                   int dissolution, const uint8_t *solid, const double *vel,
+                   const double *mineral, const double *u0) {
+  or_lbm *o = (or_lbm *)calloc(1, sizeof(or_lbm));
+  if (!o) return NULL;
+  o->nx = nx;
+  o->ny = ny;
+  memcpy(o->edge, edge, sizeof(o->edge));
+  o->tau = tau;
+  o->react_mode = react_mode;
+  o->k_scalar = k_scalar;
+  o->dissolution = dissolution;
+  size_t N = nn(o);
+  o->k = (double *)malloc(N * sizeof(double));
+  o->vel = (double *)malloc(2 * N * sizeof(double));
+  o->solid = (uint8_t *)malloc(N);
+  o->mineral = (double *)malloc(N * sizeof(double));
+  o->f = (double *)calloc(NQ * N, sizeof(double));
+  o->fpost = (double *)calloc(NQ * N, sizeof(double));
+  o->fnew = (double *)calloc(NQ * N, sizeof(double));
+  o->known = (uint8_t *)calloc(NQ * N, 1);
+  o->u = (double *)calloc(N, sizeof(double));
+  for (size_t n = 0; n < N; ++n) {
+    o->k[n] = k_field ? k_field[n] : k_scalar;
+    o->solid[n] = solid ? (solid[n] ? 1 : 0) : 0;
+    o->mineral[n] = mineral ? mineral[n] : 1.0;
+    o->vel[n] = vel ? vel[n] : 0.0;
+    o->vel[N + n] = vel ? vel[N + n] : 0.0;
+  }
+  /* Initialisation, Sec. 6.2 (i): f_i(x, 0) = f_i^eq(x, 0; u_0(x)). */
+  for (size_t n = 0; n < N; ++n) {
+    if (o->solid[n]) continue;
+    for (int i = 0; i < NQ; ++i)
+      o->f[(size_t)i * N + n] = feq(i, u0 ? u0[n] : 0.0, o->vel[n], o->vel[N + n]);
+  }
+  moments(o);
+  return o;
+}
+
+void or_lbm_free(or_lbm *o) {
+  if (!o) return;
+  free(o->k); free(o->vel); free(o->solid); free(o->mineral);
+  free(o->f); free(o->fpost); free(o->fnew); free(o->known); free(o->u);
+  free(o);
+}
+
+/* ---- one time step -------------------------------------------------------- */
+
+/* Value index of edge node (x, y) on side s in the edge-data layout
+ * [W: ny][E: ny][S: nx][N: nx]. */
+static size_t edge_slot(const or_lbm *o, int s, int x, int y) {
+  switch (s) {
+    case SIDE_W: return (size_t)y;
+    case SIDE_E: return (size_t)o->ny + (size_t)y;
+    case SIDE_S: return 2 * (size_t)o->ny + (size_t)x;
+    default: return 2 * (size_t)o->ny + (size_t)o->nx + (size_t)x;
+  }
+}
+
+/* Collision with reaction sink; mineral bookkeeping. */
+static void collide(or_lbm *o, double *fout) {
+  size_t N = nn(o);
+  const double omega = 1.0 / o->tau;
+#pragma omp parallel for schedule(static)
+  for (int y = 0; y < o->ny; ++y)
+    for (int x = 0; x < o->nx; ++x) {
+      size_t n = at(o, x, y);
+      if (o->solid[n]) continue;
+      double u = 0.0;
+      for (int i = 0; i < NQ; ++i) u += o->f[(size_t)i * N + n];
+      double kr = reactive(o, x, y) ? o->k[n] : 0.0;
+      for (int i = 0; i < NQ; ++i) {
+        double fi = o->f[(size_t)i * N + n];
+        double post = fi + omega * (feq(i, u, o->vel[n], o->vel[N + n]) - fi);
+        fout[(size_t)i * N + n] = post - WT[i] * kr * u;
+      }
+    }
+}
+
+/* Mineral decrement: the sink k u at a reactive fluid node x is taken from
+ * its solid neighbours y = x + e_j in proportion to w_j.  Gathered per solid
+ * node so that each node's update is one plain sum. */
+static void dissolve_gather(or_lbm *o) {
+  size_t N = nn(o);
+#pragma omp parallel for schedule(static)
+  for (int y = 0; y < o->ny; ++y)
+    for (int x = 0; x < o->nx; ++x) {
+      size_t n = at(o, x, y);
+      if (!o->solid[n]) continue;
+      double take = 0.0;
+      for (int j = 1; j < NQ; ++j) {
+        int sx, sy; /* the fluid node whose link j points at (x, y) */
+        if (!locate(o, x - CX[j], y - CY[j], &sx, &sy)) continue;
+        size_t s = at(o, sx, sy);
+        if (o->solid[s] || !reactive(o, sx, sy)) continue;
+        double us = 0.0;
+        for (int i = 0; i < NQ; ++i) us += o->f[(size_t)i * N + s];
+        take += o->k[s] * us * WT[j] / solid_link_weight(o, sx, sy);
+      }
+      o->mineral[n] -= take;
+    }
+  (void)N;
+}
+
+/* Push streaming with halfway bounce-back at solid neighbours. */
+static void stream(or_lbm *o) {
+  size_t N = nn(o);
+  memset(o->known, 0, NQ * N);
+  memset(o->fnew, 0, NQ * N * sizeof(double));
+  for (int y = 0; y < o->ny; ++y)
+    for (int x = 0; x < o->nx; ++x) {
+      size_t n = at(o, x, y);
+      if (o->solid[n]) continue;
+      for (int i = 0; i < NQ; ++i) {
+        double v = o->fpost[(size_t)i * N + n];
+        int tx, ty;
+        if (!locate(o, x + CX[i], y + CY[i], &tx, &ty)) continue; /* leaves */
+        size_t t = at(o, tx, ty);
+        if (o->solid[t]) {
+          int r = reverse_of(i);
+          o->fnew[(size_t)r * N + n] = v;
+          o->known[(size_t)r * N + n] = 1;
+        } else {
+          o->fnew[(size_t)i * N + t] = v;
+          o->known[(size_t)i * N + t] = 1;
+        }
+      }
+    }
+}
+
+static void apply_bc(or_lbm *o, int j, int eta, const double *ua,
+                     const double *ub, const double *q) {
+  size_t N = nn(o);
+  const double frac = (double)j / (double)eta;
+  for (int y = 0; y < o->ny; ++y)
+    for (int x = 0; x < o->nx; ++x) {
+      size_t n = at(o, x, y);
+      if (o->solid[n]) continue;
+      int on[4] = {x == 0 && o->edge[SIDE_W] != EDGE_PERIODIC,
+                   x == o->nx - 1 && o->edge[SIDE_E] != EDGE_PERIODIC,
+                   y == 0 && o->edge[SIDE_S] != EDGE_PERIODIC,
+                   y == o->ny - 1 && o->edge[SIDE_N] != EDGE_PERIODIC};
+      if (!(on[0] || on[1] || on[2] || on[3])) continue;
+      double f[NQ];
+      int unk[NQ], nunk = 0;
+      for (int i = 0; i < NQ; ++i) {
+        f[i] = o->fnew[(size_t)i * N + n];
+        unk[i] = !o->known[(size_t)i * N + n];
+        nunk += unk[i];
+      }
+      if (!nunk) continue;
+      int dside = -1, nside = -1;
+      for (int s = 0; s < 4; ++s) {
+        if (!on[s]) continue;
+        if (o->edge[s] == EDGE_DIRICHLET && dside < 0) dside = s;
+        if (o->edge[s] == EDGE_NEUMANN && nside < 0) nside = s;
+      }
+      if (dside >= 0) {
+        size_t e = edge_slot(o, dside, x, y);
+        double a = ua ? ua[e] : 0.0, b = ub ? ub[e] : 0.0;
+        double up = (1.0 - frac) * a + frac * b; /* Eq. "MTS" */
+        o->bc_infeasible += or_maxent_dirichlet(f, unk, up);
+      } else {
+        /* outward normal: normalised sum over the node's Neumann sides */
+        double nxn = 0.0, nyn = 0.0;
+        static const double SN[4][2] = {{-1, 0}, {1, 0}, {0, -1}, {0, 1}};
+        for (int s = 0; s < 4; ++s)
+          if (on[s] && o->edge[s] == EDGE_NEUMANN) {
+            nxn += SN[s][0];
+            nyn += SN[s][1];
+          }
+        double len = sqrt(nxn * nxn + nyn * nyn);
+        nxn /= len;
+        nyn /= len;
+        /* unknowns tangent to the normal: halfway bounce-back */
+        for (int i = 0; i < NQ; ++i)
+          if (unk[i] && CX[i] * nxn + CY[i] * nyn >= 0.0) {
+            f[i] = o->fpost[(size_t)reverse_of(i) * N + n];
+            unk[i] = 0;
+          }
+        double qv = q ? q[edge_slot(o, nside, x, y)] : 0.0;
+        int fail = 0;
+        o->bc_infeasible +=
+            or_maxent_neumann(f, unk, nxn, nyn, qv, &o->newton_iters, &fail);
+        o->newton_fail += fail;
+      }
+      for (int i = 0; i < NQ; ++i) o->fnew[(size_t)i * N + n] = f[i];
+    }
+}
+
+/* Run n substeps j = 1..n of a coarse step split eta ways.  ua, ub: Dirichlet
+ * data at the start and the end of the coarse step, q: Neumann data, each in
+ * the edge layout [W: ny][E: ny][S: nx][N: nx] (NULL means zero). */
+void or_lbm_substeps(or_lbm *o, int n, int eta, const double *ua,
+                     const double *ub, const double *q) {
+  size_t N = nn(o);
+  for (int j = 1; j <= n; ++j) {
+    /* collide (with the reaction sink) */
+    collide(o, o->fpost);
+    {
+      double r = 0.0;
+      for (int y = 0; y < o->ny; ++y)
+        for (int x = 0; x < o->nx; ++x)
+          if (reactive(o, x, y)) r += o->k[at(o, x, y)] * o->u[at(o, x, y)];
+      o->reacted += r;
+    }
+    if (o->dissolution && o->react_mode == REACT_SURFACE) dissolve_gather(o);
+    /* stream, then boundary conditions */
+    stream(o);
+    apply_bc(o, j, eta, ua, ub, q);
+    memcpy(o->f, o->fnew, NQ * N * sizeof(double));
+    /* dissolution: solid nodes whose mineral is used up become fluid */
+    if (o->dissolution && o->react_mode == REACT_SURFACE)
+      for (size_t m = 0; m < N; ++m)
+        if (o->solid[m] && o->mineral[m] <= 0.0) {
+          o->solid[m] = 0;
+          for (int i = 0; i < NQ; ++i) o->f[(size_t)i * N + m] = 0.0;
+          o->flips += 1;
+        }
+    moments(o);
+    for (int y = 0; y < o->ny; ++y)
+      if (!o->solid[at(o, o->nx - 1, y)]) o->J += o->u[at(o, o->nx - 1, y)];
+    o->steps += 1;
+  }
+}
+
+/* ---- read-out ------------------------------------------------------------- */
+
+void or_lbm_get_u(const or_lbm *o, double *out) { memcpy(out, o->u, nn(o) * sizeof(double)); }
+void or_lbm_get_f(const or_lbm *o, double *out) { memcpy(out, o->f, NQ * nn(o) * sizeof(double)); }
+void or_lbm_get_solid(const or_lbm *o, uint8_t *out) { memcpy(out, o->solid, nn(o)); }
+void or_lbm_get_mineral(const or_lbm *o, double *out) { memcpy(out, o->mineral, nn(o) * sizeof(double)); }
+
+/* Post-collision populations of the current state (what the next step would
+ * stream), for comparing against a solver that stores them. */
+void or_lbm_get_fpost(or_lbm *o, double *out) { collide(o, out); }
+
+/* diag: [mass, J, reacted, bc_infeasible, flips, newton_iters, newton_fail, steps] */
+void or_lbm_diag(const or_lbm *o, double *d) {
+  double m = 0.0;
+  for (size_t n = 0; n < nn(o); ++n) m += o->u[n];
+  d[0] = m;
+  d[1] = o->J;
+  d[2] = o->reacted;
+  d[3] = (double)o->bc_infeasible;
+  d[4] = (double)o->flips;
+  d[5] = (double)o->newton_iters;
+  d[6] = (double)o->newton_fail;
+  d[7] = (double)o->steps;
+}
+
+/* Boltzmann H of Eq. "BH" summed over fluid nodes; +inf if some f < 0. */
+double or_lbm_H(const or_lbm *o) {
+  size_t N = nn(o);
+  double h = 0.0;
+  for (size_t n = 0; n < N; ++n) {
+    if (o->solid[n]) continue;
+    for (int i = 0; i < NQ; ++i) {
+      double v = o->f[(size_t)i * N + n];
+      if (v < 0.0) return INFINITY;
+      if (v > 0.0) h += v * log(v / WT[i]);
+    }
+  }
+  return h;
+}
+
+/* LBM -> FEM transfer, Sec. 6.2 (ii): bilinear value of u at lattice
+ * coordinates (px, py) from the four surrounding nodes.  Periodic edges wrap;
+ * across a non-periodic edge the point must lie inside [0, n-1]. */
+double or_trace_point(const or_lbm *o, double px, double py) {
+  int x1 = (int)floor(px), y1 = (int)floor(py);
+  if (o->edge[SIDE_W] != EDGE_PERIODIC && x1 >= o->nx - 1) x1 = o->nx - 2;
+  if (o->edge[SIDE_S] != EDGE_PERIODIC && y1 >= o->ny - 1) y1 = o->ny - 2;
+  double gx = px - x1, gy = py - y1;
+  int ax, ay, bx, by;
+  locate(o, x1, y1, &ax, &ay);
+  locate(o, x1 + 1, y1 + 1, &bx, &by);
+  double u1 = o->u[at(o, ax, ay)], u2 = o->u[at(o, bx, ay)];
+  double u3 = o->u[at(o, bx, by)], u4 = o->u[at(o, ax, by)];
+  return u1 * (1 - gx) * (1 - gy) + u2 * gx * (1 - gy) + u3 * gx * gy +
+         u4 * (1 - gx) * gy;
+}

@@ -1,0 +1,151 @@
+"""Seeded synthetic inputs for the pore-scale workloads.
+
+This module holds no arithmetic of the method: it only draws geometries,
+velocity fields and boundary-data arrays.  The CUDA path and the CPU oracle
+both take their inputs from here, so each side sees the same numbers.
+
+Random numbers come from splitmix64 (Steele, Lea and Flood, "Fast splittable
+pseudorandom number generators", OOPSLA 2014), written out below so that the
+streams do not depend on the numpy version installed.
+
+Workload recipes (lattice units, D2Q9):
+  * porous medium: random overlapping disks, radius uniform in [8, 24] nodes,
+    centres uniform over the lattice, added until the solid fraction reaches
+    1 - porosity; the first and last columns stay fluid so that the inlet and
+    outlet boundary nodes exist;
+  * advection velocity: v = (d psi/dy, -d psi/dx) of a stream function made of
+    16 random Fourier modes with integer wave vectors in [-8, 8]^2 \\ {0},
+    amplitudes N(0,1)/|k| and phases U[0, 2 pi), scaled so that max |v| = umax,
+    then zeroed in solids.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+_MASK = (1 << 64) - 1
+_GOLDEN = 0x9E3779B97F4A7C15
+
+
+class SplitMix64:
+    """Sequential splitmix64 stream."""
+
+    def __init__(self, seed: int):
+        self.state = int(seed) & _MASK
+
+    def next_u64(self) -> int:
+        self.state = (self.state + _GOLDEN) & _MASK
+        z = self.state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _MASK
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _MASK
+        return z ^ (z >> 31)
+
+    def uniform(self) -> float:
+        """Uniform double in [0, 1) from the top 53 bits."""
+        return (self.next_u64() >> 11) * (1.0 / 9007199254740992.0)
+
+    def normal(self) -> float:
+        """Standard normal by the Box-Muller transform."""
+        u1 = 1.0 - self.uniform()
+        u2 = self.uniform()
+        return math.sqrt(-2.0 * math.log(u1)) * math.cos(2.0 * math.pi * u2)
+
+
+def uniform_array(seed: int, n: int) -> np.ndarray:
+    """n uniforms in [0, 1): element i is the (i+1)-th output of
+    SplitMix64(seed), computed vectorised with wrapping uint64 arithmetic."""
+    i = np.arange(1, n + 1, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(int(seed) & _MASK) + i * np.uint64(_GOLDEN)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    return (z >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+def disk_packing(nx: int, ny: int, porosity: float, seed: int,
+                 rmin: float = 8.0, rmax: float = 24.0) -> np.ndarray:
+    """uint8 [ny, nx] solid mask (1 = solid) of random overlapping disks."""
+    rng = SplitMix64(seed)
+    solid = np.zeros((ny, nx), dtype=np.uint8)
+    target = int(math.ceil((1.0 - porosity) * nx * ny))
+    count = 0
+    guard = 0
+    while count < target and nx > 2:
+        cx = rng.uniform() * nx
+        cy = rng.uniform() * ny
+        r = rmin + (rmax - rmin) * rng.uniform()
+        x0, x1 = max(1, int(math.floor(cx - r))), min(nx - 2, int(math.ceil(cx + r)))
+        y0, y1 = max(0, int(math.floor(cy - r))), min(ny - 1, int(math.ceil(cy + r)))
+        guard += 1
+        if guard > 100 * nx * ny:
+            break
+        if x0 > x1 or y0 > y1:
+            continue
+        xs = np.arange(x0, x1 + 1, dtype=np.float64)
+        ys = np.arange(y0, y1 + 1, dtype=np.float64)
+        inside = ((xs[None, :] - cx) ** 2 + (ys[:, None] - cy) ** 2) <= r * r
+        box = solid[y0:y1 + 1, x0:x1 + 1]
+        count += int(np.count_nonzero(inside & (box == 0)))
+        box[inside] = 1
+    return solid
+
+
+def streamfunction_velocity(nx: int, ny: int, seed: int, n_modes: int = 16,
+                            umax: float = 0.05, kmax: int = 8,
+                            solid: np.ndarray | None = None) -> np.ndarray:
+    """float64 [2, ny, nx] divergence-free velocity from a random stream
+    function, scaled to max |v| = umax and zeroed at solid nodes."""
+    rng = SplitMix64(seed)
+    modes = []
+    while len(modes) < n_modes:
+        kx = int(rng.uniform() * (2 * kmax + 1)) - kmax
+        ky = int(rng.uniform() * (2 * kmax + 1)) - kmax
+        if kx == 0 and ky == 0:
+            continue
+        amp = rng.normal() / math.hypot(kx, ky)
+        phase = 2.0 * math.pi * rng.uniform()
+        modes.append((kx, ky, amp, phase))
+    x = np.arange(nx, dtype=np.float64)[None, :]
+    y = np.arange(ny, dtype=np.float64)[:, None]
+    vx = np.zeros((ny, nx))
+    vy = np.zeros((ny, nx))
+    for kx, ky, amp, phase in modes:
+        c = amp * np.cos(2.0 * math.pi * (kx * x / nx + ky * y / ny) + phase)
+        vx += c * (2.0 * math.pi * ky / ny)
+        vy -= c * (2.0 * math.pi * kx / nx)
+    speed = np.sqrt(vx * vx + vy * vy).max()
+    if speed > 0:
+        vx *= umax / speed
+        vy *= umax / speed
+    vel = np.stack([vx, vy])
+    if solid is not None:
+        vel[:, solid != 0] = 0.0
+    return vel
+
+
+def edge_array(nx: int, ny: int, W=0.0, E=0.0, S=0.0, N=0.0) -> np.ndarray:
+    """Per-edge-node data in the layout [W: ny][E: ny][S: nx][N: nx]; each
+    side takes a scalar or an array of that side's length."""
+    out = np.zeros(2 * (nx + ny))
+    out[0:ny] = W
+    out[ny:2 * ny] = E
+    out[2 * ny:2 * ny + nx] = S
+    out[2 * ny + nx:] = N
+    return out
+
+
+def porous_case(nx: int, ny: int, seed: int, porosity: float = 0.6,
+                tau: float = 0.7, k: float = 1e-3, umax: float = 0.05,
+                c_in: float = 1.0) -> dict:
+    """Reactive porous lattice: disks at the given porosity, stream-function
+    velocity, surface reaction rate k with dissolution, Dirichlet c_in on the
+    west edge, zero-flux Neumann on the east edge, periodic in y, c0 = 0."""
+    solid = disk_packing(nx, ny, porosity, seed)
+    vel = streamfunction_velocity(nx, ny, seed + 1_000_003, umax=umax, solid=solid)
+    return dict(
+        nx=nx, ny=ny, tau=tau, edges=(1, 2, 0, 0), solid=solid, vel=vel,
+        u0=np.zeros((ny, nx)), react_mode=1, k=k, dissolution=True,
+        mineral=np.ones((ny, nx)), u_dir=edge_array(nx, ny, W=c_in),
+        q_neu=edge_array(nx, ny))

@@ -1,0 +1,379 @@
+"""Pins for the FP64 oracle against facts fixed outside the oracle itself:
+the paper's printed table, closed forms, a spectral solution of the linear
+scheme, invariants and brute-force entropy minimisation.  CPU only."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_1601_02708_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+CX = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
+CY = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])
+W = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+
+
+def _e1_table():
+    rows = []
+    with open(os.path.join(GOLDEN, "e1_lbm_table.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                _, h, dt, err = line.split()
+                rows.append((float(h), float(dt), float(err)))
+    return rows
+
+
+def _run_e1(oracle_mod, h):
+    D = 4.0 / (5.0 * math.pi ** 2)
+    n_nodes = int(round(1.0 / h)) + 1
+    dt = h * h / (6.0 * D)           # the bound h^2 = 6 dt D  ->  tau = 1
+    steps = int(round(0.25 / dt))
+    x = np.arange(n_nodes) * h
+    X, Y = np.meshgrid(x, x)
+    u0 = np.sin(math.pi * Y) * np.cos(math.pi * X / 2)
+    o = oracle_mod.LBMOracle(n_nodes, n_nodes, 1.0, edges=(2, 1, 1, 1), u0=u0)
+    o.substeps(steps)
+    return np.abs(o.u() - math.exp(-steps * dt) * u0).max(), o
+
+
+def test_e1_table_bound_and_order(oracle_mod):
+    """Sec. 4.1.2, Table "LBM_p1": the max error at t = 0.25 stays below the
+    printed errors and falls at least at second order.  (Compared at the
+    lattice time n*dt closest to 0.25; at tau = 1 the interior update is the
+    9-point average whose symbol matches exp(-D k^2 dt) to O(h^6), so the
+    error here is far below the printed one.)"""
+    rows = _e1_table()[:3]
+    errs = []
+    for h, dt, printed in rows:
+        err, o = _run_e1(oracle_mod, h)
+        assert err <= printed, (h, err, printed)
+        assert o.diag()["newton_fail"] == 0
+        errs.append(err)
+    for a, b in zip(errs, errs[1:]):
+        assert a / b >= 4.0 * 0.9
+
+
+def test_tau1_eigenmode_amplification(oracle_mod):
+    """At tau = 1 and v = 0 the collide+stream map sends u to
+    sum_i w_i u(x - e_i); on a periodic lattice the Fourier mode cos(a x) cos(b y)
+    is multiplied by (2 + cos a)(2 + cos b) / 9 each step (exact)."""
+    nx, ny, steps = 24, 16, 37
+    a, b = 2 * math.pi * 3 / nx, 2 * math.pi * 2 / ny
+    X, Y = np.meshgrid(np.arange(nx), np.arange(ny))
+    u0 = np.cos(a * X) * np.cos(b * Y)
+    o = oracle_mod.LBMOracle(nx, ny, 1.0, u0=u0)
+    o.substeps(steps)
+    g = (2 + math.cos(a)) * (2 + math.cos(b)) / 9.0
+    np.testing.assert_allclose(o.u(), g ** steps * u0, rtol=0, atol=1e-14)
+
+
+def _spectral_u(nx, ny, kx, ky, tau, vx, vy, k_react, steps):
+    """u after `steps` of the linear D2Q9 scheme for u0 = cos(k.x), solved in
+    Fourier space: collision C = (1-1/tau) I + E 1^T / tau - k w 1^T with
+    E_i = w_i (1 + 3 e.v + 4.5 (e.v)^2 - 1.5 v.v); push streaming multiplies
+    population i by exp(-i k.e_i)."""
+    ev = CX * vx + CY * vy
+    E = W * (1 + 3 * ev + 4.5 * ev ** 2 - 1.5 * (vx * vx + vy * vy))
+    one = np.ones(9)
+    C = (1 - 1 / tau) * np.eye(9) + np.outer(E, one) / tau - k_react * np.outer(W, one)
+    S = np.diag(np.exp(-1j * (kx * CX + ky * CY)))
+    M = S @ C
+    amp = np.linalg.matrix_power(M, steps) @ E.astype(complex)
+    X, Y = np.meshgrid(np.arange(nx), np.arange(ny))
+    return np.real(amp.sum() * np.exp(1j * (kx * X + ky * Y)))
+
+
+@pytest.mark.parametrize("tau,vx,vy,k", [(0.73, 0.04, -0.03, 2e-3),
+                                         (1.6, -0.05, 0.02, 0.0),
+                                         (0.55, 0.01, 0.05, 1e-2)])
+def test_fourier_solution_of_the_scheme(oracle_mod, tau, vx, vy, k):
+    """Periodic lattice, uniform velocity, bulk first-order sink: the oracle's
+    real-space loops match the spectral solution of the same linear scheme."""
+    nx, ny, steps = 20, 12, 45
+    kx, ky = 2 * math.pi * 3 / nx, 2 * math.pi * 1 / ny
+    X, Y = np.meshgrid(np.arange(nx), np.arange(ny))
+    vel = np.stack([np.full((ny, nx), vx), np.full((ny, nx), vy)])
+    o = oracle_mod.LBMOracle(nx, ny, tau, vel=vel, u0=np.cos(kx * X + ky * Y),
+                             react_mode=2 if k else 0, k=k)
+    o.substeps(steps)
+    ref = _spectral_u(nx, ny, kx, ky, tau, vx, vy, k, steps)
+    np.testing.assert_allclose(o.u(), ref, rtol=0, atol=2e-13)
+
+
+def test_gaussian_pulse_second_order(oracle_mod):
+    """Advection-diffusion of a Gaussian on a periodic lattice against the
+    continuum solution with D = c_s^2 (tau - 1/2) (Sec. 4.1): sigma^2 grows
+    by 2 D t and the centre moves with v; refining h by 2 (diffusive scaling)
+    cuts the error about 4 times."""
+    tau = 0.8
+    D = (tau - 0.5) / 3.0
+    errs = []
+    for level in (1, 2):
+        n = 64 * level
+        sig0 = 4.0 * level
+        steps = 150 * level * level
+        vx, vy = 0.04 / level, 0.02 / level
+        x0 = y0 = n / 2 - 10 * level
+        X, Y = np.meshgrid(np.arange(n), np.arange(n))
+        u0 = np.exp(-((X - x0) ** 2 + (Y - y0) ** 2) / (2 * sig0 ** 2))
+        vel = np.stack([np.full((n, n), vx), np.full((n, n), vy)])
+        o = oracle_mod.LBMOracle(n, n, tau, vel=vel, u0=u0)
+        o.substeps(steps)
+        s2 = sig0 ** 2 + 2 * D * steps
+        xc, yc = x0 + vx * steps, y0 + vy * steps
+        exact = sig0 ** 2 / s2 * np.exp(-((X - xc) ** 2 + (Y - yc) ** 2) / (2 * s2))
+        errs.append(np.abs(o.u() - exact).max())
+    assert errs[1] < 1e-3
+    assert errs[0] / errs[1] > 3.0, errs
+
+
+def test_linear_profile_between_dirichlet_walls(oracle_mod):
+    """v = 0, Dirichlet c = 2 and c = 1 on the west/east walls, periodic in y:
+    the steady state is exactly linear.  Its populations
+    f_i = w_i (c - tau e_i.grad c) are proportional to w_i on each wall's
+    unknown set, so the max-entropy closed form reproduces it to rounding."""
+    nx, ny, tau = 12, 4, 0.8
+    o = oracle_mod.LBMOracle(nx, ny, tau, edges=(1, 1, 0, 0),
+                             u0=np.full((ny, nx), 1.5))
+    ud = inputs.edge_array(nx, ny, W=2.0, E=1.0)
+    o.substeps(6000, 1, ud, ud)
+    exact = 2.0 - np.arange(nx) / (nx - 1)
+    np.testing.assert_allclose(o.u(), np.broadcast_to(exact, (ny, nx)), atol=1e-12)
+
+
+def test_linear_profile_with_neumann_flux(oracle_mod):
+    """Dirichlet c = 2 on the west, Neumann first moment q = -tau g / 3 on the
+    east (the flux of the linear profile with slope g): the steady state is
+    c = 2 + g x, reproduced exactly by the max-entropy Neumann condition."""
+    nx, ny, tau, g = 12, 4, 0.8, -0.05
+    o = oracle_mod.LBMOracle(nx, ny, tau, edges=(1, 2, 0, 0), u0=np.ones((ny, nx)))
+    ud = inputs.edge_array(nx, ny, W=2.0)
+    q = inputs.edge_array(nx, ny, E=-tau * g / 3.0)
+    o.substeps(30000, 1, ud, ud, q)
+    exact = 2.0 + g * np.arange(nx)
+    np.testing.assert_allclose(o.u(), np.broadcast_to(exact, (ny, nx)), atol=1e-11)
+    assert o.diag()["newton_fail"] == 0
+
+
+def test_uniform_first_order_decay(oracle_mod):
+    """Uniform field, bulk sink k: u_n = (1 - k)^n u_0 exactly; and within
+    n k^2 / 2 of exp(-k n)."""
+    k, steps = 0.01, 120
+    o = oracle_mod.LBMOracle(8, 6, 0.9, u0=np.full((6, 8), 3.0), react_mode=2, k=k)
+    o.substeps(steps)
+    np.testing.assert_allclose(o.u(), 3.0 * (1 - k) ** steps, rtol=1e-13)
+    assert abs(o.u()[0, 0] / 3.0 - math.exp(-k * steps)) <= steps * k * k / 2
+
+
+def test_mass_conservation_with_solids(oracle_mod):
+    """Periodic lattice with bounce-back solids and a stream-function velocity,
+    no reaction: the total mass is constant to rounding."""
+    nx, ny = 48, 40
+    solid = inputs.disk_packing(nx, ny, 0.6, seed=11, rmin=2, rmax=5)
+    vel = inputs.streamfunction_velocity(nx, ny, seed=12, solid=solid)
+    u0 = inputs.uniform_array(13, nx * ny).reshape(ny, nx) * (solid == 0)
+    o = oracle_mod.LBMOracle(nx, ny, 0.6, solid=solid, vel=vel, u0=u0)
+    m0 = o.diag()["mass"]
+    o.substeps(2000)
+    assert abs(o.diag()["mass"] - m0) <= 1e-12 * m0
+    assert np.all(o.u()[solid != 0] == 0)
+
+
+def test_zero_flux_box_nonnegative_and_H_monotone(oracle_mod):
+    """Sec. 4.1.3: square pulse in a zero-flux box (max-entropy Neumann on all
+    sides, diagonal normals at the corners), D = 1e-2 at the tau = 1 bound:
+    every population stays non-negative and H does not increase."""
+    n = 41
+    h = 1.0 / (n - 1)
+    X, Y = np.meshgrid(np.arange(n) * h, np.arange(n) * h)
+    u0 = ((X >= 0.4) & (X <= 0.6) & (Y >= 0.4) & (Y <= 0.6)).astype(float)
+    o = oracle_mod.LBMOracle(n, n, 1.0, edges=(2, 2, 2, 2), u0=u0)
+    h_prev = o.H()
+    for _ in range(40):
+        o.substeps(10)
+        assert o.f().min() >= 0.0
+        h_now = o.H()
+        assert h_now <= h_prev + 1e-12
+        h_prev = h_now
+    d = o.diag()
+    assert d["newton_fail"] == 0 and d["bc_infeasible"] == 0
+
+
+# ---- single-node maximum entropy by brute force ------------------------------
+
+def _H(f, idx):
+    f = np.asarray(f)
+    return float(sum(f[i] * math.log(f[i] / W[i]) for i in idx if f[i] > 0))
+
+
+def _simplex_min(idx, S, coef, res=500):
+    """Minimise sum_{i in idx} f_i log(f_i / w_i) over f >= 0 with
+    sum_i coef_i f_i = S, for three unknowns, by a dense grid followed by a
+    shrinking local grid search."""
+    assert len(idx) == 3
+    best = None
+
+    def point(p, q):
+        g = [p * S / coef[0], q * S / coef[1], (1 - p - q) * S / coef[2]]
+        return g
+
+    def search(p0, q0, span, m):
+        nonlocal best
+        ps = np.linspace(max(0, p0 - span), min(1, p0 + span), m)
+        for p in ps:
+            qs = np.linspace(max(0, q0 - span), min(1 - p, q0 + span), m)
+            for q in qs:
+                if p + q > 1:
+                    continue
+                g = point(p, q)
+                val = sum(gi * math.log(gi / W[i]) for gi, i in zip(g, idx) if gi > 0)
+                if best is None or val < best[0]:
+                    best = (val, p, q)
+
+    search(0.5, 0.5, 0.5, res)
+    span = 1.0 / res
+    for _ in range(30):
+        _, p, q = best
+        search(p, q, 2 * span, 21)
+        span /= 4
+    _, p, q = best
+    return point(p, q)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_dirichlet_maxent_matches_brute_force(oracle_mod, seed):
+    """Sec. 4.1.1 (a) on a west-edge node: minimising H over the unknowns
+    E, NE, SE subject to sum_i f_i = u^p by brute force."""
+    rng = np.random.default_rng(seed)
+    f = rng.uniform(0.01, 0.2, 9)
+    unk = np.zeros(9, int)
+    idx = [1, 5, 8]
+    unk[idx] = 1
+    known = sum(f[i] for i in range(9) if not unk[i])
+    up = known + rng.uniform(0.05, 0.5)
+    got, bad = oracle_mod.maxent_dirichlet(f, unk, up)
+    assert not bad
+    brute = _simplex_min(idx, up - known, [1.0, 1.0, 1.0])
+    np.testing.assert_allclose(got[idx], brute, rtol=1e-7)
+    assert abs(got.sum() - up) < 1e-14
+    # KKT: log(f_i / w_i) is equal across the unknowns
+    lg = np.log(got[idx] / W[idx])
+    assert np.ptp(lg) < 1e-12
+
+
+def test_dirichlet_corner_is_proportional_to_weights(oracle_mod):
+    """A corner with five unknowns: the minimiser of H with a mass constraint
+    has log(f_i/w_i) + 1 + lambda = 0 for all unknowns, i.e. f proportional
+    to w; checked against a direct constrained minimisation (scipy)."""
+    scipy_opt = pytest.importorskip("scipy.optimize")
+    f = np.linspace(0.02, 0.1, 9)
+    idx = [1, 2, 5, 6, 8]
+    unk = np.zeros(9, int)
+    unk[idx] = 1
+    known = sum(f[i] for i in range(9) if not unk[i])
+    up = known + 0.3
+    got, _ = oracle_mod.maxent_dirichlet(f, unk, up)
+    res = scipy_opt.minimize(
+        lambda g: sum(gi * math.log(gi / W[i]) for gi, i in zip(g, idx)),
+        np.full(5, 0.06), method="SLSQP", bounds=[(1e-12, None)] * 5,
+        constraints=[{"type": "eq", "fun": lambda g: g.sum() - 0.3}],
+        options={"ftol": 1e-15, "maxiter": 500})
+    np.testing.assert_allclose(got[idx], res.x, rtol=1e-5)
+    np.testing.assert_allclose(got[idx] / W[idx], 0.3 / W[idx].sum(), rtol=1e-14)
+
+
+@pytest.mark.parametrize("seed", [4, 5])
+def test_neumann_axis_matches_brute_force_and_closed_form(oracle_mod, seed):
+    """Sec. 4.1.1 (b) on an east-edge node (n = (1, 0)): unknowns W, NW, SW
+    all have e.n = -1, so the Newton root gives f proportional to w with
+    sum_unknown f = sum_{e.n > 0} (e.n) f - q."""
+    rng = np.random.default_rng(seed)
+    f = rng.uniform(0.01, 0.2, 9)
+    unk = np.zeros(9, int)
+    idx = [3, 6, 7]
+    unk[idx] = 1
+    q = -rng.uniform(0.0, 0.05)
+    outgoing = f[1] + f[5] + f[8]
+    got, bad, iters, fail = oracle_mod.maxent_neumann(f, unk, (1.0, 0.0), q)
+    assert not bad and not fail and iters > 0
+    S = outgoing - q
+    np.testing.assert_allclose(got[idx], W[idx] / W[idx].sum() * S, rtol=1e-13)
+    brute = _simplex_min(idx, S, [1.0, 1.0, 1.0])
+    np.testing.assert_allclose(got[idx], brute, rtol=1e-7)
+
+
+def test_neumann_diagonal_matches_quadratic_and_brute_force(oracle_mod):
+    """Corner of two Neumann sides, n = (-1, -1)/sqrt 2: unknowns E, N carry
+    e.n = -1/sqrt 2 and NE carries -sqrt 2, so with t = exp(gamma / sqrt 2)
+    the constraint is the quadratic
+      (w_E + w_N)/sqrt 2 * t/e + sqrt 2 w_NE t^2/e = S,   S = -R > 0,
+    solved here in closed form; brute force confirms the minimum of H."""
+    rng = np.random.default_rng(7)
+    f = rng.uniform(0.01, 0.2, 9)
+    unk = np.zeros(9, int)
+    idx = [1, 2, 5]
+    unk[idx] = 1
+    n = np.array([-1.0, -1.0]) / math.sqrt(2)
+    q = 0.0
+    got, bad, _, fail = oracle_mod.maxent_neumann(f, unk, n, q)
+    assert not bad and not fail
+    a = CX * n[0] + CY * n[1]
+    R = q - sum(a[j] * f[j] for j in range(9) if j not in idx)
+    S = -R
+    A = (W[1] + W[2]) / math.sqrt(2) / math.e
+    B = math.sqrt(2) * W[5] / math.e
+    t = 2 * S / (A + math.sqrt(A * A + 4 * B * S))
+    closed = np.array([W[1] * t / math.e, W[2] * t / math.e, W[5] * t * t / math.e])
+    np.testing.assert_allclose(got[idx], closed, rtol=1e-13)
+    brute = _simplex_min(idx, S, [-a[1], -a[2], -a[5]])
+    np.testing.assert_allclose(got[idx], brute, rtol=1e-6)
+
+
+def test_infeasible_boundary_data_are_counted(oracle_mod):
+    """Dirichlet data below the known mass give negative unknowns (applied
+    literally, counted); Neumann data with R > 0 set the unknowns to zero."""
+    f = np.full(9, 0.1)
+    unk = np.zeros(9, int)
+    unk[[1, 5, 8]] = 1
+    got, bad = oracle_mod.maxent_dirichlet(f, unk, 0.2)
+    assert bad and got[1] < 0 and abs(got.sum() - 0.2) < 1e-15
+    unk = np.zeros(9, int)
+    unk[[3, 6, 7]] = 1
+    got, bad, _, _ = oracle_mod.maxent_neumann(f, unk, (1.0, 0.0), 1.0)
+    assert bad and np.all(got[[3, 6, 7]] == 0)
+
+
+def test_dissolution_mass_balance(oracle_mod):
+    """Surface reaction with dissolution: the mass removed by the sink equals
+    the mineral lost by the solid nodes (to rounding); exhausted solid nodes
+    turn fluid and no remaining solid node has exhausted mineral."""
+    nx, ny = 40, 24
+    case = inputs.porous_case(nx, ny, seed=21, porosity=0.55, k=0.05)
+    solid0 = inputs.disk_packing(nx, ny, 0.55, 21, rmin=2, rmax=4)
+    m0 = np.full((ny, nx), 0.02)
+    o = oracle_mod.LBMOracle(nx, ny, 0.8, edges=case["edges"], solid=solid0,
+                             vel=inputs.streamfunction_velocity(nx, ny, 22, solid=solid0),
+                             u0=np.zeros((ny, nx)), react_mode=1, k=0.05,
+                             dissolution=True, mineral=m0)
+    o.substeps(300, 1, case["u_dir"], case["u_dir"], case["q_neu"])
+    d = o.diag()
+    lost = (m0 - o.mineral())[solid0 != 0].sum()
+    assert d["flips"] > 0
+    assert abs(lost - d["reacted"]) <= 1e-12 * max(1.0, d["reacted"])
+    s = o.solid()
+    assert np.all(o.mineral()[s != 0] > 0)
+    assert np.all(o.mineral()[(solid0 != 0) & (s == 0)] <= 0)
+
+
+def test_trace_is_exact_for_bilinear_fields(oracle_mod):
+    """Sec. 6.2 (ii): the LBM -> FEM transfer reproduces a bilinear field."""
+    nx, ny = 9, 7
+    X, Y = np.meshgrid(np.arange(nx), np.arange(ny))
+    u0 = 0.3 + 0.1 * X - 0.05 * Y + 0.02 * X * Y
+    o = oracle_mod.LBMOracle(nx, ny, 1.0, edges=(1, 1, 1, 1), u0=u0)
+    rng = np.random.default_rng(3)
+    pts = np.stack([rng.uniform(0, nx - 1, 50), rng.uniform(0, ny - 1, 50)], 1)
+    exact = 0.3 + 0.1 * pts[:, 0] - 0.05 * pts[:, 1] + 0.02 * pts[:, 0] * pts[:, 1]
+    np.testing.assert_allclose(o.trace(pts), exact, atol=1e-14)
