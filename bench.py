@@ -1,0 +1,359 @@
+"""Benchmark of the fused D2Q9 ADE-LBM step on the 4096 x 4096 reactive
+porous workload.
+
+One benchmark step is one lattice time step of the whole hot path: pull
+streaming with bounce-back, max-entropy Dirichlet inlet / Neumann outlet,
+moments, BGK collision with the surface reaction sink, and the dissolution
+pass (mineral update and exact mask flips).
+
+Workload (synthetic, seeded): 4096 x 4096 nodes, random overlapping disks
+(radius 8-24) at porosity 0.6, 16-mode stream-function velocity with
+|v|max = 0.05, tau = 0.7, first-order surface reaction k = 1e-3 with unit
+mineral per solid node, Dirichlet c = 1 on the west side, zero-flux Neumann
+on the east side, periodic in y, c0 = 0.  The populations (2 x 604 MB) are
+larger than L2, so no flush is needed between steps.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+instead, on a crop of the same workload sized to finish in about a minute.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "LBM-ADE GLUPS & % HBM roofline (FP32 vs FP64); adjoint/forward time ratio"
+# Algorithmic bytes of the fused step per node and launch: a fluid node reads
+# and writes 9 populations, reads 2 velocity components and its mask byte; a
+# solid node costs its mask byte.
+BYTES_FLUID = {32: 9 * 4 * 2 + 2 * 4 + 1, 64: 9 * 8 * 2 + 2 * 8 + 1}
+BYTES_SOLID = 1
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def measured_peak_gbs():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() in ("active", "1"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload(n):
+    from paper_1601_02708_gb300 import inputs
+    case = inputs.porous_case(n, n, seed=2)
+    return case
+
+
+def lattice_kwargs(case):
+    return {k: case[k] for k in ("edges", "solid", "vel", "u0", "react_mode", "k",
+                                 "dissolution", "mineral")}
+
+
+def run_oracle(case, steps, crop=None):
+    """Time `steps` oracle steps (FP64 CPU) on the workload or a crop of it.
+    Returns (seconds, nodes, threads)."""
+    import oracle
+    oracle.build()
+    kw = lattice_kwargs(case)
+    nx, ny = case["nx"], case["ny"]
+    ud, q = case["u_dir"], case["q_neu"]
+    if crop is not None:
+        from paper_1601_02708_gb300 import inputs
+        c = inputs.porous_case(crop, crop, seed=2)
+        kw, nx, ny, ud, q = lattice_kwargs(c), crop, crop, c["u_dir"], c["q_neu"]
+    ref = oracle.LBMOracle(nx, ny, case["tau"], **kw)
+    t0 = time.perf_counter()
+    ref.substeps(steps, 1, ud, ud, q)
+    dt = time.perf_counter() - t0
+    threads = _env_int("OMP_NUM_THREADS", os.cpu_count() or 1)
+    return dt, nx * ny, threads
+
+
+def reference_arm(args):
+    """The FP64 CPU oracle timed as it stands, each step a time step of a
+    crop of the workload sized so that all steps end in about a minute."""
+    rank = _env_int("RANK", 0)
+    if rank != 0:
+        return
+    case = workload(64)  # parameters only; the crop is regenerated
+    case["tau"] = 0.7
+    cal_t, cal_nodes, _ = run_oracle(case, 2, crop=256)
+    rate = 2 * cal_nodes / max(cal_t, 1e-9)               # node-steps per second
+    total = max(1, args.steps + args.warmup)
+    side = int(math.sqrt(60.0 * rate / total) // 64 * 64)
+    side = max(64, min(args.size, side))
+    if args.warmup:
+        run_oracle(case, args.warmup, crop=side)
+    dt, nodes, threads = run_oracle(case, args.steps, crop=side)
+    glups = nodes * args.steps / dt / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": glups, "unit": "GLUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"reactive porous D2Q9 ADE-LBM, {side}x{side} crop of "
+                               "the 4096x4096 generator (porosity 0.6, tau 0.7, k 1e-3, "
+                               "dissolution)", "nx": side, "ny": side},
+        "cpu_baseline": {"value": glups, "unit": "GLUPS", "cores": threads, "kind": "oracle",
+                         "sample": f"{args.steps} steps of a {side}x{side} crop"},
+        "e2e": {"value": glups, "unit": "GLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--size", type=int, default=4096)
+    ap.add_argument("--fp64-steps", type=int, default=300)
+    ap.add_argument("--cpu-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+
+    import torch
+
+    from paper_1601_02708_gb300 import LBM
+
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    local = _env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    n = args.size
+    case = workload(n)
+    kw = lattice_kwargs(case)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    ud, q = dev(case["u_dir"]), dev(case["q_neu"])
+    nodes = n * n
+    stream = torch.cuda.current_stream()
+
+    # ---- FP32 fused step: the headline ------------------------------------
+    lat = LBM(n, n, case["tau"], precision=32, **kw)
+    lat.substeps(args.warmup, 1, ud, ud, q)
+    barrier()
+    lat.kernel_timing(True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        barrier()
+        ev0.record(stream)
+        lat.substeps(args.steps, 1, ud, ud, q)
+        ev1.record(stream)
+        ev1.synchronize()
+        barrier()
+    ms = max_over_ranks(ev0.elapsed_time(ev1))
+    step_ms, step_n, diss_ms, diss_n = lat.kernel_times()
+    lat.kernel_timing(False)
+    diag = lat.diagnostics()
+    n_solid = diag["n_solid"]
+    n_fluid = nodes - n_solid
+    lat.close()
+    del lat
+    torch.cuda.empty_cache()
+
+    value = world * nodes * args.steps / (ms / 1e3) / 1e9
+    peak, peak_kind = measured_peak_gbs()
+    bytes_step = BYTES_FLUID[32] * n_fluid + BYTES_SOLID * n_solid
+    per_launch_ms = step_ms / max(step_n, 1)
+    achieved = bytes_step / (per_launch_ms / 1e3) / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "lbm_step_traffic.json")
+    try:
+        from paper_1601_02708_gb300 import build as _b
+        import hashlib
+        h = hashlib.sha256()
+        for src in sorted(_b.sources()) + [os.path.join(_b.CSRC, "lbm_kernels.cuh"),
+                                           os.path.join(_b.CSRC, "lbm_lattice.cuh")]:
+            h.update(open(src, "rb").read())
+        rec = json.load(open(tpath))
+        if rec.get("source_sha256") == h.hexdigest():
+            traffic = rec["dram_bytes_per_launch_full_size"]
+    except (OSError, ValueError, KeyError):
+        traffic = None
+
+    # ---- FP64 mode of the same kernels ---------------------------------------
+    fp64 = None
+    if args.fp64_steps > 0:
+        lat64 = LBM(n, n, case["tau"], precision=64, **kw)
+        lat64.substeps(3, 1, ud, ud, q)
+        barrier()
+        lat64.kernel_timing(True)
+        ev0.record(stream)
+        lat64.substeps(args.fp64_steps, 1, ud, ud, q)
+        ev1.record(stream)
+        ev1.synchronize()
+        ms64 = max_over_ranks(ev0.elapsed_time(ev1))
+        s64_ms, s64_n, _, _ = lat64.kernel_times()
+        d64 = lat64.diagnostics()
+        lat64.close()
+        del lat64
+        torch.cuda.empty_cache()
+        b64 = BYTES_FLUID[64] * (nodes - d64["n_solid"]) + BYTES_SOLID * d64["n_solid"]
+        a64 = b64 / (s64_ms / max(s64_n, 1) / 1e3) / 1e9
+        fp64 = {"value": world * nodes * args.fp64_steps / (ms64 / 1e3) / 1e9,
+                "unit": "GLUPS", "steps": args.fp64_steps,
+                "ms_per_step": ms64 / args.fp64_steps,
+                "roofline": {"bound": "hbm", "achieved": a64, "peak": peak,
+                             "unit": "GB/s", "frac": a64 / peak}}
+
+    # ---- end to end through the public API with host buffers -----------------
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        h_solid = pin(kw["solid"].astype(np.uint8))
+        h_vel, h_min, h_u0 = pin(kw["vel"]), pin(kw["mineral"]), pin(kw["u0"])
+        h_ud, h_q = pin(case["u_dir"]), pin(case["q_neu"])
+        h_out = torch.empty((n, n), dtype=torch.float32).pin_memory()
+        kwh = dict(kw, solid=h_solid, vel=h_vel, mineral=h_min, u0=h_u0)
+        barrier()
+        t0 = time.perf_counter()
+        lat2 = LBM(n, n, case["tau"], precision=32, **kwh)
+        lat2.substeps(args.steps, 1, h_ud, h_ud, h_q)
+        lat2.concentration(h_out, precision=32)
+        barrier()
+        t_e2e = max_over_ranks(time.perf_counter() - t0)
+        lat2.close()
+        bi = sum(t.numel() * t.element_size() for t in (h_solid, h_vel, h_min, h_u0)) + \
+            3 * h_ud.numel() * 8
+        bo = h_out.numel() * h_out.element_size()
+        e2e = {"value": world * nodes * args.steps / t_e2e / 1e9, "unit": "GLUPS",
+               "h2d_bytes_per_step": bi / args.steps, "d2h_bytes_per_step": bo / args.steps,
+               "seconds": t_e2e}
+
+    # ---- CPU oracle on a bounded sample --------------------------------------
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.cpu_steps > 0:
+        dt, cn, threads = run_oracle(case, args.cpu_steps)
+        cpu = {"value": cn * args.cpu_steps / dt / 1e9, "unit": "GLUPS", "cores": threads,
+               "kind": "oracle",
+               "sample": f"{args.cpu_steps} steps of the full {n}x{n} lattice, FP64, "
+                         f"{dt:.1f} s"}
+
+    if rank == 0:
+        launches = step_n + diss_n
+        line = {
+            "metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"reactive porous D2Q9 ADE-LBM {n}x{n}, disks r 8-24 at "
+                                   "porosity 0.6, 16-mode stream function |v|max 0.05, "
+                                   "tau 0.7, surface k 1e-3 with dissolution, Dirichlet "
+                                   "inlet / Neumann outlet, periodic y",
+                       "nx": n, "ny": n, "fluid_nodes": n_fluid,
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "l2": "inputs larger than L2 (2 x 604 MB populations), no flush"},
+            "fluid_glups": world * n_fluid * args.steps / (ms / 1e3) / 1e9,
+            "roofline": {"bound": "hbm", "kernel": "lbm_step<float>",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind,
+                         "traffic": traffic, "algorithmic_bytes_per_launch": bytes_step,
+                         "kernel_ms_per_launch": per_launch_ms,
+                         "dissolve_ms_per_launch": diss_ms / max(diss_n, 1)},
+            "fp64": fp64, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clocks.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

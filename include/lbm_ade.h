@@ -1,0 +1,179 @@
+/*
+ * lbm_ade.h -- C ABI of the GB300 lattice Boltzmann advection-diffusion-
+ * reaction library (liblbmade.so).
+ *
+ * The library advances the pore-scale subdomain of the hybrid FEM/LBM
+ * multi-time-step method of Karimi & Nakshatrala (arXiv 1601.02708): a D2Q9
+ * BGK lattice Boltzmann scheme for the advection-diffusion equation
+ * (Sec. 4.1, Eqs. "LBE", "Collision", "LBM_feq", "LBM_Macro") with the
+ * maximum-entropy Dirichlet and Neumann boundary conditions of Sec. 4.1.1,
+ * halfway bounce-back at solid nodes, a first-order reaction sink with
+ * optional mineral dissolution, the multi-time-step interpolation of
+ * interface data (Sec. 6.2 (iii), Eq. "MTS") and the LBM -> FEM trace
+ * (Sec. 6.2 (ii)).
+ *
+ * Conventions shared by every call
+ *  - Lattice units: h = dt = 1, c_s^2 = 1/3, D = (tau - 1/2) / 3.
+ *  - D2Q9 direction order: 0 rest, 1 E(+1,0), 2 N(0,+1), 3 W(-1,0), 4 S(0,-1),
+ *    5 NE, 6 NW, 7 SW, 8 SE; weights 4/9, 1/9 (1-4), 1/36 (5-8).
+ *  - Node fields are row-major [ny][nx] (x fastest), populations
+ *    [9][ny][nx], velocity [2][ny][nx] (v_x plane, then v_y plane).
+ *  - Edge data (Dirichlet values, Neumann fluxes) use the edge layout
+ *    [W: ny][E: ny][S: nx][N: nx], length 2 (nx + ny); W is x = 0, E is
+ *    x = nx - 1, S is y = 0, N is y = ny - 1.  A corner node takes its value
+ *    from the first side in the order W, E, S, N whose kind applies.
+ *  - Every pointer argument may point to host memory or to device memory of
+ *    the context's device; the library detects which.  Inputs are copied (or
+ *    read on the context's stream before the call's work completes); the
+ *    library never keeps or frees caller memory.  Results written to host
+ *    memory are complete when the call returns; results written to device
+ *    memory are ordered on the context's stream.
+ *  - Every call returns an lbm_status; no call aborts, exits or traps.  On an
+ *    error, lbm_last_error() describes it (per thread).
+ */
+#ifndef LBM_ADE_H
+#define LBM_ADE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_ADE_ABI_VERSION 1
+
+typedef struct lbm_ctx lbm_ctx; /* opaque; owned by the library until lbm_destroy */
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_ERR_ARG = -1,     /* invalid argument (size, tau <= 1/2, edge kinds, NULL) */
+  LBM_ERR_CUDA = -2,    /* a CUDA call failed; the message names it */
+  LBM_ERR_NOMEM = -3,   /* device allocation failed */
+  LBM_ERR_STATE = -4    /* context misuse (e.g. restore from a foreign blob) */
+} lbm_status;
+
+typedef enum {
+  LBM_EDGE_PERIODIC = 0,  /* wraps to the opposite side (both sides must be periodic) */
+  LBM_EDGE_DIRICHLET = 1, /* max-entropy Dirichlet, Sec. 4.1.1 (a) */
+  LBM_EDGE_NEUMANN = 2    /* max-entropy Neumann on the first moment, Sec. 4.1.1 (b) */
+} lbm_edge_kind;
+
+typedef enum {
+  LBM_REACT_NONE = 0,
+  LBM_REACT_SURFACE = 1, /* sink at fluid nodes with a solid D2Q9 neighbour */
+  LBM_REACT_BULK = 2     /* sink at every fluid node */
+} lbm_react_mode;
+
+enum { LBM_SIDE_W = 0, LBM_SIDE_E = 1, LBM_SIDE_S = 2, LBM_SIDE_N = 3 };
+
+typedef struct {
+  int nx, ny;        /* lattice nodes, each >= 2 */
+  int precision;     /* 32: FP32 populations and arithmetic (FP64 boundary
+                        solves, mineral and sums); 64: FP64 throughout */
+  int edge[4];       /* lbm_edge_kind of the W, E, S, N sides */
+  double tau;        /* BGK relaxation time (Eq. "Collision"), > 1/2 */
+  int react_mode;    /* lbm_react_mode */
+  double k_scalar;   /* first-order rate where k_field is NULL */
+  int dissolution;   /* nonzero (surface mode only): the sink removes mineral
+                        from the solid neighbours in proportion to the link
+                        weights; a solid node whose mineral reaches <= 0
+                        becomes fluid with zero populations */
+} lbm_params;
+
+typedef struct {
+  double mass;             /* sum of u over the lattice at the current time */
+  double outlet_J;         /* sum over all steps of the east-edge (x = nx-1)
+                              fluid-node concentrations */
+  long long steps;         /* time steps taken since lbm_init */
+  long long bc_infeasible; /* boundary solves whose data had no non-negative
+                              solution (Dirichlet: applied literally; Neumann:
+                              unknowns set to zero) */
+  long long flips;         /* solid nodes turned fluid by dissolution */
+  long long n_solid;       /* solid nodes at the current time */
+} lbm_diag;
+
+/* Create a context and initialise the populations to the equilibrium of u0,
+ * f_i(x, 0) = f_i^eq(x, 0; u0(x)) (Sec. 6.2 (i), Eq. "LBM_feq").
+ *   solid   [ny][nx] nonzero = solid node (NULL: all fluid)
+ *   vel     [2][ny][nx] advection velocity, lattice units (NULL: zero);
+ *           the caller zeroes it in solids
+ *   k_field [ny][nx] per-node rate (NULL: p->k_scalar everywhere)
+ *   mineral [ny][nx] mineral mass of solid nodes (NULL: 1.0)
+ *   u0      [ny][nx] initial concentration (NULL: zero)
+ *   stream  cudaStream_t the context launches on (NULL: legacy default)
+ * Device memory is allocated by the library and released by lbm_destroy. */
+lbm_status lbm_init(lbm_ctx** out, const lbm_params* p, const uint8_t* solid,
+                    const double* vel, const double* k_field,
+                    const double* mineral, const double* u0, void* stream);
+
+/* Advance n time steps: substeps j = 1..n of a coarse step split eta ways
+ * (Algorithm 1, inner loop).  Each step streams, applies bounce-back and the
+ * boundary conditions, takes the moments, reacts and collides.  Dirichlet
+ * data at substep j are (1 - j/eta) u_dir_t0 + (j/eta) u_dir_t1 (Eq. "MTS");
+ * q_neu are the Neumann first-moment values e.n-weighted, outward positive.
+ * Edge arrays use the edge layout; NULL means zero (u_dir_t1 NULL: equal to
+ * u_dir_t0).  n = 0 is a no-op.  Asynchronous on the context's stream. */
+lbm_status lbm_substeps(lbm_ctx* c, int n, int eta, const double* u_dir_t0,
+                        const double* u_dir_t1, const double* q_neu);
+
+/* LBM -> FEM transfer, Sec. 6.2 (ii): bilinear value of the current u at
+ * npts points xy[npts][2] given in lattice coordinates.  A point outside
+ * [0, nx-1] x [0, ny-1] across a non-periodic side yields NaN. */
+lbm_status lbm_interface_trace(lbm_ctx* c, int npts, const double* xy,
+                               double* u_out);
+
+/* Current concentration u = sum_i f_i (Eq. "LBM_Macro"), [ny][nx], written
+ * as float (out_precision 32) or double (64); zero at solid nodes. */
+lbm_status lbm_get_concentration(lbm_ctx* c, void* out, int out_precision);
+
+/* Stored populations [9][ny][nx] as double.  They are post-collision: the
+ * values the next step streams. */
+lbm_status lbm_get_populations(lbm_ctx* c, double* out);
+
+/* Current solid mask [ny][nx] (1 = solid) and mineral mass [ny][nx].  The
+ * mineral already carries the sink of the stored post-collision populations,
+ * i.e. one reaction step beyond the returned concentration. */
+lbm_status lbm_get_solid(lbm_ctx* c, uint8_t* out);
+lbm_status lbm_get_mineral(lbm_ctx* c, double* out);
+
+/* Reductions over the lattice in FP64, in a fixed order (deterministic). */
+lbm_status lbm_diagnostics(lbm_ctx* c, lbm_diag* out);
+
+/* Schwarz rollback (Algorithm 1 restarts every sub-iteration from the state
+ * at the start of the coarse step): lbm_state_bytes gives the size of a
+ * state blob; lbm_save writes the full state into a caller-owned buffer of
+ * at least that size; lbm_restore reads it back into the same context. */
+lbm_status lbm_state_bytes(lbm_ctx* c, size_t* bytes);
+lbm_status lbm_save(lbm_ctx* c, void* buf, size_t bytes);
+lbm_status lbm_restore(lbm_ctx* c, const void* buf, size_t bytes);
+
+/* Kernel timing for performance reports.  While enabled, lbm_substeps
+ * records a CUDA event pair on the context's stream around every launch of
+ * the fused step kernel and of the dissolution kernel;
+ * lbm_kernel_times_read waits for the stream and returns the summed device
+ * milliseconds and launch counts since the last enable (step kernel first,
+ * then dissolution), then keeps timing.  Timing adds two event records per
+ * launch and nothing else to the launch sequence. */
+lbm_status lbm_kernel_timing(lbm_ctx* c, int enable);
+lbm_status lbm_kernel_times_read(lbm_ctx* c, double* step_ms, long long* step_launches,
+                                 double* dissolve_ms, long long* dissolve_launches);
+
+/* Change the stream the context launches on; wait for its work. */
+lbm_status lbm_set_stream(lbm_ctx* c, void* stream);
+lbm_status lbm_synchronize(lbm_ctx* c);
+
+/* Release the context's device memory (waits for its stream first). */
+void lbm_destroy(lbm_ctx* c);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* lbm_last_error(void);
+
+/* LBM_ADE_ABI_VERSION of the loaded library. */
+int lbm_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_ADE_H */

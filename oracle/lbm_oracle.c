@@ -149,6 +149,7 @@ static double solid_link_weight(const or_lbm *o, int x, int y) {
 
 static void moments(or_lbm *o) {
   size_t N = nn(o);
+#pragma omp parallel for schedule(static)
   for (size_t n = 0; n < N; ++n) {
     double s = 0.0;
     if (!o->solid[n])
@@ -305,10 +306,11 @@ static size_t edge_slot(const or_lbm *o, int s, int x, int y) {
 }
 
 /* Collision with reaction sink; mineral bookkeeping. */
-static void collide(or_lbm *o, double *fout) {
+static double collide(or_lbm *o, double *fout) {
   size_t N = nn(o);
   const double omega = 1.0 / o->tau;
-#pragma omp parallel for schedule(static)
+  double removed = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : removed)
   for (int y = 0; y < o->ny; ++y)
     for (int x = 0; x < o->nx; ++x) {
       size_t n = at(o, x, y);
@@ -321,7 +323,9 @@ static void collide(or_lbm *o, double *fout) {
         double post = fi + omega * (feq(i, u, o->vel[n], o->vel[N + n]) - fi);
         fout[(size_t)i * N + n] = post - WT[i] * kr * u;
       }
+      removed += kr * u;
     }
+  return removed;
 }
 
 /* Mineral decrement: the sink k u at a reactive fluid node x is taken from
@@ -354,6 +358,9 @@ static void stream(or_lbm *o) {
   size_t N = nn(o);
   memset(o->known, 0, NQ * N);
   memset(o->fnew, 0, NQ * N * sizeof(double));
+  /* each (population, node) of fnew has exactly one writer, so rows can be
+     streamed in parallel */
+#pragma omp parallel for schedule(static)
   for (int y = 0; y < o->ny; ++y)
     for (int x = 0; x < o->nx; ++x) {
       size_t n = at(o, x, y);
@@ -443,14 +450,7 @@ void or_lbm_substeps(or_lbm *o, int n, int eta, const double *ua,
   size_t N = nn(o);
   for (int j = 1; j <= n; ++j) {
     /* collide (with the reaction sink) */
-    collide(o, o->fpost);
-    {
-      double r = 0.0;
-      for (int y = 0; y < o->ny; ++y)
-        for (int x = 0; x < o->nx; ++x)
-          if (reactive(o, x, y)) r += o->k[at(o, x, y)] * o->u[at(o, x, y)];
-      o->reacted += r;
-    }
+    o->reacted += collide(o, o->fpost);
     if (o->dissolution && o->react_mode == REACT_SURFACE) dissolve_gather(o);
     /* stream, then boundary conditions */
     stream(o);
@@ -480,7 +480,10 @@ void or_lbm_get_mineral(const or_lbm *o, double *out) { memcpy(out, o->mineral, 
 
 /* Post-collision populations of the current state (what the next step would
  * stream), for comparing against a solver that stores them. */
-void or_lbm_get_fpost(or_lbm *o, double *out) { collide(o, out); }
+void or_lbm_get_fpost(or_lbm *o, double *out) {
+  memset(out, 0, NQ * nn(o) * sizeof(double)); /* solid nodes hold no populations */
+  (void)collide(o, out);
+}
 
 /* diag: [mass, J, reacted, bc_infeasible, flips, newton_iters, newton_fail, steps] */
 void or_lbm_diag(const or_lbm *o, double *d) {

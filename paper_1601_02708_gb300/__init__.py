@@ -1,0 +1,13 @@
+"""GB300-native D2Q9 lattice Boltzmann advection-diffusion-reaction library
+for the pore-scale subdomain of the hybrid FEM/LBM multi-time-step method
+(Karimi & Nakshatrala, arXiv 1601.02708).
+
+The compute path is the CUDA library liblbmade.so (C ABI in
+include/lbm_ade.h); `LBM` wraps it.  Nothing here falls back to a CPU
+implementation: without the built library, constructing `LBM` raises.
+"""
+from .lbm import (DIRICHLET, LBM, LBMError, NEUMANN, PERIODIC, REACT_BULK,
+                  REACT_NONE, REACT_SURFACE)
+
+__all__ = ["LBM", "LBMError", "PERIODIC", "DIRICHLET", "NEUMANN",
+           "REACT_NONE", "REACT_SURFACE", "REACT_BULK"]

@@ -1,0 +1,90 @@
+"""ctypes declarations of the C ABI in include/lbm_ade.h (marshalling only)."""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+LBM_OK = 0
+STATUS_NAMES = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_CUDA",
+                -3: "LBM_ERR_NOMEM", -4: "LBM_ERR_STATE"}
+
+
+class LBMError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("precision", ctypes.c_int), ("edge", ctypes.c_int * 4),
+                ("tau", ctypes.c_double), ("react_mode", ctypes.c_int),
+                ("k_scalar", ctypes.c_double), ("dissolution", ctypes.c_int)]
+
+
+class Diag(ctypes.Structure):
+    _fields_ = [("mass", ctypes.c_double), ("outlet_J", ctypes.c_double),
+                ("steps", ctypes.c_longlong), ("bc_infeasible", ctypes.c_longlong),
+                ("flips", ctypes.c_longlong), ("n_solid", ctypes.c_longlong)]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load liblbmade.so; raises if it has not been built (there is no
+    fallback: the CUDA library is the only implementation)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(
+                f"{path} is missing: build it with paper_1601_02708_gb300.build.build() "
+                "(or __graft_entry__.build())")
+        lib = ctypes.CDLL(path)
+        P, I, D, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+        sig = {
+            "lbm_init": [ctypes.POINTER(P), ctypes.POINTER(Params), P, P, P, P, P, P],
+            "lbm_substeps": [P, I, I, P, P, P],
+            "lbm_interface_trace": [P, I, P, P],
+            "lbm_get_concentration": [P, P, I],
+            "lbm_get_populations": [P, P],
+            "lbm_get_solid": [P, P],
+            "lbm_get_mineral": [P, P],
+            "lbm_diagnostics": [P, ctypes.POINTER(Diag)],
+            "lbm_state_bytes": [P, ctypes.POINTER(S)],
+            "lbm_save": [P, P, S],
+            "lbm_restore": [P, P, S],
+            "lbm_set_stream": [P, P],
+            "lbm_synchronize": [P],
+            "lbm_kernel_timing": [P, I],
+            "lbm_kernel_times_read": [P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong),
+                                      ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong)],
+        }
+        for name, args in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = I
+        lib.lbm_destroy.argtypes = [P]
+        lib.lbm_destroy.restype = None
+        lib.lbm_last_error.argtypes = []
+        lib.lbm_last_error.restype = ctypes.c_char_p
+        lib.lbm_abi_version.argtypes = []
+        lib.lbm_abi_version.restype = I
+        _lib = lib
+        return lib
+
+
+def check(status: int):
+    if status != LBM_OK:
+        msg = load().lbm_last_error().decode(errors="replace")
+        raise LBMError(status, msg)

@@ -1,0 +1,815 @@
+// lbm_api.cu -- C ABI of liblbmade.so (declared in include/lbm_ade.h).
+//
+// Owns the device state of one lattice and launches the kernels of
+// lbm_kernels.cuh on the context's stream.  Host-side work is argument
+// checking, residency detection of caller pointers and launch bookkeeping.
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "lbm_ade.h"
+#include "lbm_kernels.cuh"
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+lbm_status fail(lbm_status s, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+#define CK(call)                                                              \
+  do {                                                                        \
+    cudaError_t e_ = (call);                                                  \
+    if (e_ != cudaSuccess)                                                    \
+      return fail(e_ == cudaErrorMemoryAllocation ? LBM_ERR_NOMEM             \
+                                                  : LBM_ERR_CUDA,             \
+                  "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),     \
+                  __FILE__, __LINE__);                                        \
+  } while (0)
+
+bool on_device(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+cudaMemcpyKind kind_from(const void* p) {
+  return on_device(p) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+}
+
+// ---- small element-wise kernels: layout conversion only -------------------
+template <typename T>
+__global__ void k_pitch_in(const double* __restrict__ src, T* __restrict__ dst,
+                           int nx, int ny, int pitch, int planes, double fill) {
+  const long long total = (long long)nx * ny * planes;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long p = i / ((long long)nx * ny), r = i % ((long long)nx * ny);
+    const long long y = r / nx, x = r % nx;
+    dst[(p * ny + y) * pitch + x] = (T)(src ? src[i] : fill);
+  }
+}
+
+__global__ void k_mask_in(const uint8_t* __restrict__ src, uint8_t* __restrict__ dst,
+                          int nx, int ny, int pitch) {
+  const long long total = (long long)nx * ny;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long y = i / nx, x = i % nx;
+    dst[y * pitch + x] = (src && src[i]) ? lbm::kSolid : 0;
+  }
+}
+
+template <typename T, typename O>
+__global__ void k_pitch_out(const T* __restrict__ src, O* __restrict__ dst, int nx,
+                            int ny, int pitch, int planes) {
+  const long long total = (long long)nx * ny * planes;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long p = i / ((long long)nx * ny), r = i % ((long long)nx * ny);
+    const long long y = r / nx, x = r % nx;
+    dst[i] = (O)src[(p * ny + y) * pitch + x];
+  }
+}
+
+__global__ void k_solid_out(const uint8_t* __restrict__ mask, uint8_t* __restrict__ dst,
+                            int nx, int ny, int pitch) {
+  const long long total = (long long)nx * ny;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long y = i / nx, x = i % nx;
+    dst[i] = (mask[y * pitch + x] & lbm::kSolid) ? 1 : 0;
+  }
+}
+
+// Fixed-order FP64 reductions for lbm_diagnostics (one block).
+struct DiagDev {
+  double mass, J;
+  long long infeasible, n_solid;
+};
+__global__ void k_diag(const double* __restrict__ partial, int nparts,
+                       const double* __restrict__ jnode, int ny,
+                       const long long* __restrict__ infeas, int nedge,
+                       const uint8_t* __restrict__ mask, int nx, int pitch,
+                       DiagDev* out) {
+  __shared__ double sd[256];
+  __shared__ long long sl[256];
+  const int t = threadIdx.x;
+  double m = 0.0, j = 0.0;
+  long long c = 0, ns = 0;
+  for (int i = t; i < nparts; i += blockDim.x) m += partial[i];
+  for (int i = t; i < ny; i += blockDim.x) j += jnode[i];
+  for (int i = t; i < nedge; i += blockDim.x) c += infeas[i];
+  for (long long i = t; i < (long long)nx * ny; i += blockDim.x) {
+    const long long y = i / nx, x = i % nx;
+    ns += (mask[y * pitch + x] & lbm::kSolid) ? 1 : 0;
+  }
+  double* outs[2] = {&out->mass, &out->J};
+  double vals[2] = {m, j};
+  for (int k = 0; k < 2; ++k) {
+    sd[t] = vals[k];
+    __syncthreads();
+    if (t == 0) {
+      double s = 0.0;
+      for (int i = 0; i < (int)blockDim.x; ++i) s += sd[i];
+      *outs[k] = s;
+    }
+    __syncthreads();
+  }
+  long long* louts[2] = {&out->infeasible, &out->n_solid};
+  long long lv[2] = {c, ns};
+  for (int k = 0; k < 2; ++k) {
+    sl[t] = lv[k];
+    __syncthreads();
+    if (t == 0) {
+      long long s = 0;
+      for (int i = 0; i < (int)blockDim.x; ++i) s += sl[i];
+      *louts[k] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// LBM -> FEM transfer (Sec. 6.2 (ii)): bilinear patch of the four nodes
+// around each point.
+template <typename Real>
+__global__ void k_trace(const Real* __restrict__ u, int nx, int ny, int pitch,
+                        int per_x, int per_y, const double* __restrict__ xy,
+                        int npts, double* __restrict__ out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= npts) return;
+  const double px = xy[2 * k], py = xy[2 * k + 1];
+  const bool bad = (!per_x && !(px >= 0.0 && px <= nx - 1)) ||
+                   (!per_y && !(py >= 0.0 && py <= ny - 1)) || !isfinite(px) ||
+                   !isfinite(py);
+  if (bad) {
+    out[k] = nan("");
+    return;
+  }
+  int x1 = (int)floor(px), y1 = (int)floor(py);
+  if (!per_x && x1 >= nx - 1) x1 = nx - 2;
+  if (!per_y && y1 >= ny - 1) y1 = ny - 2;
+  const double gx = px - x1, gy = py - y1;
+  int ax = x1, ay = y1, bx = x1 + 1, by = y1 + 1;
+  if (per_x) { ax = ((ax % nx) + nx) % nx; bx = ((bx % nx) + nx) % nx; }
+  if (per_y) { ay = ((ay % ny) + ny) % ny; by = ((by % ny) + ny) % ny; }
+  const double u1 = (double)u[(long long)ay * pitch + ax];
+  const double u2 = (double)u[(long long)ay * pitch + bx];
+  const double u3 = (double)u[(long long)by * pitch + bx];
+  const double u4 = (double)u[(long long)by * pitch + ax];
+  out[k] = u1 * (1 - gx) * (1 - gy) + u2 * gx * (1 - gy) + u3 * gx * gy +
+           u4 * (1 - gx) * gy;
+}
+
+int grid1d(long long n) {
+  long long b = (n + 255) / 256;
+  if (b < 1) b = 1;
+  if (b > 152 * 32) b = 152 * 32;
+  return (int)b;
+}
+
+}  // namespace
+
+struct lbm_ctx {
+  lbm_params p;
+  int pitch = 0;
+  long long plane = 0;
+  size_t esize = 4;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  void* f[2] = {nullptr, nullptr};  // Real [9][ny][pitch]
+  int cur = 0;                      // buffer holding the current f*
+  uint8_t* mask = nullptr;
+  void* vel = nullptr;     // Real [2][ny][pitch]
+  void* kf = nullptr;      // Real [ny][pitch] or null
+  void* u = nullptr;       // Real [ny][pitch]
+  void* ureact = nullptr;  // Real [ny][pitch] (dissolution)
+  double* mineral = nullptr;
+  double* edge = nullptr;  // [3][nedge]: u_dir_t0, u_dir_t1, q
+  long long* infeasible = nullptr;  // [nedge]
+  double* jnode = nullptr;          // [ny]
+  double* partial = nullptr;        // [nblocks]
+  int* flip_list = nullptr;
+  int* flip_count = nullptr;  // + done counter + padding
+  long long* counters = nullptr;  // [0] flips total
+  DiagDev* diag = nullptr;
+  void* scratch = nullptr;  // host-copy staging for outputs
+  size_t scratch_bytes = 0;
+  long long steps = 0;
+  int nedge = 0;
+  dim3 grid, block;
+  // kernel timing (lbm_kernel_timing): event pairs per launch, folded into
+  // the sums whenever the pool fills or the times are read
+  bool timing = false;
+  static constexpr int kPool = 512;
+  cudaEvent_t ev[2][kPool][2] = {};
+  int ev_used[2] = {0, 0};
+  double ms_sum[2] = {0.0, 0.0};
+  long long launches[2] = {0, 0};
+};
+
+namespace {
+
+template <typename Real>
+lbm::StepArgs<Real> step_args(lbm_ctx* c, double frac) {
+  lbm::StepArgs<Real> a;
+  a.fin = (const Real*)c->f[c->cur];
+  a.fout = (Real*)c->f[c->cur ^ 1];
+  a.mask = c->mask;
+  a.vel = (const Real*)c->vel;
+  a.kf = (const Real*)c->kf;
+  a.u_out = (Real*)c->u;
+  a.ureact = (Real*)c->ureact;
+  a.ua = c->edge;
+  a.ub = c->edge + c->nedge;
+  a.q = c->edge + 2 * c->nedge;
+  a.infeasible = c->infeasible;
+  a.jnode = c->jnode;
+  a.partial = c->partial;
+  a.plane = c->plane;
+  a.nx = c->p.nx;
+  a.ny = c->p.ny;
+  a.pitch = c->pitch;
+  a.per_x = c->p.edge[0] == LBM_EDGE_PERIODIC;
+  a.per_y = c->p.edge[2] == LBM_EDGE_PERIODIC;
+  for (int s = 0; s < 4; ++s) a.edge[s] = c->p.edge[s];
+  a.react_mode = c->p.react_mode;
+  a.dissolution = c->p.dissolution;
+  a.omega = (Real)(1.0 / c->p.tau);
+  a.k_scalar = (Real)c->p.k_scalar;
+  a.frac = frac;
+  return a;
+}
+
+lbm::DissolveArgs dissolve_args(lbm_ctx* c) {
+  lbm::DissolveArgs d;
+  d.mask = c->mask;
+  d.mineral = c->mineral;
+  d.flip_list = c->flip_list;
+  d.flip_count = c->flip_count;
+  d.done = (unsigned*)(c->flip_count + 1);
+  d.flips_total = c->counters;
+  d.nx = c->p.nx;
+  d.ny = c->p.ny;
+  d.pitch = c->pitch;
+  d.per_x = c->p.edge[0] == LBM_EDGE_PERIODIC;
+  d.per_y = c->p.edge[2] == LBM_EDGE_PERIODIC;
+  d.check_all = 0;
+  return d;
+}
+
+lbm_status fold_times(lbm_ctx* c, int which) {
+  if (c->ev_used[which] == 0) return LBM_OK;
+  CK(cudaEventSynchronize(c->ev[which][c->ev_used[which] - 1][1]));
+  for (int i = 0; i < c->ev_used[which]; ++i) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, c->ev[which][i][0], c->ev[which][i][1]));
+    c->ms_sum[which] += ms;
+  }
+  c->launches[which] += c->ev_used[which];
+  c->ev_used[which] = 0;
+  return LBM_OK;
+}
+
+// Record the opening event of a timed launch (which: 0 step, 1 dissolve).
+lbm_status time_begin(lbm_ctx* c, int which) {
+  if (!c->timing) return LBM_OK;
+  if (c->ev_used[which] == lbm_ctx::kPool) {
+    lbm_status s = fold_times(c, which);
+    if (s != LBM_OK) return s;
+  }
+  cudaEvent_t* e = c->ev[which][c->ev_used[which]];
+  if (!e[0]) {
+    CK(cudaEventCreate(&e[0]));
+    CK(cudaEventCreate(&e[1]));
+  }
+  CK(cudaEventRecord(e[0], c->stream));
+  return LBM_OK;
+}
+lbm_status time_end(lbm_ctx* c, int which) {
+  if (!c->timing) return LBM_OK;
+  CK(cudaEventRecord(c->ev[which][c->ev_used[which]][1], c->stream));
+  c->ev_used[which] += 1;
+  return LBM_OK;
+}
+
+template <typename Real>
+lbm_status launch_dissolve(lbm_ctx* c, bool check_all = false) {
+  lbm_status s = time_begin(c, 1);
+  if (s != LBM_OK) return s;
+  lbm::DissolveArgs d = dissolve_args(c);
+  d.check_all = check_all ? 1 : 0;
+  lbm::lbm_dissolve<Real><<<c->grid, c->block, 0, c->stream>>>(d, (const Real*)c->ureact);
+  CK(cudaGetLastError());
+  return time_end(c, 1);
+}
+
+template <typename Real>
+lbm_status run_steps(lbm_ctx* c, int n, int eta) {
+  for (int j = 1; j <= n; ++j) {
+    const double frac = (double)j / (double)eta;
+    auto a = step_args<Real>(c, frac);
+    lbm_status s0 = time_begin(c, 0);
+    if (s0 != LBM_OK) return s0;
+    if (j == n)
+      lbm::lbm_step<Real, true><<<c->grid, c->block, 0, c->stream>>>(a);
+    else
+      lbm::lbm_step<Real, false><<<c->grid, c->block, 0, c->stream>>>(a);
+    CK(cudaGetLastError());
+    s0 = time_end(c, 0);
+    if (s0 != LBM_OK) return s0;
+    c->cur ^= 1;
+    if (c->p.dissolution) {
+      lbm_status s = launch_dissolve<Real>(c);
+      if (s != LBM_OK) return s;
+    }
+    c->steps += 1;
+  }
+  return LBM_OK;
+}
+
+template <typename Real>
+lbm_status run_init(lbm_ctx* c, const double* u0dev) {
+  auto a = step_args<Real>(c, 0.0);
+  a.fout = (Real*)c->f[0];
+  lbm::lbm_init_kernel<Real><<<c->grid, c->block, 0, c->stream>>>(a, u0dev);
+  CK(cudaGetLastError());
+  c->cur = 0;
+  // the first pass also flips solid nodes given with no mineral at all
+  if (c->p.dissolution) return launch_dissolve<Real>(c, true);
+  return LBM_OK;
+}
+
+// Copy a caller array of `count` doubles (host or device) to a device buffer.
+lbm_status stage_doubles(lbm_ctx* c, const double* src, size_t count, double** out,
+                         bool* owned) {
+  *owned = false;
+  *out = nullptr;
+  if (!src) return LBM_OK;
+  if (on_device(src)) {
+    *out = const_cast<double*>(src);
+    return LBM_OK;
+  }
+  CK(cudaMalloc((void**)out, count * sizeof(double)));
+  *owned = true;
+  CK(cudaMemcpyAsync(*out, src, count * sizeof(double), cudaMemcpyHostToDevice,
+                     c->stream));
+  return LBM_OK;
+}
+
+void free_ctx(lbm_ctx* c) {
+  if (!c) return;
+  for (int w = 0; w < 2; ++w)
+    for (int i = 0; i < lbm_ctx::kPool; ++i)
+      for (int k = 0; k < 2; ++k)
+        if (c->ev[w][i][k]) cudaEventDestroy(c->ev[w][i][k]);
+  void* ptrs[] = {c->f[0], c->f[1], c->mask, c->vel, c->kf, c->u, c->ureact,
+                  c->mineral, c->edge, c->infeasible, c->jnode, c->partial,
+                  c->flip_list, c->flip_count, c->counters, c->diag, c->scratch};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete c;
+}
+
+lbm_status ensure_scratch(lbm_ctx* c, size_t bytes) {
+  if (c->scratch_bytes >= bytes) return LBM_OK;
+  if (c->scratch) cudaFree(c->scratch);
+  c->scratch = nullptr;
+  c->scratch_bytes = 0;
+  CK(cudaMalloc(&c->scratch, bytes));
+  c->scratch_bytes = bytes;
+  return LBM_OK;
+}
+
+lbm_status init_impl(lbm_ctx* c, const uint8_t* solid, const double* vel,
+                     const double* k_field, const double* mineral, const double* u0) {
+  const lbm_params& p = c->p;
+  const size_t nxy = (size_t)p.nx * p.ny;
+  c->pitch = (p.nx + 31) / 32 * 32;
+  c->plane = (long long)c->pitch * p.ny;
+  c->esize = p.precision == 64 ? 8 : 4;
+  c->nedge = 2 * (p.nx + p.ny);
+  c->block = dim3(lbm::kBX, lbm::kBY);
+  c->grid = dim3((p.nx + lbm::kBX - 1) / lbm::kBX, (p.ny + lbm::kBY - 1) / lbm::kBY);
+  const size_t plane_b = (size_t)c->plane * c->esize;
+  CK(cudaGetDevice(&c->device));
+  CK(cudaMalloc(&c->f[0], 9 * plane_b));
+  CK(cudaMalloc(&c->f[1], 9 * plane_b));
+  CK(cudaMemsetAsync(c->f[0], 0, 9 * plane_b, c->stream));
+  CK(cudaMemsetAsync(c->f[1], 0, 9 * plane_b, c->stream));
+  CK(cudaMalloc((void**)&c->mask, (size_t)c->plane));
+  CK(cudaMemsetAsync(c->mask, 0, (size_t)c->plane, c->stream));
+  CK(cudaMalloc(&c->vel, 2 * plane_b));
+  CK(cudaMemsetAsync(c->vel, 0, 2 * plane_b, c->stream));
+  CK(cudaMalloc(&c->u, plane_b));
+  CK(cudaMemsetAsync(c->u, 0, plane_b, c->stream));
+  if (k_field) CK(cudaMalloc(&c->kf, plane_b));
+  if (p.dissolution) {
+    CK(cudaMalloc(&c->ureact, plane_b));
+    CK(cudaMemsetAsync(c->ureact, 0, plane_b, c->stream));
+    CK(cudaMalloc((void**)&c->mineral, (size_t)c->plane * sizeof(double)));
+    CK(cudaMalloc((void**)&c->flip_list, (size_t)c->plane * sizeof(int)));
+  }
+  CK(cudaMalloc((void**)&c->flip_count, 4 * sizeof(int)));
+  CK(cudaMemsetAsync(c->flip_count, 0, 4 * sizeof(int), c->stream));
+  CK(cudaMalloc((void**)&c->counters, 4 * sizeof(long long)));
+  CK(cudaMemsetAsync(c->counters, 0, 4 * sizeof(long long), c->stream));
+  CK(cudaMalloc((void**)&c->edge, 3 * (size_t)c->nedge * sizeof(double)));
+  CK(cudaMemsetAsync(c->edge, 0, 3 * (size_t)c->nedge * sizeof(double), c->stream));
+  CK(cudaMalloc((void**)&c->infeasible, (size_t)c->nedge * sizeof(long long)));
+  CK(cudaMemsetAsync(c->infeasible, 0, (size_t)c->nedge * sizeof(long long), c->stream));
+  CK(cudaMalloc((void**)&c->jnode, (size_t)p.ny * sizeof(double)));
+  CK(cudaMemsetAsync(c->jnode, 0, (size_t)p.ny * sizeof(double), c->stream));
+  CK(cudaMalloc((void**)&c->partial, (size_t)c->grid.x * c->grid.y * sizeof(double)));
+  CK(cudaMalloc((void**)&c->diag, sizeof(DiagDev)));
+
+  // inputs: host arrays are staged through temporary device buffers
+  double *dvel = nullptr, *dk = nullptr, *dmin = nullptr, *du0 = nullptr;
+  bool ovel = false, ok = false, omin = false, ou0 = false;
+  uint8_t* dsolid = nullptr;
+  bool osolid = false;
+  lbm_status st = LBM_OK;
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(c->stream);
+    if (ovel) cudaFree(dvel);
+    if (ok) cudaFree(dk);
+    if (omin) cudaFree(dmin);
+    if (ou0) cudaFree(du0);
+    if (osolid) cudaFree(dsolid);
+  };
+  if ((st = stage_doubles(c, vel, 2 * nxy, &dvel, &ovel)) != LBM_OK ||
+      (st = stage_doubles(c, k_field, nxy, &dk, &ok)) != LBM_OK ||
+      (st = stage_doubles(c, mineral, nxy, &dmin, &omin)) != LBM_OK ||
+      (st = stage_doubles(c, u0, nxy, &du0, &ou0)) != LBM_OK) {
+    cleanup();
+    return st;
+  }
+  if (solid) {
+    if (on_device(solid)) {
+      dsolid = const_cast<uint8_t*>(solid);
+    } else {
+      cudaError_t e = cudaMalloc((void**)&dsolid, nxy);
+      if (e != cudaSuccess) { cleanup(); return fail(LBM_ERR_NOMEM, "cudaMalloc: %s", cudaGetErrorString(e)); }
+      osolid = true;
+      cudaMemcpyAsync(dsolid, solid, nxy, cudaMemcpyHostToDevice, c->stream);
+    }
+  }
+  const int g = grid1d((long long)nxy * 2);
+  k_mask_in<<<g, 256, 0, c->stream>>>(dsolid, c->mask, p.nx, p.ny, c->pitch);
+  if (c->esize == 8) {
+    k_pitch_in<double><<<g, 256, 0, c->stream>>>(dvel, (double*)c->vel, p.nx, p.ny, c->pitch, 2, 0.0);
+    if (dk) k_pitch_in<double><<<g, 256, 0, c->stream>>>(dk, (double*)c->kf, p.nx, p.ny, c->pitch, 1, 0.0);
+  } else {
+    k_pitch_in<float><<<g, 256, 0, c->stream>>>(dvel, (float*)c->vel, p.nx, p.ny, c->pitch, 2, 0.0);
+    if (dk) k_pitch_in<float><<<g, 256, 0, c->stream>>>(dk, (float*)c->kf, p.nx, p.ny, c->pitch, 1, 0.0);
+  }
+  if (p.dissolution)
+    k_pitch_in<double><<<g, 256, 0, c->stream>>>(dmin, c->mineral, p.nx, p.ny, c->pitch, 1, 1.0);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) { cleanup(); return fail(LBM_ERR_CUDA, "input conversion: %s", cudaGetErrorString(e)); }
+  st = c->esize == 8 ? run_init<double>(c, du0) : run_init<float>(c, du0);
+  cleanup();
+  if (st != LBM_OK) return st;
+  CK(cudaGetLastError());
+  return LBM_OK;
+}
+
+lbm_status check_ctx(const lbm_ctx* c) {
+  if (!c) return fail(LBM_ERR_ARG, "null context");
+  return LBM_OK;
+}
+
+// state blob layout (all sections 256-byte aligned)
+struct Section {
+  void* ptr;
+  size_t bytes;
+};
+int state_sections(lbm_ctx* c, Section* s) {
+  int k = 0;
+  const size_t plane_b = (size_t)c->plane * c->esize;
+  s[k++] = {c->f[c->cur], 9 * plane_b};
+  s[k++] = {c->mask, (size_t)c->plane};
+  s[k++] = {c->u, plane_b};
+  s[k++] = {c->infeasible, (size_t)c->nedge * sizeof(long long)};
+  s[k++] = {c->jnode, (size_t)c->p.ny * sizeof(double)};
+  s[k++] = {c->partial, (size_t)c->grid.x * c->grid.y * sizeof(double)};
+  s[k++] = {c->counters, 4 * sizeof(long long)};
+  if (c->p.dissolution) s[k++] = {c->mineral, (size_t)c->plane * sizeof(double)};
+  return k;
+}
+size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+struct BlobHeader {
+  unsigned long long magic;
+  long long steps;
+  int nx, ny, precision, dissolution;
+};
+const unsigned long long kMagic = 0x4C424D4144453031ull;  // "LBMADE01"
+
+}  // namespace
+
+extern "C" {
+
+int lbm_abi_version(void) { return LBM_ADE_ABI_VERSION; }
+
+const char* lbm_last_error(void) { return g_err; }
+
+lbm_status lbm_init(lbm_ctx** out, const lbm_params* p, const uint8_t* solid,
+                    const double* vel, const double* k_field, const double* mineral,
+                    const double* u0, void* stream) {
+  g_err[0] = 0;
+  if (!out || !p) return fail(LBM_ERR_ARG, "lbm_init: null out or params");
+  *out = nullptr;
+  if (p->nx < 2 || p->ny < 2) return fail(LBM_ERR_ARG, "lbm_init: nx, ny must be >= 2");
+  if ((long long)((p->nx + 31) / 32 * 32) * p->ny > INT_MAX)
+    return fail(LBM_ERR_ARG, "lbm_init: lattice too large (pitch*ny > INT_MAX)");
+  if (p->precision != 32 && p->precision != 64)
+    return fail(LBM_ERR_ARG, "lbm_init: precision must be 32 or 64");
+  if (!(p->tau > 0.5) || !std::isfinite(p->tau))
+    return fail(LBM_ERR_ARG, "lbm_init: tau must be finite and > 1/2");
+  for (int s = 0; s < 4; ++s)
+    if (p->edge[s] < 0 || p->edge[s] > 2) return fail(LBM_ERR_ARG, "lbm_init: bad edge kind");
+  if ((p->edge[0] == LBM_EDGE_PERIODIC) != (p->edge[1] == LBM_EDGE_PERIODIC) ||
+      (p->edge[2] == LBM_EDGE_PERIODIC) != (p->edge[3] == LBM_EDGE_PERIODIC))
+    return fail(LBM_ERR_ARG, "lbm_init: opposite sides must both be periodic or both not");
+  if (p->react_mode < 0 || p->react_mode > 2) return fail(LBM_ERR_ARG, "lbm_init: bad react_mode");
+  if (!std::isfinite(p->k_scalar)) return fail(LBM_ERR_ARG, "lbm_init: k_scalar not finite");
+  if (p->dissolution && p->react_mode != LBM_REACT_SURFACE)
+    return fail(LBM_ERR_ARG, "lbm_init: dissolution needs react_mode = LBM_REACT_SURFACE");
+  lbm_ctx* c = new (std::nothrow) lbm_ctx();
+  if (!c) return fail(LBM_ERR_NOMEM, "lbm_init: host allocation failed");
+  c->p = *p;
+  c->stream = (cudaStream_t)stream;
+  lbm_status st = init_impl(c, solid, vel, k_field, mineral, u0);
+  if (st != LBM_OK) {
+    free_ctx(c);
+    return st;
+  }
+  *out = c;
+  return LBM_OK;
+}
+
+lbm_status lbm_substeps(lbm_ctx* c, int n, int eta, const double* u_dir_t0,
+                        const double* u_dir_t1, const double* q_neu) {
+  if (check_ctx(c)) return LBM_ERR_ARG;
+  if (n < 0 || eta < 1) return fail(LBM_ERR_ARG, "lbm_substeps: need n >= 0, eta >= 1");
+  if (n == 0) return LBM_OK;
+  const size_t eb = (size_t)c->nedge * sizeof(double);
+  double* e = c->edge;
+  if (u_dir_t0) CK(cudaMemcpyAsync(e, u_dir_t0, eb, kind_from(u_dir_t0), c->stream));
+  else CK(cudaMemsetAsync(e, 0, eb, c->stream));
+  const double* b = u_dir_t1 ? u_dir_t1 : u_dir_t0;
+  if (b) CK(cudaMemcpyAsync(e + c->nedge, b, eb, kind_from(b), c->stream));
+  else CK(cudaMemsetAsync(e + c->nedge, 0, eb, c->stream));
+  if (q_neu) CK(cudaMemcpyAsync(e + 2 * c->nedge, q_neu, eb, kind_from(q_neu), c->stream));
+  else CK(cudaMemsetAsync(e + 2 * c->nedge, 0, eb, c->stream));
+  // host-sourced edge data must not be reused before the copies complete
+  if ((u_dir_t0 && !on_device(u_dir_t0)) || (b && !on_device(b)) ||
+      (q_neu && !on_device(q_neu)))
+    CK(cudaStreamSynchronize(c->stream));
+  return c->esize == 8 ? run_steps<double>(c, n, eta) : run_steps<float>(c, n, eta);
+}
+
+lbm_status lbm_interface_trace(lbm_ctx* c, int npts, const double* xy, double* u_out) {
+  if (check_ctx(c)) return LBM_ERR_ARG;
+  if (npts < 0 || (npts > 0 && (!xy || !u_out)))
+    return fail(LBM_ERR_ARG, "lbm_interface_trace: bad arguments");
+  if (npts == 0) return LBM_OK;
+  const bool xy_dev = on_device(xy), out_dev = on_device(u_out);
+  const double* dxy = xy;
+  double* dout = u_out;
+  const size_t in_b = 2 * (size_t)npts * sizeof(double), out_b = (size_t)npts * sizeof(double);
+  if (!xy_dev || !out_dev) {
+    lbm_status s = ensure_scratch(c, align256(in_b) + out_b);
+    if (s != LBM_OK) return s;
+  }
+  if (!xy_dev) {
+    CK(cudaMemcpyAsync(c->scratch, xy, in_b, cudaMemcpyHostToDevice, c->stream));
+    dxy = (const double*)c->scratch;
+  }
+  if (!out_dev) dout = (double*)((char*)c->scratch + align256(in_b));
+  const int per_x = c->p.edge[0] == LBM_EDGE_PERIODIC, per_y = c->p.edge[2] == LBM_EDGE_PERIODIC;
+  const int g = (npts + 255) / 256;
+  if (c->esize == 8)
+    k_trace<double><<<g, 256, 0, c->stream>>>((const double*)c->u, c->p.nx, c->p.ny, c->pitch, per_x, per_y, dxy, npts, dout);
+  else
+    k_trace<float><<<g, 256, 0, c->stream>>>((const float*)c->u, c->p.nx, c->p.ny, c->pitch, per_x, per_y, dxy, npts, dout);
+  CK(cudaGetLastError());
+  if (!out_dev) {
+    CK(cudaMemcpyAsync(u_out, dout, out_b, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  } else if (!xy_dev) {
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  return LBM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+// Copy a pitched device field out to a caller array (host or device) of
+// `planes` [ny][nx] planes, converting to O.
+template <typename T, typename O>
+lbm_status field_out(lbm_ctx* c, const T* src, O* dst, int planes) {
+  const size_t bytes = (size_t)planes * c->p.nx * c->p.ny * sizeof(O);
+  const bool dev = on_device(dst);
+  O* d = dst;
+  if (!dev) {
+    lbm_status s = ensure_scratch(c, bytes);
+    if (s != LBM_OK) return s;
+    d = (O*)c->scratch;
+  }
+  k_pitch_out<T, O><<<grid1d((long long)planes * c->p.nx * c->p.ny), 256, 0, c->stream>>>(
+      src, d, c->p.nx, c->p.ny, c->pitch, planes);
+  CK(cudaGetLastError());
+  if (!dev) {
+    CK(cudaMemcpyAsync(dst, d, bytes, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  return LBM_OK;
+}
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_get_concentration(lbm_ctx* c, void* out, int out_precision) {
+  if (check_ctx(c)) return LBM_ERR_ARG;
+  if (!out || (out_precision != 32 && out_precision != 64))
+    return fail(LBM_ERR_ARG, "lbm_get_concentration: bad arguments");
+  if (c->esize == 8)
+    return out_precision == 64 ? field_out<double, double>(c, (const double*)c->u, (double*)out, 1)
+                               : field_out<double, float>(c, (const double*)c->u, (float*)out, 1);
+  return out_precision == 64 ? field_out<float, double>(c, (const float*)c->u, (double*)out, 1)
+                             : field_out<float, float>(c, (const float*)c->u, (float*)out, 1);
+}
+
+lbm_status lbm_get_populations(lbm_ctx* c, double* out) {
+  if (check_ctx(c)) return LBM_ERR_ARG;
+  if (!out) return fail(LBM_ERR_ARG, "lbm_get_populations: null out");
+  if (c->esize == 8) return field_out<double, double>(c, (const double*)c->f[c->cur], out, 9);
+  return field_out<float, double>(c, (const float*)c->f[c->cur], out, 9);
+}
+
+lbm_status lbm_get_solid(lbm_ctx* c, uint8_t* out) {
+  if (check_ctx(c)) return LBM_ERR_ARG;
+  if (!out) return fail(LBM_ERR_ARG, "lbm_get_solid: null out");
+  const size_t bytes = (size_t)c->p.nx * c->p.ny;
+  const bool dev = on_device(out);
+  uint8_t* d = out;
+  if (!dev) {
+    lbm_status s = ensure_scratch(c, bytes);
+    if (s != LBM_OK) return s;
+    d = (uint8_t*)c->scratch;
+  }
+  k_solid_out<<<grid1d((long long)bytes), 256, 0, c->stream>>>(c->mask, d, c->p.nx, c->p.ny, c->pitch);
+  CK(cudaGetLastError());
+  if (!dev) {
+    CK(cudaMemcpyAsync(out, d, bytes, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_get_mineral(lbm_ctx* c, double* out) {
+  if (check_ctx(c)) return LBM_ERR_ARG;
+  if (!out) return fail(LBM_ERR_ARG, "lbm_get_mineral: null out");
+  if (!c->p.dissolution) return fail(LBM_ERR_STATE, "lbm_get_mineral: dissolution is off");
+  return field_out<double, double>(c, c->mineral, out, 1);
+}
+
+lbm_status lbm_diagnostics(lbm_ctx* c, lbm_diag* out) {
+  if (check_ctx(c)) return LBM_ERR_ARG;
+  if (!out) return fail(LBM_ERR_ARG, "lbm_diagnostics: null out");
+  k_diag<<<1, 256, 0, c->stream>>>(c->partial, (int)(c->grid.x * c->grid.y), c->jnode,
+                                   c->p.ny, c->infeasible, c->nedge, c->mask, c->p.nx,
+                                   c->pitch, c->diag);
+  CK(cudaGetLastError());
+  DiagDev h;
+  long long ctr[4];
+  CK(cudaMemcpyAsync(&h, c->diag, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(ctr, c->counters, sizeof(ctr), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  out->mass = h.mass;
+  out->outlet_J = h.J;
+  out->steps = c->steps;
+  out->bc_infeasible = h.infeasible;
+  out->flips = ctr[0];
+  out->n_solid = h.n_solid;
+  return LBM_OK;
+}
+
+lbm_status lbm_state_bytes(lbm_ctx* c, size_t* bytes) {
+  if (check_ctx(c)) return LBM_ERR_ARG;
+  if (!bytes) return fail(LBM_ERR_ARG, "lbm_state_bytes: null out");
+  Section s[16];
+  const int k = state_sections(c, s);
+  size_t total = align256(sizeof(BlobHeader));
+  for (int i = 0; i < k; ++i) total += align256(s[i].bytes);
+  *bytes = total;
+  return LBM_OK;
+}
+
+lbm_status lbm_save(lbm_ctx* c, void* buf, size_t bytes) {
+  size_t need = 0;
+  lbm_status st = lbm_state_bytes(c, &need);
+  if (st != LBM_OK) return st;
+  if (!buf || bytes < need) return fail(LBM_ERR_ARG, "lbm_save: buffer smaller than lbm_state_bytes");
+  const bool dev = on_device(buf);
+  const cudaMemcpyKind k = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  BlobHeader h{kMagic, c->steps, c->p.nx, c->p.ny, c->p.precision, c->p.dissolution};
+  CK(cudaMemcpyAsync(buf, &h, sizeof(h), dev ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, c->stream));
+  Section s[16];
+  const int n = state_sections(c, s);
+  size_t off = align256(sizeof(BlobHeader));
+  for (int i = 0; i < n; ++i) {
+    CK(cudaMemcpyAsync((char*)buf + off, s[i].ptr, s[i].bytes, k, c->stream));
+    off += align256(s[i].bytes);
+  }
+  CK(cudaStreamSynchronize(c->stream));  // the header lives on this stack frame
+  return LBM_OK;
+}
+
+lbm_status lbm_restore(lbm_ctx* c, const void* buf, size_t bytes) {
+  size_t need = 0;
+  lbm_status st = lbm_state_bytes(c, &need);
+  if (st != LBM_OK) return st;
+  if (!buf || bytes < need) return fail(LBM_ERR_ARG, "lbm_restore: buffer smaller than lbm_state_bytes");
+  const bool dev = on_device(buf);
+  BlobHeader h;
+  CK(cudaMemcpyAsync(&h, buf, sizeof(h), dev ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (h.magic != kMagic || h.nx != c->p.nx || h.ny != c->p.ny ||
+      h.precision != c->p.precision || h.dissolution != c->p.dissolution)
+    return fail(LBM_ERR_STATE, "lbm_restore: blob does not belong to this lattice");
+  const cudaMemcpyKind k = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  Section s[16];
+  const int n = state_sections(c, s);
+  size_t off = align256(sizeof(BlobHeader));
+  for (int i = 0; i < n; ++i) {
+    CK(cudaMemcpyAsync(s[i].ptr, (const char*)buf + off, s[i].bytes, k, c->stream));
+    off += align256(s[i].bytes);
+  }
+  c->steps = h.steps;
+  if (!dev) CK(cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+lbm_status lbm_kernel_timing(lbm_ctx* c, int enable) {
+  if (check_ctx(c)) return LBM_ERR_ARG;
+  for (int w = 0; w < 2; ++w) {
+    lbm_status s = fold_times(c, w);
+    if (s != LBM_OK) return s;
+    c->ms_sum[w] = 0.0;
+    c->launches[w] = 0;
+  }
+  c->timing = enable != 0;
+  return LBM_OK;
+}
+
+lbm_status lbm_kernel_times_read(lbm_ctx* c, double* step_ms, long long* step_launches,
+                                 double* dissolve_ms, long long* dissolve_launches) {
+  if (check_ctx(c)) return LBM_ERR_ARG;
+  for (int w = 0; w < 2; ++w) {
+    lbm_status s = fold_times(c, w);
+    if (s != LBM_OK) return s;
+  }
+  if (step_ms) *step_ms = c->ms_sum[0];
+  if (step_launches) *step_launches = c->launches[0];
+  if (dissolve_ms) *dissolve_ms = c->ms_sum[1];
+  if (dissolve_launches) *dissolve_launches = c->launches[1];
+  return LBM_OK;
+}
+
+lbm_status lbm_set_stream(lbm_ctx* c, void* stream) {
+  if (check_ctx(c)) return LBM_ERR_ARG;
+  CK(cudaStreamSynchronize(c->stream));
+  c->stream = (cudaStream_t)stream;
+  return LBM_OK;
+}
+
+lbm_status lbm_synchronize(lbm_ctx* c) {
+  if (check_ctx(c)) return LBM_ERR_ARG;
+  CK(cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+void lbm_destroy(lbm_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  free_ctx(c);
+}
+
+}  // extern "C"

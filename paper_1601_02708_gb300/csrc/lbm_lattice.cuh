@@ -1,0 +1,121 @@
+// lbm_lattice.cuh -- D2Q9 lattice constants and the node-level pieces of the
+// step: equilibrium, maximum-entropy boundary solves.  Device code only.
+#pragma once
+#include <cstdint>
+
+namespace lbm {
+
+// D2Q9: 0 rest, 1 E, 2 N, 3 W, 4 S, 5 NE, 6 NW, 7 SW, 8 SE (Sec. 4.1, the
+// standard DnQm lattice with c_s^2 = 1/3).  constexpr functions so that the
+// fully unrolled loops fold every lookup into an immediate.
+__host__ __device__ constexpr int cx_of(int i) {
+  return (i == 1 || i == 5 || i == 8) ? 1 : (i == 3 || i == 6 || i == 7) ? -1 : 0;
+}
+__host__ __device__ constexpr int cy_of(int i) {
+  return (i == 2 || i == 5 || i == 6) ? 1 : (i == 4 || i == 7 || i == 8) ? -1 : 0;
+}
+__host__ __device__ constexpr int opp_of(int i) {
+  return i == 0 ? 0 : (i <= 4 ? ((i + 1) % 4) + 1 : ((i - 3) % 4) + 5);
+}
+__host__ __device__ constexpr double w_of(int i) {
+  return i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+}
+
+enum : uint8_t {
+  kSolid = 1,    // solid while this step streams (pull / bounce-back)
+  kPending = 2   // turns fluid before this step collides (dissolution)
+};
+
+enum { kPeriodic = 0, kDirichlet = 1, kNeumann = 2 };
+enum { kReactNone = 0, kReactSurface = 1, kReactBulk = 2 };
+
+// Solid as seen by the collision of the current step (after dissolution).
+__device__ __forceinline__ bool solid_post(uint8_t m) {
+  return (m & kSolid) && !(m & kPending);
+}
+
+// Index of edge node (x, y) of side s in the edge layout [W|E|S|N].
+__device__ __forceinline__ int edge_slot(int s, int x, int y, int nx, int ny) {
+  return s == 0 ? y : s == 1 ? ny + y : s == 2 ? 2 * ny + x : 2 * ny + nx + x;
+}
+
+// Maximum-entropy Dirichlet, Sec. 4.1.1 (a): the unknowns minimising
+// H = sum f log(f/w) under sum f = up are proportional to w.  Computed in
+// FP64.  Returns true if the data admit no non-negative solution.
+template <typename Real>
+__device__ bool maxent_dirichlet(Real (&f)[9], unsigned unknown, double up) {
+  double wu = 0.0, known = 0.0;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    if (unknown & (1u << i)) wu += w_of(i);
+    else known += (double)f[i];
+  }
+  const double rest = up - known;
+  const double scale = rest / wu;
+#pragma unroll
+  for (int i = 0; i < 9; ++i)
+    if (unknown & (1u << i)) f[i] = (Real)(w_of(i) * scale);
+  return rest < 0.0;
+}
+
+// Maximum-entropy Neumann, Sec. 4.1.1 (b), for an outward normal (sx, sy)
+// with sx, sy in {-1, 0, 1} (a side, or the corner of two Neumann sides).
+// Unknowns with e.n = 0 (corner tangents) take halfway bounce-back of the
+// node's own post-collision population fbb[opp(i)].  On a side every M^-
+// unknown has e.n = -1 and the root gives f proportional to w; at a corner
+// (n = (sx, sy)/sqrt 2) the unknowns have e.n = -1/sqrt 2 or -sqrt 2 and the
+// root condition is a quadratic in t = exp(gamma / sqrt 2), solved in closed
+// form.  Returns true if the data admit no root (R > 0; unknowns set to 0).
+template <typename Real>
+__device__ bool maxent_neumann(Real (&f)[9], unsigned unknown, int sx, int sy,
+                               double q, const Real (&fbb)[9]) {
+  const bool corner = (sx != 0) && (sy != 0);
+  const double inv_len = corner ? 0.70710678118654752440 : 1.0;
+  double R = q;
+  double w1 = 0.0, w2 = 0.0;  // weights of M^- with |e.n| = 1/sqrt2 (or 1), sqrt2
+  unsigned m1 = 0, m2 = 0;
+#pragma unroll
+  for (int i = 1; i < 9; ++i) {
+    const int d = cx_of(i) * sx + cy_of(i) * sy;
+    if (unknown & (1u << i)) {
+      if (d == 0) {
+        f[i] = fbb[opp_of(i)];
+      } else if (d == -1) {
+        m1 |= 1u << i;
+        w1 += w_of(i);
+      } else {  // d == -2 (corner diagonal)
+        m2 |= 1u << i;
+        w2 += w_of(i);
+      }
+    } else {
+      R -= (double)d * inv_len * (double)f[i];
+    }
+  }
+  const double S = -R;
+  if (!(S > 0.0)) {
+#pragma unroll
+    for (int i = 1; i < 9; ++i)
+      if ((m1 | m2) & (1u << i)) f[i] = (Real)0;
+    return S < 0.0;
+  }
+  if (!corner) {
+    const double scale = S / w1;
+#pragma unroll
+    for (int i = 1; i < 9; ++i)
+      if (m1 & (1u << i)) f[i] = (Real)(w_of(i) * scale);
+    return false;
+  }
+  // (w1 / (sqrt2 e)) t + (sqrt2 w2 / e) t^2 = S
+  const double inv_e = 0.36787944117144233;  // exp(-1)
+  const double A = w1 * 0.70710678118654752440 * inv_e;
+  const double B = w2 * 1.41421356237309504880 * inv_e;
+  const double t = 2.0 * S / (A + sqrt(A * A + 4.0 * B * S));
+#pragma unroll
+  for (int i = 1; i < 9; ++i) {
+    if (m1 & (1u << i)) f[i] = (Real)(w_of(i) * t * inv_e);
+    if (m2 & (1u << i)) f[i] = (Real)(w_of(i) * t * t * inv_e);
+  }
+  return false;
+}
+
+}  // namespace lbm

@@ -107,14 +107,22 @@ def streamfunction_velocity(nx: int, ny: int, seed: int, n_modes: int = 16,
         amp = rng.normal() / math.hypot(kx, ky)
         phase = 2.0 * math.pi * rng.uniform()
         modes.append((kx, ky, amp, phase))
-    x = np.arange(nx, dtype=np.float64)[None, :]
-    y = np.arange(ny, dtype=np.float64)[:, None]
-    vx = np.zeros((ny, nx))
-    vy = np.zeros((ny, nx))
+    # cos(a(x) + b(y)) = cos a cos b - sin a sin b: every mode is a sum of
+    # two outer products, so both components are one [ny, 2M] x [2M, nx]
+    # matrix product.
+    x = np.arange(nx, dtype=np.float64)
+    y = np.arange(ny, dtype=np.float64)
+    cols_x, rows_vx, rows_vy = [], [], []
     for kx, ky, amp, phase in modes:
-        c = amp * np.cos(2.0 * math.pi * (kx * x / nx + ky * y / ny) + phase)
-        vx += c * (2.0 * math.pi * ky / ny)
-        vy -= c * (2.0 * math.pi * kx / nx)
+        a = 2.0 * math.pi * kx * x / nx
+        b = 2.0 * math.pi * ky * y / ny + phase
+        cols_x += [np.cos(a), -np.sin(a)]
+        gy, gx = 2.0 * math.pi * ky / ny, 2.0 * math.pi * kx / nx
+        rows_vx += [amp * gy * np.cos(b), amp * gy * np.sin(b)]
+        rows_vy += [-amp * gx * np.cos(b), -amp * gx * np.sin(b)]
+    X = np.stack(cols_x)                  # [2M, nx]
+    vx = np.stack(rows_vx, axis=1) @ X    # [ny, nx]
+    vy = np.stack(rows_vy, axis=1) @ X
     speed = np.sqrt(vx * vx + vy * vy).max()
     if speed > 0:
         vx *= umax / speed

@@ -1,0 +1,254 @@
+"""Python face of liblbmade.so: one D2Q9 ADE-LBM lattice on one GPU.
+
+Argument marshalling only; every step of the method runs in the CUDA
+library.  Arrays may be numpy arrays (host) or torch tensors (host or CUDA);
+device tensors are passed to the library by pointer, host arrays are copied
+by the library.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import Diag, LBMError, Params, check
+
+PERIODIC, DIRICHLET, NEUMANN = 0, 1, 2
+REACT_NONE, REACT_SURFACE, REACT_BULK = 0, 1, 2
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _is_tensor(a):
+    try:
+        return isinstance(a, _torch().Tensor)
+    except ImportError:  # pragma: no cover
+        return False
+
+
+_NP = {"f64": np.float64, "f32": np.float32, "u8": np.uint8}
+
+
+def _in_ptr(a, kind, count, keep):
+    """Pointer to a contiguous copy of `a` (dtype `kind`, `count` elements)."""
+    if a is None:
+        return None
+    if _is_tensor(a):
+        torch = _torch()
+        td = {"f64": torch.float64, "f32": torch.float32, "u8": torch.uint8}[kind]
+        t = a.detach()
+        if t.dtype != td:
+            t = (t != 0).to(td) if kind == "u8" else t.to(td)
+        t = t.contiguous()
+        if t.numel() != count:
+            raise ValueError(f"expected {count} elements, got {t.numel()}")
+        keep.append(t)
+        return t.data_ptr()
+    arr = np.asarray(a)
+    if kind == "u8":
+        arr = (arr != 0).astype(np.uint8)
+    arr = np.ascontiguousarray(arr, dtype=_NP[kind]).reshape(-1)
+    if arr.size != count:
+        raise ValueError(f"expected {count} elements, got {arr.size}")
+    keep.append(arr)
+    return arr.ctypes.data
+
+
+def _out_ptr(out, kind, count):
+    if _is_tensor(out):
+        torch = _torch()
+        td = {"f64": torch.float64, "f32": torch.float32, "u8": torch.uint8}[kind]
+        if out.dtype != td or not out.is_contiguous() or out.numel() != count:
+            raise ValueError("output tensor has the wrong dtype, size or layout")
+        return out.data_ptr()
+    if not (isinstance(out, np.ndarray) and out.dtype == _NP[kind]
+            and out.flags["C_CONTIGUOUS"] and out.size == count):
+        raise ValueError("output array has the wrong dtype, size or layout")
+    return out.ctypes.data
+
+
+def current_stream_handle():
+    """cudaStream_t of torch's current stream (None without CUDA)."""
+    torch = _torch()
+    if not torch.cuda.is_available():
+        return None
+    return torch.cuda.current_stream().cuda_stream
+
+
+class LBM:
+    """A D2Q9 lattice for the advection-diffusion(-reaction) equation.
+
+    Parameters follow the problem statement of the pore-scale subdomain
+    (Sec. 6, Eq. "CouplingPDE"): lattice size, relaxation time ``tau``
+    (D = (tau - 1/2) / 3 in lattice units), side kinds ``edges`` for W, E, S, N
+    (PERIODIC, DIRICHLET or NEUMANN), solid mask, advection velocity
+    [2, ny, nx], initial concentration, and the first-order reaction
+    (``react_mode``, ``k`` or ``k_field``, ``dissolution``, ``mineral``).
+    ``precision`` 32 runs FP32 populations with FP64 boundary solves and
+    sums; 64 runs FP64 throughout.
+    """
+
+    def __init__(self, nx, ny, tau, edges=(PERIODIC,) * 4, precision=32,
+                 solid=None, vel=None, u0=None, react_mode=REACT_NONE, k=0.0,
+                 k_field=None, dissolution=False, mineral=None, stream=None):
+        self._lib = _lib.load()
+        self.nx, self.ny = int(nx), int(ny)
+        self.precision = int(precision)
+        p = Params()
+        p.nx, p.ny, p.precision = self.nx, self.ny, self.precision
+        for i, e in enumerate(edges):
+            p.edge[i] = int(e)
+        p.tau = float(tau)
+        p.react_mode = int(react_mode)
+        p.k_scalar = float(k)
+        p.dissolution = int(bool(dissolution))
+        self.params = p
+        self.edges = tuple(int(e) for e in edges)
+        N = self.nx * self.ny
+        keep = []
+        args = (_in_ptr(solid, "u8", N, keep), _in_ptr(vel, "f64", 2 * N, keep),
+                _in_ptr(k_field, "f64", N, keep), _in_ptr(mineral, "f64", N, keep),
+                _in_ptr(u0, "f64", N, keep))
+        if stream is None:
+            stream = current_stream_handle()
+        self._stream = stream
+        h = ctypes.c_void_p()
+        check(self._lib.lbm_init(ctypes.byref(h), ctypes.byref(p), *args, stream))
+        self._h = h
+
+    # -- lifetime --------------------------------------------------------------
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._lib.lbm_destroy(h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise LBMError(-4, "context is closed")
+        return self._h
+
+    @property
+    def n_edge(self):
+        return 2 * (self.nx + self.ny)
+
+    # -- stepping --------------------------------------------------------------
+    def substeps(self, n, eta=1, u_dir_t0=None, u_dir_t1=None, q_neu=None):
+        """Advance n steps (substeps j = 1..n of ratio eta); edge arrays in
+        the layout [W: ny][E: ny][S: nx][N: nx]."""
+        keep = []
+        m = self.n_edge
+        a = _in_ptr(u_dir_t0, "f64", m, keep)
+        b = _in_ptr(u_dir_t1, "f64", m, keep)
+        q = _in_ptr(q_neu, "f64", m, keep)
+        check(self._lib.lbm_substeps(self.handle, int(n), int(eta), a, b, q))
+        self._keep = keep  # device inputs stay referenced until the next call
+
+    def kernel_timing(self, enable=True):
+        """Record CUDA events around every step and dissolution launch."""
+        check(self._lib.lbm_kernel_timing(self.handle, int(bool(enable))))
+
+    def kernel_times(self):
+        """(step_ms_total, step_launches, dissolve_ms_total, dissolve_launches)."""
+        a, c = ctypes.c_double(), ctypes.c_double()
+        b, d = ctypes.c_longlong(), ctypes.c_longlong()
+        check(self._lib.lbm_kernel_times_read(self.handle, ctypes.byref(a), ctypes.byref(b),
+                                              ctypes.byref(c), ctypes.byref(d)))
+        return a.value, b.value, c.value, d.value
+
+    def synchronize(self):
+        check(self._lib.lbm_synchronize(self.handle))
+
+    # -- read-out --------------------------------------------------------------
+    def concentration(self, out=None, precision=64):
+        """u = sum_i f_i at the current time, [ny, nx] (numpy unless `out`
+        is given)."""
+        kind = "f64" if precision == 64 else "f32"
+        if out is None:
+            out = np.empty((self.ny, self.nx), dtype=_NP[kind])
+        check(self._lib.lbm_get_concentration(
+            self.handle, _out_ptr(out, kind, self.nx * self.ny), int(precision)))
+        return out
+
+    def populations(self, out=None):
+        """Stored post-collision populations [9, ny, nx] (FP64)."""
+        if out is None:
+            out = np.empty((9, self.ny, self.nx))
+        check(self._lib.lbm_get_populations(self.handle, _out_ptr(out, "f64", 9 * self.nx * self.ny)))
+        return out
+
+    def solid(self, out=None):
+        if out is None:
+            out = np.empty((self.ny, self.nx), dtype=np.uint8)
+        check(self._lib.lbm_get_solid(self.handle, _out_ptr(out, "u8", self.nx * self.ny)))
+        return out
+
+    def mineral(self, out=None):
+        if out is None:
+            out = np.empty((self.ny, self.nx))
+        check(self._lib.lbm_get_mineral(self.handle, _out_ptr(out, "f64", self.nx * self.ny)))
+        return out
+
+    def diagnostics(self):
+        d = Diag()
+        check(self._lib.lbm_diagnostics(self.handle, ctypes.byref(d)))
+        return {k: getattr(d, k) for k, _ in Diag._fields_}
+
+    def trace(self, xy, out=None):
+        """LBM -> FEM transfer (Sec. 6.2 (ii)) at points xy [npts, 2] in
+        lattice coordinates."""
+        keep = []
+        if _is_tensor(xy):
+            npts = xy.numel() // 2
+        else:
+            xy = np.asarray(xy, dtype=np.float64).reshape(-1, 2)
+            npts = xy.shape[0]
+        ptr = _in_ptr(xy, "f64", 2 * npts, keep)
+        if out is None:
+            out = np.empty(npts)
+        check(self._lib.lbm_interface_trace(self.handle, int(npts), ptr,
+                                            _out_ptr(out, "f64", npts)))
+        return out
+
+    # -- Schwarz rollback ------------------------------------------------------
+    def state_bytes(self):
+        n = ctypes.c_size_t()
+        check(self._lib.lbm_state_bytes(self.handle, ctypes.byref(n)))
+        return n.value
+
+    def save(self, buf=None):
+        """Save the full state into `buf` (a uint8 torch tensor, CUDA or
+        host, or a numpy array) allocated here if not given."""
+        nb = self.state_bytes()
+        if buf is None:
+            torch = _torch()
+            buf = torch.empty(nb, dtype=torch.uint8,
+                              device="cuda" if torch.cuda.is_available() else "cpu")
+        check(self._lib.lbm_save(self.handle, _out_ptr(buf, "u8", buf.numel() if _is_tensor(buf) else buf.size), nb))
+        return buf
+
+    def restore(self, buf):
+        nb = buf.numel() if _is_tensor(buf) else buf.size
+        ptr = buf.data_ptr() if _is_tensor(buf) else buf.ctypes.data
+        check(self._lib.lbm_restore(self.handle, ptr, nb))
+
+
+__all__ = ["LBM", "LBMError", "PERIODIC", "DIRICHLET", "NEUMANN",
+           "REACT_NONE", "REACT_SURFACE", "REACT_BULK"]

@@ -1,0 +1,54 @@
+"""The C-ABI library builds, loads without a GPU and exports every entry
+point declared in include/lbm_ade.h (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", h)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(lbm_\w+)\s*\(", text))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1601_02708_gb300 import build
+    return ctypes.CDLL(build.build())
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("lbm_init", "lbm_substeps", "lbm_interface_trace"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in sorted(_declared()) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_abi_version(lib):
+    lib.lbm_abi_version.restype = ctypes.c_int
+    text = open(os.path.join(ROOT, "include", "lbm_ade.h")).read()
+    want = int(re.search(r"#define LBM_ADE_ABI_VERSION (\d+)", text).group(1))
+    assert lib.lbm_abi_version() == want
+
+
+def test_product_path_has_no_oracle_dependency():
+    """The package never imports or loads the oracle."""
+    pkg = os.path.join(ROOT, "paper_1601_02708_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in text and "from oracle" not in text, f
+                assert "lbm_oracle" not in text, f

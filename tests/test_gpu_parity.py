@@ -1,0 +1,325 @@
+"""CUDA path (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerances: FP64 mode 1e-12 relative to max|u| (rounding-order differences
+only); FP32 mode 1e-5 relative to max|u| (the stated FP32 bound).  The
+integer solid mask is compared bit for bit.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1601_02708_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = {64: 1e-12, 32: 1e-5}
+
+
+@pytest.fixture(scope="module")
+def gb():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1601_02708_gb300 import build
+    build.build()
+    import paper_1601_02708_gb300 as pkg
+    return pkg
+
+
+def _relerr(a, b):
+    scale = max(np.abs(b).max(), 1e-300)
+    return np.abs(a - b).max() / scale
+
+
+def _porous(nx, ny, seed, k=0.05, mineral=0.03, porosity=0.6, rmin=3, rmax=7):
+    solid = inputs.disk_packing(nx, ny, porosity, seed, rmin=rmin, rmax=rmax)
+    vel = inputs.streamfunction_velocity(nx, ny, seed + 1, solid=solid)
+    return dict(edges=(1, 2, 0, 0), solid=solid, vel=vel, u0=np.zeros((ny, nx)),
+                react_mode=1, k=k, dissolution=True,
+                mineral=np.full((ny, nx), mineral))
+
+
+def _compare_state(lat, ref, ref_next_mineral, prec, fpost=True):
+    u, u_ref = lat.concentration(), ref.u()
+    assert _relerr(u, u_ref) <= TOL[prec]
+    assert np.array_equal(lat.solid(), ref.solid())
+    if fpost:
+        assert _relerr(lat.populations(), ref.fpost()) <= TOL[prec]
+    if ref_next_mineral is not None:
+        m = lat.mineral()
+        solid = ref.solid() != 0
+        assert _relerr(m[solid], ref_next_mineral[solid]) <= (1e-12 if prec == 64 else 1e-5)
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_periodic_reactive_fourier_lattice(gb, oracle_mod, prec):
+    """Periodic lattice with uniform velocity and bulk sink: the path with no
+    boundaries and no solids."""
+    nx, ny, steps = 67, 29, 80
+    X, Y = np.meshgrid(np.arange(nx), np.arange(ny))
+    u0 = 1.0 + 0.5 * np.cos(2 * math.pi * (3 * X / nx + Y / ny))
+    vel = np.stack([np.full((ny, nx), 0.03), np.full((ny, nx), -0.02)])
+    kw = dict(vel=vel, u0=u0, react_mode=2, k=2e-3)
+    ref = oracle_mod.LBMOracle(nx, ny, 0.73, **kw)
+    ref.substeps(steps)
+    lat = gb.LBM(nx, ny, 0.73, precision=prec, **kw)
+    lat.substeps(steps)
+    _compare_state(lat, ref, None, prec)
+    d = lat.diagnostics()
+    assert abs(d["mass"] - ref.diag()["mass"]) <= TOL[prec] * ref.diag()["mass"]
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("shape", [(97, 61), (33, 9), (128, 64)])
+def test_porous_dissolution_parity(gb, oracle_mod, prec, shape):
+    """Disks, stream-function velocity, surface reaction with dissolution
+    (mineral small enough that nodes flip), Dirichlet inlet, Neumann outlet,
+    periodic y; ragged shapes that leave partial tiles."""
+    nx, ny = shape
+    steps = 150
+    kw = _porous(nx, ny, seed=nx * 7 + ny)
+    ud = inputs.edge_array(nx, ny, W=1.0)
+    q = inputs.edge_array(nx, ny)
+    ref = oracle_mod.LBMOracle(nx, ny, 0.7, **kw)
+    ref.substeps(steps, 1, ud, ud, q)
+    lat = gb.LBM(nx, ny, 0.7, precision=prec, **kw)
+    lat.substeps(steps, 1, ud, ud, q)
+    d_ref = ref.diag()
+    u_ref, solid_ref, fpost_ref = ref.u(), ref.solid(), ref.fpost()
+    ref.substeps(1, 1, ud, ud, q)           # mineral one reaction step ahead
+    m_next = ref.mineral()
+    u = lat.concentration()
+    assert _relerr(u, u_ref) <= TOL[prec]
+    assert np.array_equal(lat.solid(), solid_ref)
+    assert _relerr(lat.populations(), fpost_ref) <= TOL[prec]
+    s = solid_ref != 0
+    mtol = 1e-12 if prec == 64 else 1e-5
+    if s.any():
+        assert np.abs(lat.mineral()[s] - m_next[s]).max() <= mtol
+    d = lat.diagnostics()
+    assert d["steps"] == steps
+    assert abs(d["outlet_J"] - d_ref["J"]) <= TOL[prec] * max(1.0, d_ref["J"])
+    assert abs(d["mass"] - d_ref["mass"]) <= TOL[prec] * d_ref["mass"]
+    if prec == 64:
+        # FP32 rounds the outlet's ~1e-50 populations to zero, so the count of
+        # infeasible Neumann solves (R > 0 by a hair) is only comparable in FP64
+        assert d["bc_infeasible"] == d_ref["bc_infeasible"]
+    assert d["flips"] == ref.diag()["flips"]  # flips decided one step ahead
+    if shape == (97, 61):
+        assert d["flips"] > 0
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_e1_worked_example(gb, oracle_mod, prec):
+    """Sec. 4.1.2 on the GPU: Neumann on x = 0, Dirichlet 0 elsewhere
+    (Dirichlet wins at the corners), matches the oracle and the table bound."""
+    D = 4.0 / (5.0 * math.pi ** 2)
+    h = 0.02
+    n = int(round(1 / h)) + 1
+    dt = h * h / (6 * D)
+    steps = int(round(0.25 / dt))
+    x = np.arange(n) * h
+    X, Y = np.meshgrid(x, x)
+    u0 = np.sin(math.pi * Y) * np.cos(math.pi * X / 2)
+    ref = oracle_mod.LBMOracle(n, n, 1.0, edges=(2, 1, 1, 1), u0=u0)
+    ref.substeps(steps)
+    lat = gb.LBM(n, n, 1.0, edges=(2, 1, 1, 1), precision=prec, u0=u0)
+    lat.substeps(steps)
+    u = lat.concentration()
+    assert _relerr(u, ref.u()) <= TOL[prec]
+    assert np.abs(u - math.exp(-steps * dt) * u0).max() <= 6.2e-4
+    assert lat.diagnostics()["bc_infeasible"] == ref.diag()["bc_infeasible"]
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_zero_flux_box_neumann_corners(gb, oracle_mod, prec):
+    """Sec. 4.1.3 box: max-entropy Neumann on all four sides, so the corners
+    take the diagonal-normal solution (closed-form quadratic on the GPU,
+    Newton in the oracle)."""
+    n = 41
+    X, Y = np.meshgrid(np.linspace(0, 1, n), np.linspace(0, 1, n))
+    u0 = ((X >= 0.4) & (X <= 0.6) & (Y >= 0.4) & (Y <= 0.6)).astype(float)
+    u0 += 0.1 * X * Y  # mass at the corners, so the corner solves matter
+    ref = oracle_mod.LBMOracle(n, n, 1.0, edges=(2, 2, 2, 2), u0=u0)
+    ref.substeps(200)
+    lat = gb.LBM(n, n, 1.0, edges=(2, 2, 2, 2), precision=prec, u0=u0)
+    lat.substeps(200)
+    _compare_state(lat, ref, None, prec)
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_multi_time_step_interpolation(gb, oracle_mod, prec):
+    """Eq. "MTS": Dirichlet data interpolated between two coarse levels over
+    eta substeps, on all four sides (Dirichlet corners), in several calls."""
+    nx, ny, eta = 45, 38, 7
+    rng = np.random.default_rng(0)
+    u0 = rng.uniform(0, 1, (ny, nx))
+    vel = np.stack([np.full((ny, nx), 0.02), np.full((ny, nx), 0.01)])
+    ref = oracle_mod.LBMOracle(nx, ny, 0.9, edges=(1, 1, 1, 1), vel=vel, u0=u0)
+    lat = gb.LBM(nx, ny, 0.9, edges=(1, 1, 1, 1), precision=prec, vel=vel, u0=u0)
+    a = rng.uniform(0, 2, 2 * (nx + ny))
+    for _ in range(3):
+        b = rng.uniform(0, 2, 2 * (nx + ny))
+        ref.substeps(eta, eta, a, b)
+        lat.substeps(eta, eta, a, b)
+        a = b
+    _compare_state(lat, ref, None, prec)
+    assert lat.diagnostics()["bc_infeasible"] == ref.diag()["bc_infeasible"]
+
+
+def test_neumann_flux_and_interface_trace(gb, oracle_mod):
+    """Nonzero Neumann data on N and S, Dirichlet on W/E, then the bilinear
+    LBM -> FEM trace at random points (Sec. 6.2 (ii))."""
+    nx, ny = 50, 36
+    rng = np.random.default_rng(1)
+    u0 = rng.uniform(0.5, 1.5, (ny, nx))
+    q = inputs.edge_array(nx, ny, S=rng.uniform(-0.01, 0.0, nx), N=-0.005)
+    ud = inputs.edge_array(nx, ny, W=1.2, E=0.8)
+    ref = oracle_mod.LBMOracle(nx, ny, 0.8, edges=(1, 1, 2, 2), u0=u0)
+    ref.substeps(90, 1, ud, ud, q)
+    lat = gb.LBM(nx, ny, 0.8, edges=(1, 1, 2, 2), precision=64, u0=u0)
+    lat.substeps(90, 1, ud, ud, q)
+    _compare_state(lat, ref, None, 64)
+    pts = np.stack([rng.uniform(0, nx - 1, 200), rng.uniform(0, ny - 1, 200)], 1)
+    pts[0] = (nx - 1, ny - 1)
+    pts[1] = (0, 0)
+    np.testing.assert_allclose(lat.trace(pts), ref.trace(pts), rtol=0, atol=1e-12)
+    bad = lat.trace(np.array([[-0.5, 3.0], [3.0, ny]]))
+    assert np.isnan(bad).all()
+
+
+def test_save_restore_is_exact(gb):
+    """Schwarz rollback: restoring a saved state and re-running reproduces
+    the first run bit for bit (device and host blobs)."""
+    import torch
+    nx, ny = 80, 48
+    kw = _porous(nx, ny, seed=3)
+    ud = inputs.edge_array(nx, ny, W=1.0)
+    lat = gb.LBM(nx, ny, 0.7, precision=32, **kw)
+    lat.substeps(20, 1, ud, ud)
+    blob = lat.save()
+    host = np.empty(lat.state_bytes(), dtype=np.uint8)
+    lat.save(host)
+    lat.substeps(30, 1, ud, ud)
+    u1, m1, d1 = lat.concentration(), lat.mineral(), lat.diagnostics()
+    for b in (blob, host):
+        lat.restore(b)
+        lat.substeps(30, 1, ud, ud)
+        assert np.array_equal(lat.concentration(), u1)
+        assert np.array_equal(lat.mineral(), m1)
+        assert lat.diagnostics() == d1
+    assert isinstance(blob, torch.Tensor) and blob.is_cuda
+
+
+def test_device_pointers_and_determinism(gb):
+    """Inputs as CUDA tensors give the same state as host arrays, and two
+    runs are bit-identical (no atomics in any sum)."""
+    import torch
+    nx, ny = 64, 40
+    kw = _porous(nx, ny, seed=9)
+    ud = inputs.edge_array(nx, ny, W=1.0)
+    a = gb.LBM(nx, ny, 0.7, precision=32, **kw)
+    dev = {k: (torch.from_numpy(np.asarray(v)).cuda() if isinstance(v, np.ndarray) else v)
+           for k, v in kw.items()}
+    b = gb.LBM(nx, ny, 0.7, precision=32, **dev)
+    a.substeps(40, 1, ud, ud)
+    b.substeps(40, 1, torch.from_numpy(ud).cuda(), None)
+    out = torch.empty((ny, nx), dtype=torch.float32, device="cuda")
+    b.concentration(out, precision=32)
+    torch.cuda.synchronize()
+    assert np.array_equal(a.concentration(precision=32), out.cpu().numpy())
+    assert a.diagnostics() == b.diagnostics()
+
+
+def test_edge_cases(gb, oracle_mod):
+    """Degenerate inputs: zero steps, an all-solid lattice, the smallest
+    lattice, and argument errors reported as status codes."""
+    lat = gb.LBM(2, 2, 0.8, edges=(1, 2, 1, 2), precision=64, u0=np.ones((2, 2)))
+    u_before = lat.concentration()
+    lat.substeps(0)
+    assert np.array_equal(lat.concentration(), u_before)
+    ref = oracle_mod.LBMOracle(2, 2, 0.8, edges=(1, 2, 1, 2), u0=np.ones((2, 2)))
+    ud = np.full(8, 0.3)
+    ref.substeps(5, 1, ud, ud)
+    lat.substeps(5, 1, ud, ud)
+    assert _relerr(lat.concentration(), ref.u()) <= 1e-12
+    full = gb.LBM(16, 8, 0.8, precision=32, solid=np.ones((8, 16)), u0=np.ones((8, 16)))
+    full.substeps(3)
+    assert np.all(full.concentration() == 0)
+    assert full.diagnostics()["n_solid"] == 128
+    with pytest.raises(gb.LBMError):
+        gb.LBM(8, 8, 0.5)
+    with pytest.raises(gb.LBMError):
+        gb.LBM(8, 8, 0.8, edges=(0, 1, 0, 0))
+    with pytest.raises(gb.LBMError):
+        gb.LBM(8, 8, 0.8, react_mode=2, dissolution=True)
+    with pytest.raises(gb.LBMError):
+        gb.LBM(1, 8, 0.8)
+    with pytest.raises(gb.LBMError):
+        lat.substeps(-1)
+
+
+def test_full_size_lattice_sampled_parity(gb, oracle_mod):
+    """The 4096 x 4096 porous workload (porosity 0.6, disks r 8-24, 16-mode
+    stream function, tau 0.7, k 1e-3 with dissolution), FP32, in the launch
+    configuration the benchmark times: the whole field, mask and mineral
+    after a few steps against the oracle."""
+    n = 4096
+    case = inputs.porous_case(n, n, seed=2)
+    kw = {k: case[k] for k in ("edges", "solid", "vel", "u0", "react_mode", "k",
+                               "dissolution", "mineral")}
+    ud, q = case["u_dir"], case["q_neu"]
+    steps = 4
+    ref = oracle_mod.LBMOracle(n, n, case["tau"], **kw)
+    ref.substeps(steps, 1, ud, ud, q)
+    lat = gb.LBM(n, n, case["tau"], precision=32, **kw)
+    lat.substeps(steps, 1, ud, ud, q)
+    assert _relerr(lat.concentration(), ref.u()) <= 1e-5
+    assert np.array_equal(lat.solid(), ref.solid())
+    d, d_ref = lat.diagnostics(), ref.diag()
+    assert abs(d["mass"] - d_ref["mass"]) <= 1e-6 * d_ref["mass"]
+    assert abs(d["outlet_J"] - d_ref["J"]) <= 1e-6 * max(d_ref["J"], 1.0)
+
+
+def test_full_size_fp32_against_fp64_mode(gb):
+    """At 4096 x 4096 the oracle cannot run thousands of steps inside a test;
+    FP64 mode of the same kernels (pinned to the oracle at 1e-12 above)
+    stands in for it: transport without dissolution, FP32 within 1e-5 of
+    FP64 after 2,000 steps."""
+    n = 4096
+    case = inputs.porous_case(n, n, seed=2)
+    kw = {k: case[k] for k in ("edges", "solid", "vel", "u0", "react_mode", "k",
+                               "mineral")}
+    ud, q = case["u_dir"], case["q_neu"]
+    a = gb.LBM(n, n, case["tau"], precision=32, **kw)
+    b = gb.LBM(n, n, case["tau"], precision=64, **kw)
+    a.substeps(2000, 1, ud, ud, q)
+    b.substeps(2000, 1, ud, ud, q)
+    assert _relerr(a.concentration(), b.concentration()) <= 1e-5
+
+
+@pytest.mark.parametrize("dissolution", [False, True])
+def test_fp32_bound_over_ten_thousand_steps(gb, oracle_mod, dissolution):
+    """The FP32 bound after the 10,000-step run length of the large workload,
+    on a 128 x 128 lattice of the same generator that the oracle can finish:
+    max|u32 - u_oracle| <= 1e-5 max|u|; with dissolution (over a thousand
+    flips) the FP32 mask also matches the oracle's, and FP64 mode matches to
+    1e-12 with an identical mask."""
+    n, steps = 128, 10000
+    case = inputs.porous_case(n, n, seed=2)
+    case["solid"] = inputs.disk_packing(n, n, 0.6, 2, rmin=3, rmax=8)
+    case["vel"] = inputs.streamfunction_velocity(n, n, 3, solid=case["solid"])
+    kw = {k: case[k] for k in ("edges", "solid", "vel", "u0", "react_mode", "k",
+                               "mineral")}
+    kw["dissolution"] = dissolution
+    ud, q = case["u_dir"], case["q_neu"]
+    ref = oracle_mod.LBMOracle(n, n, case["tau"], **kw)
+    ref.substeps(steps, 1, ud, ud, q)
+    for prec in (32, 64):
+        lat = gb.LBM(n, n, case["tau"], precision=prec, **kw)
+        lat.substeps(steps, 1, ud, ud, q)
+        assert _relerr(lat.concentration(), ref.u()) <= TOL[prec]
+        assert np.array_equal(lat.solid(), ref.solid())
+    if dissolution:
+        assert ref.diag()["flips"] > 1000
