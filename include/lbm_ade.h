@@ -50,7 +50,9 @@ typedef enum {
   LBM_ERR_ARG = -1,     /* invalid argument (size, tau <= 1/2, edge kinds, NULL) */
   LBM_ERR_CUDA = -2,    /* a CUDA call failed; the message names it */
   LBM_ERR_NOMEM = -3,   /* device allocation failed */
-  LBM_ERR_STATE = -4    /* context misuse (e.g. restore from a foreign blob) */
+  LBM_ERR_STATE = -4,   /* context misuse (e.g. restore from a foreign blob) */
+  LBM_ERR_TIMEOUT = -5  /* a kernel's bounded wait expired; the context's
+                           results since the last good call are invalid */
 } lbm_status;
 
 typedef enum {

@@ -12,7 +12,8 @@ _lib = None
 
 LBM_OK = 0
 STATUS_NAMES = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_CUDA",
-                -3: "LBM_ERR_NOMEM", -4: "LBM_ERR_STATE"}
+                -3: "LBM_ERR_NOMEM", -4: "LBM_ERR_STATE",
+                -5: "LBM_ERR_TIMEOUT"}
 
 
 class LBMError(RuntimeError):

@@ -1,9 +1,12 @@
 // lbm_api.cu -- C ABI of liblbmade.so (declared in include/lbm_ade.h).
 //
 // Owns the device state of one lattice and launches the kernels of
-// lbm_kernels.cuh on the context's stream.  Host-side work is argument
-// checking, residency detection of caller pointers and launch bookkeeping.
+// lbm_kernels.cuh / lbm_tma.cuh on the context's stream.  Host-side work is
+// argument checking, residency detection of caller pointers, layout
+// conversion and launch bookkeeping.
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <climits>
 #include <cmath>
@@ -14,6 +17,7 @@
 
 #include "lbm_ade.h"
 #include "lbm_kernels.cuh"
+#include "lbm_tma.cuh"
 
 namespace {
 
@@ -37,6 +41,12 @@ lbm_status fail(lbm_status s, const char* fmt, ...) {
                   __FILE__, __LINE__);                                        \
   } while (0)
 
+#define TRY(...)                       \
+  do {                                 \
+    lbm_status s_ = (__VA_ARGS__);     \
+    if (s_ != LBM_OK) return s_;       \
+  } while (0)
+
 bool on_device(const void* p) {
   if (!p) return false;
   cudaPointerAttributes at;
@@ -51,73 +61,102 @@ cudaMemcpyKind kind_from(const void* p) {
   return on_device(p) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
 }
 
-// ---- small element-wise kernels: layout conversion only -------------------
+using lbm::kXO;
+using lbm::kYO;
+
+// ---- layout conversion kernels (interior [ny][nx] <-> padded) -------------
 template <typename T>
-__global__ void k_pitch_in(const double* __restrict__ src, T* __restrict__ dst,
-                           int nx, int ny, int pitch, int planes, double fill) {
+__global__ void k_pitch_in(const double* __restrict__ src, T* __restrict__ dst, int nx,
+                           int ny, int pitch, int planes, double fill) {
   const long long total = (long long)nx * ny * planes;
+  const long long plane = (long long)pitch * lbm::padded_rows(ny);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     const long long p = i / ((long long)nx * ny), r = i % ((long long)nx * ny);
     const long long y = r / nx, x = r % nx;
-    dst[(p * ny + y) * pitch + x] = (T)(src ? src[i] : fill);
+    dst[p * plane + (y + kYO) * pitch + (x + kXO)] = (T)(src ? src[i] : fill);
   }
 }
 
-__global__ void k_mask_in(const uint8_t* __restrict__ src, uint8_t* __restrict__ dst,
-                          int nx, int ny, int pitch) {
+// Link word of every interior node (see lbm_lattice.cuh) from the caller's
+// solid array; periodic sides wrap, other sides are outside.
+__global__ void k_link_in(const uint8_t* __restrict__ src, uint32_t* __restrict__ link, int nx,
+                          int ny, int pitch, int per_x, int per_y) {
   const long long total = (long long)nx * ny;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-       i += (long long)gridDim.x * blockDim.x) {
-    const long long y = i / nx, x = i % nx;
-    dst[y * pitch + x] = (src && src[i]) ? lbm::kSolid : 0;
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+       id += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(id % nx), y = (int)(id / nx);
+    uint32_t w = (src && src[id]) ? lbm::kOwnSolid : 0u;
+    for (int i = 1; i < 9; ++i) {
+      int sx = x - lbm::cx_of(i), sy = y - lbm::cy_of(i);
+      bool out = false;
+      if (sx < 0 || sx >= nx) {
+        if (per_x) sx = (sx + nx) % nx; else out = true;
+      }
+      if (sy < 0 || sy >= ny) {
+        if (per_y) sy = (sy + ny) % ny; else out = true;
+      }
+      if (out) w |= lbm::up_bit(lbm::kUpOutShift, i);
+      else if (src && src[(long long)sy * nx + sx])
+        w |= lbm::up_bit(lbm::kUpSolidShift, i) | lbm::up_bit(lbm::kUpPostShift, i);
+    }
+    link[(long long)(y + kYO) * pitch + (x + kXO)] = w;
   }
 }
 
 template <typename T, typename O>
-__global__ void k_pitch_out(const T* __restrict__ src, O* __restrict__ dst, int nx,
-                            int ny, int pitch, int planes) {
+__global__ void k_pitch_out(const T* __restrict__ src, O* __restrict__ dst, int nx, int ny,
+                            int pitch, int planes) {
   const long long total = (long long)nx * ny * planes;
+  const long long plane = (long long)pitch * lbm::padded_rows(ny);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     const long long p = i / ((long long)nx * ny), r = i % ((long long)nx * ny);
     const long long y = r / nx, x = r % nx;
-    dst[i] = (O)src[(p * ny + y) * pitch + x];
+    dst[i] = (O)src[p * plane + (y + kYO) * pitch + (x + kXO)];
   }
 }
 
-__global__ void k_solid_out(const uint8_t* __restrict__ mask, uint8_t* __restrict__ dst,
+__global__ void k_solid_out(const uint32_t* __restrict__ link, uint8_t* __restrict__ dst,
                             int nx, int ny, int pitch) {
   const long long total = (long long)nx * ny;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     const long long y = i / nx, x = i % nx;
-    dst[i] = (mask[y * pitch + x] & lbm::kSolid) ? 1 : 0;
+    dst[i] = (link[(y + kYO) * pitch + (x + kXO)] & lbm::kOwnSolid) ? 1 : 0;
   }
+}
+
+// Solid-node count (integer sums in any order give the same result).
+__global__ void k_count_solid(const uint32_t* __restrict__ link, int nx, int ny, int pitch,
+                              unsigned long long* out) {
+  unsigned long long c = 0;
+  const long long total = (long long)nx * ny;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long y = i / nx, x = i % nx;
+    c += (link[(y + kYO) * pitch + (x + kXO)] & lbm::kOwnSolid) ? 1 : 0;
+  }
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
 }
 
 // Fixed-order FP64 reductions for lbm_diagnostics (one block).
 struct DiagDev {
   double mass, J;
-  long long infeasible, n_solid;
+  long long infeasible;
 };
 __global__ void k_diag(const double* __restrict__ partial, int nparts,
                        const double* __restrict__ jnode, int ny,
-                       const long long* __restrict__ infeas, int nedge,
-                       const uint8_t* __restrict__ mask, int nx, int pitch,
-                       DiagDev* out) {
+                       const long long* __restrict__ infeas, int nedge, DiagDev* out) {
   __shared__ double sd[256];
   __shared__ long long sl[256];
   const int t = threadIdx.x;
   double m = 0.0, j = 0.0;
-  long long c = 0, ns = 0;
+  long long c = 0;
   for (int i = t; i < nparts; i += blockDim.x) m += partial[i];
   for (int i = t; i < ny; i += blockDim.x) j += jnode[i];
   for (int i = t; i < nedge; i += blockDim.x) c += infeas[i];
-  for (long long i = t; i < (long long)nx * ny; i += blockDim.x) {
-    const long long y = i / nx, x = i % nx;
-    ns += (mask[y * pitch + x] & lbm::kSolid) ? 1 : 0;
-  }
   double* outs[2] = {&out->mass, &out->J};
   double vals[2] = {m, j};
   for (int k = 0; k < 2; ++k) {
@@ -130,32 +169,27 @@ __global__ void k_diag(const double* __restrict__ partial, int nparts,
     }
     __syncthreads();
   }
-  long long* louts[2] = {&out->infeasible, &out->n_solid};
-  long long lv[2] = {c, ns};
-  for (int k = 0; k < 2; ++k) {
-    sl[t] = lv[k];
-    __syncthreads();
-    if (t == 0) {
-      long long s = 0;
-      for (int i = 0; i < (int)blockDim.x; ++i) s += sl[i];
-      *louts[k] = s;
-    }
-    __syncthreads();
+  sl[t] = c;
+  __syncthreads();
+  if (t == 0) {
+    long long s = 0;
+    for (int i = 0; i < (int)blockDim.x; ++i) s += sl[i];
+    out->infeasible = s;
   }
 }
 
 // LBM -> FEM transfer (Sec. 6.2 (ii)): bilinear patch of the four nodes
 // around each point.
 template <typename Real>
-__global__ void k_trace(const Real* __restrict__ u, int nx, int ny, int pitch,
-                        int per_x, int per_y, const double* __restrict__ xy,
-                        int npts, double* __restrict__ out) {
+__global__ void k_trace(const Real* __restrict__ u, int nx, int ny, int pitch, int per_x,
+                        int per_y, const double* __restrict__ xy, int npts,
+                        double* __restrict__ out) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= npts) return;
   const double px = xy[2 * k], py = xy[2 * k + 1];
-  const bool bad = (!per_x && !(px >= 0.0 && px <= nx - 1)) ||
-                   (!per_y && !(py >= 0.0 && py <= ny - 1)) || !isfinite(px) ||
-                   !isfinite(py);
+  const bool bad = !isfinite(px) || !isfinite(py) ||
+                   (!per_x && !(px >= 0.0 && px <= nx - 1)) ||
+                   (!per_y && !(py >= 0.0 && py <= ny - 1));
   if (bad) {
     out[k] = nan("");
     return;
@@ -167,12 +201,11 @@ __global__ void k_trace(const Real* __restrict__ u, int nx, int ny, int pitch,
   int ax = x1, ay = y1, bx = x1 + 1, by = y1 + 1;
   if (per_x) { ax = ((ax % nx) + nx) % nx; bx = ((bx % nx) + nx) % nx; }
   if (per_y) { ay = ((ay % ny) + ny) % ny; by = ((by % ny) + ny) % ny; }
-  const double u1 = (double)u[(long long)ay * pitch + ax];
-  const double u2 = (double)u[(long long)ay * pitch + bx];
-  const double u3 = (double)u[(long long)by * pitch + bx];
-  const double u4 = (double)u[(long long)by * pitch + ax];
-  out[k] = u1 * (1 - gx) * (1 - gy) + u2 * gx * (1 - gy) + u3 * gx * gy +
-           u4 * (1 - gx) * gy;
+  auto U = [&](int xx, int yy) {
+    return (double)u[(long long)(yy + kYO) * pitch + (xx + kXO)];
+  };
+  out[k] = U(ax, ay) * (1 - gx) * (1 - gy) + U(bx, ay) * gx * (1 - gy) +
+           U(bx, by) * gx * gy + U(ax, by) * (1 - gx) * gy;
 }
 
 int grid1d(long long n) {
@@ -182,36 +215,58 @@ int grid1d(long long n) {
   return (int)b;
 }
 
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                         cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
 }  // namespace
 
 struct lbm_ctx {
   lbm_params p;
   int pitch = 0;
-  long long plane = 0;
+  long long plane = 0;  // pitch * rows
   size_t esize = 4;
   cudaStream_t stream = nullptr;
   int device = 0;
-  void* f[2] = {nullptr, nullptr};  // Real [9][ny][pitch]
+  int num_sms = 0;
+  void* f[2] = {nullptr, nullptr};  // Real [9][rows][pitch]
   int cur = 0;                      // buffer holding the current f*
-  uint8_t* mask = nullptr;
-  void* vel = nullptr;     // Real [2][ny][pitch]
-  void* kf = nullptr;      // Real [ny][pitch] or null
-  void* u = nullptr;       // Real [ny][pitch]
-  void* ureact = nullptr;  // Real [ny][pitch] (dissolution)
+  uint32_t* link = nullptr;  // [rows][pitch] link words
+  void* vel = nullptr;     // Real [2][rows][pitch]
+  void* kf = nullptr;      // Real [rows][pitch] or null
+  void* u = nullptr;       // Real [rows][pitch]
+  void* ureact = nullptr;  // Real [rows][pitch] (dissolution)
   double* mineral = nullptr;
   double* edge = nullptr;  // [3][nedge]: u_dir_t0, u_dir_t1, q
   long long* infeasible = nullptr;  // [nedge]
   double* jnode = nullptr;          // [ny]
-  double* partial = nullptr;        // [nblocks]
+  double* partial = nullptr;        // [max(blocks)]
+  int nparts = 0;                   // partials written by the last final step
   int* flip_list = nullptr;
-  int* flip_count = nullptr;  // + done counter + padding
-  long long* counters = nullptr;  // [0] flips total
+  int* flip_count = nullptr;      // [0] count, [1] done counter
+  long long* counters = nullptr;  // [0] flips total, [1] solid count at init
+  int* status = nullptr;          // device error word
   DiagDev* diag = nullptr;
-  void* scratch = nullptr;  // host-copy staging for outputs
+  void* scratch = nullptr;  // staging for host outputs
   size_t scratch_bytes = 0;
   long long steps = 0;
   int nedge = 0;
   dim3 grid, block;
+  int dgrid = 0;  // persistent blocks of the dissolution pass
+  bool use_tma = false;
+  int tma_grid = 0, ntx = 0, nty = 0;
+  lbm::TmaMaps maps[2];  // pop map of f[0] / f[1]; other maps identical
   // kernel timing (lbm_kernel_timing): event pairs per launch, folded into
   // the sums whenever the pool fills or the times are read
   bool timing = false;
@@ -229,7 +284,7 @@ lbm::StepArgs<Real> step_args(lbm_ctx* c, double frac) {
   lbm::StepArgs<Real> a;
   a.fin = (const Real*)c->f[c->cur];
   a.fout = (Real*)c->f[c->cur ^ 1];
-  a.mask = c->mask;
+  a.link = c->link;
   a.vel = (const Real*)c->vel;
   a.kf = (const Real*)c->kf;
   a.u_out = (Real*)c->u;
@@ -240,6 +295,7 @@ lbm::StepArgs<Real> step_args(lbm_ctx* c, double frac) {
   a.infeasible = c->infeasible;
   a.jnode = c->jnode;
   a.partial = c->partial;
+  a.status = c->status;
   a.plane = c->plane;
   a.nx = c->p.nx;
   a.ny = c->p.ny;
@@ -257,7 +313,7 @@ lbm::StepArgs<Real> step_args(lbm_ctx* c, double frac) {
 
 lbm::DissolveArgs dissolve_args(lbm_ctx* c) {
   lbm::DissolveArgs d;
-  d.mask = c->mask;
+  d.link = c->link;
   d.mineral = c->mineral;
   d.flip_list = c->flip_list;
   d.flip_count = c->flip_count;
@@ -288,10 +344,7 @@ lbm_status fold_times(lbm_ctx* c, int which) {
 // Record the opening event of a timed launch (which: 0 step, 1 dissolve).
 lbm_status time_begin(lbm_ctx* c, int which) {
   if (!c->timing) return LBM_OK;
-  if (c->ev_used[which] == lbm_ctx::kPool) {
-    lbm_status s = fold_times(c, which);
-    if (s != LBM_OK) return s;
-  }
+  if (c->ev_used[which] == lbm_ctx::kPool) TRY(fold_times(c, which));
   cudaEvent_t* e = c->ev[which][c->ev_used[which]];
   if (!e[0]) {
     CK(cudaEventCreate(&e[0]));
@@ -309,34 +362,61 @@ lbm_status time_end(lbm_ctx* c, int which) {
 
 template <typename Real>
 lbm_status launch_dissolve(lbm_ctx* c, bool check_all = false) {
-  lbm_status s = time_begin(c, 1);
-  if (s != LBM_OK) return s;
+  TRY(time_begin(c, 1));
   lbm::DissolveArgs d = dissolve_args(c);
   d.check_all = check_all ? 1 : 0;
-  lbm::lbm_dissolve<Real><<<c->grid, c->block, 0, c->stream>>>(d, (const Real*)c->ureact);
+  lbm::lbm_dissolve<Real><<<c->dgrid, lbm::kDThreads, 0, c->stream>>>(
+      d, (const Real*)c->ureact);
   CK(cudaGetLastError());
   return time_end(c, 1);
 }
 
 template <typename Real>
+lbm_status launch_step(lbm_ctx* c, double frac, bool final_step);
+
+template <>
+lbm_status launch_step<double>(lbm_ctx* c, double frac, bool final_step) {
+  auto a = step_args<double>(c, frac);
+  if (final_step)
+    lbm::lbm_step<double, true><<<c->grid, c->block, 0, c->stream>>>(a);
+  else
+    lbm::lbm_step<double, false><<<c->grid, c->block, 0, c->stream>>>(a);
+  if (final_step) c->nparts = (int)(c->grid.x * c->grid.y);
+  CK(cudaGetLastError());
+  return LBM_OK;
+}
+
+template <>
+lbm_status launch_step<float>(lbm_ctx* c, double frac, bool final_step) {
+  auto a = step_args<float>(c, frac);
+  if (c->use_tma) {
+    const lbm::TmaMaps& m = c->maps[c->cur];
+    if (final_step)
+      lbm::lbm_step_tma<true><<<c->tma_grid, lbm::kTmaThreads + 32, lbm::kTmaSmem, c->stream>>>(
+          a, m, c->ntx, c->nty);
+    else
+      lbm::lbm_step_tma<false><<<c->tma_grid, lbm::kTmaThreads + 32, lbm::kTmaSmem, c->stream>>>(
+          a, m, c->ntx, c->nty);
+    if (final_step) c->nparts = c->tma_grid;
+  } else {
+    if (final_step)
+      lbm::lbm_step<float, true><<<c->grid, c->block, 0, c->stream>>>(a);
+    else
+      lbm::lbm_step<float, false><<<c->grid, c->block, 0, c->stream>>>(a);
+    if (final_step) c->nparts = (int)(c->grid.x * c->grid.y);
+  }
+  CK(cudaGetLastError());
+  return LBM_OK;
+}
+
+template <typename Real>
 lbm_status run_steps(lbm_ctx* c, int n, int eta) {
   for (int j = 1; j <= n; ++j) {
-    const double frac = (double)j / (double)eta;
-    auto a = step_args<Real>(c, frac);
-    lbm_status s0 = time_begin(c, 0);
-    if (s0 != LBM_OK) return s0;
-    if (j == n)
-      lbm::lbm_step<Real, true><<<c->grid, c->block, 0, c->stream>>>(a);
-    else
-      lbm::lbm_step<Real, false><<<c->grid, c->block, 0, c->stream>>>(a);
-    CK(cudaGetLastError());
-    s0 = time_end(c, 0);
-    if (s0 != LBM_OK) return s0;
+    TRY(time_begin(c, 0));
+    TRY(launch_step<Real>(c, (double)j / (double)eta, j == n));
+    TRY(time_end(c, 0));
     c->cur ^= 1;
-    if (c->p.dissolution) {
-      lbm_status s = launch_dissolve<Real>(c);
-      if (s != LBM_OK) return s;
-    }
+    if (c->p.dissolution) TRY(launch_dissolve<Real>(c));
     c->steps += 1;
   }
   return LBM_OK;
@@ -348,6 +428,7 @@ lbm_status run_init(lbm_ctx* c, const double* u0dev) {
   a.fout = (Real*)c->f[0];
   lbm::lbm_init_kernel<Real><<<c->grid, c->block, 0, c->stream>>>(a, u0dev);
   CK(cudaGetLastError());
+  c->nparts = (int)(c->grid.x * c->grid.y);
   c->cur = 0;
   // the first pass also flips solid nodes given with no mineral at all
   if (c->p.dissolution) return launch_dissolve<Real>(c, true);
@@ -366,8 +447,7 @@ lbm_status stage_doubles(lbm_ctx* c, const double* src, size_t count, double** o
   }
   CK(cudaMalloc((void**)out, count * sizeof(double)));
   *owned = true;
-  CK(cudaMemcpyAsync(*out, src, count * sizeof(double), cudaMemcpyHostToDevice,
-                     c->stream));
+  CK(cudaMemcpyAsync(*out, src, count * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   return LBM_OK;
 }
 
@@ -377,9 +457,10 @@ void free_ctx(lbm_ctx* c) {
     for (int i = 0; i < lbm_ctx::kPool; ++i)
       for (int k = 0; k < 2; ++k)
         if (c->ev[w][i][k]) cudaEventDestroy(c->ev[w][i][k]);
-  void* ptrs[] = {c->f[0], c->f[1], c->mask, c->vel, c->kf, c->u, c->ureact,
-                  c->mineral, c->edge, c->infeasible, c->jnode, c->partial,
-                  c->flip_list, c->flip_count, c->counters, c->diag, c->scratch};
+  void* ptrs[] = {c->f[0],   c->f[1],     c->link,      c->vel,        c->kf,
+                  c->u,      c->ureact,   c->mineral,   c->edge,       c->infeasible,
+                  c->jnode,  c->partial,  c->flip_list, c->flip_count, c->counters,
+                  c->status, c->diag,     c->scratch};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c;
@@ -395,39 +476,98 @@ lbm_status ensure_scratch(lbm_ctx* c, size_t bytes) {
   return LBM_OK;
 }
 
+lbm_status make_map(const char* what, CUtensorMap* m, CUtensorMapDataType dt, int rank,
+                    void* base, const cuuint64_t* dims, const cuuint64_t* strides,
+                    const cuuint32_t* box) {
+  auto enc = encode_fn();
+  if (!enc) return fail(LBM_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+  const cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = enc(m, dt, (cuuint32_t)rank, base, dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS)
+    return fail(LBM_ERR_CUDA, "cuTensorMapEncodeTiled failed for the %s map (%d)", what, (int)r);
+  return LBM_OK;
+}
+
+// Tensor maps of the FP32 TMA step (see lbm_tma.cuh for the boxes).
+lbm_status setup_tma(lbm_ctx* c) {
+  const cuuint64_t P = (cuuint64_t)c->pitch, H = (cuuint64_t)lbm::padded_rows(c->p.ny);
+  const cuuint64_t dpop[3] = {P, H, 9}, spop[2] = {P * 4, P * H * 4};
+  const cuuint32_t bpop[3] = {lbm::kBoxW, lbm::kBoxH, 9};
+  const cuuint64_t dvel[3] = {P, H, 2}, svel[2] = {P * 4, P * H * 4};
+  const cuuint32_t bvel[3] = {lbm::kTW, lbm::kTH, 2};
+  const cuuint64_t d2[2] = {P, H}, sf[1] = {P * 4};
+  const cuuint32_t bk[2] = {lbm::kTW, lbm::kTH};
+  for (int b = 0; b < 2; ++b) {
+    lbm::TmaMaps& m = c->maps[b];
+    TRY(make_map("population", &m.pop, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, c->f[b], dpop,
+                 spop, bpop));
+    TRY(make_map("velocity", &m.vel, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, c->vel, dvel, svel,
+                 bvel));
+    TRY(make_map("link", &m.link, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, c->link, d2, sf, bk));
+    if (c->kf)
+      TRY(make_map("rate", &m.kf, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, c->kf, d2, sf, bk));
+    else m.kf = m.link;  // never read without a rate field
+  }
+  CK(cudaFuncSetAttribute(lbm::lbm_step_tma<true>,
+                          cudaFuncAttributeMaxDynamicSharedMemorySize, lbm::kTmaSmem));
+  CK(cudaFuncSetAttribute(lbm::lbm_step_tma<false>,
+                          cudaFuncAttributeMaxDynamicSharedMemorySize, lbm::kTmaSmem));
+  c->ntx = (c->p.nx + lbm::kTW - 1) / lbm::kTW;
+  c->nty = (c->p.ny + lbm::kTH - 1) / lbm::kTH;
+  const int ntiles = c->ntx * c->nty;
+  c->tma_grid = ntiles < c->num_sms ? ntiles : c->num_sms;
+  c->use_tma = true;
+  return LBM_OK;
+}
+
 lbm_status init_impl(lbm_ctx* c, const uint8_t* solid, const double* vel,
                      const double* k_field, const double* mineral, const double* u0) {
   const lbm_params& p = c->p;
   const size_t nxy = (size_t)p.nx * p.ny;
-  c->pitch = (p.nx + 31) / 32 * 32;
-  c->plane = (long long)c->pitch * p.ny;
+  c->pitch = lbm::padded_pitch(p.nx);
+  c->plane = (long long)c->pitch * lbm::padded_rows(p.ny);
   c->esize = p.precision == 64 ? 8 : 4;
   c->nedge = 2 * (p.nx + p.ny);
   c->block = dim3(lbm::kBX, lbm::kBY);
   c->grid = dim3((p.nx + lbm::kBX - 1) / lbm::kBX, (p.ny + lbm::kBY - 1) / lbm::kBY);
   const size_t plane_b = (size_t)c->plane * c->esize;
+  const int per_x = p.edge[0] == LBM_EDGE_PERIODIC, per_y = p.edge[2] == LBM_EDGE_PERIODIC;
   CK(cudaGetDevice(&c->device));
+  CK(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
+  {
+    const long long blocks = ((long long)p.nx * p.ny + lbm::kDThreads - 1) / lbm::kDThreads;
+    const long long cap = 8LL * c->num_sms;  // 8 resident blocks of 256 per SM
+    c->dgrid = (int)(blocks < cap ? blocks : cap);
+  }
   CK(cudaMalloc(&c->f[0], 9 * plane_b));
   CK(cudaMalloc(&c->f[1], 9 * plane_b));
   CK(cudaMemsetAsync(c->f[0], 0, 9 * plane_b, c->stream));
   CK(cudaMemsetAsync(c->f[1], 0, 9 * plane_b, c->stream));
-  CK(cudaMalloc((void**)&c->mask, (size_t)c->plane));
-  CK(cudaMemsetAsync(c->mask, 0, (size_t)c->plane, c->stream));
+  CK(cudaMalloc((void**)&c->link, (size_t)c->plane * sizeof(uint32_t)));
+  CK(cudaMemsetAsync(c->link, 0, (size_t)c->plane * sizeof(uint32_t), c->stream));
   CK(cudaMalloc(&c->vel, 2 * plane_b));
   CK(cudaMemsetAsync(c->vel, 0, 2 * plane_b, c->stream));
   CK(cudaMalloc(&c->u, plane_b));
   CK(cudaMemsetAsync(c->u, 0, plane_b, c->stream));
-  if (k_field) CK(cudaMalloc(&c->kf, plane_b));
+  if (k_field) {
+    CK(cudaMalloc(&c->kf, plane_b));
+    CK(cudaMemsetAsync(c->kf, 0, plane_b, c->stream));
+  }
   if (p.dissolution) {
     CK(cudaMalloc(&c->ureact, plane_b));
     CK(cudaMemsetAsync(c->ureact, 0, plane_b, c->stream));
     CK(cudaMalloc((void**)&c->mineral, (size_t)c->plane * sizeof(double)));
-    CK(cudaMalloc((void**)&c->flip_list, (size_t)c->plane * sizeof(int)));
+    CK(cudaMemsetAsync(c->mineral, 0, (size_t)c->plane * sizeof(double), c->stream));
+    CK(cudaMalloc((void**)&c->flip_list, nxy * sizeof(int)));
   }
   CK(cudaMalloc((void**)&c->flip_count, 4 * sizeof(int)));
   CK(cudaMemsetAsync(c->flip_count, 0, 4 * sizeof(int), c->stream));
   CK(cudaMalloc((void**)&c->counters, 4 * sizeof(long long)));
   CK(cudaMemsetAsync(c->counters, 0, 4 * sizeof(long long), c->stream));
+  CK(cudaMalloc((void**)&c->status, sizeof(int)));
+  CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
   CK(cudaMalloc((void**)&c->edge, 3 * (size_t)c->nedge * sizeof(double)));
   CK(cudaMemsetAsync(c->edge, 0, 3 * (size_t)c->nedge * sizeof(double), c->stream));
   CK(cudaMalloc((void**)&c->infeasible, (size_t)c->nedge * sizeof(long long)));
@@ -463,13 +603,17 @@ lbm_status init_impl(lbm_ctx* c, const uint8_t* solid, const double* vel,
       dsolid = const_cast<uint8_t*>(solid);
     } else {
       cudaError_t e = cudaMalloc((void**)&dsolid, nxy);
-      if (e != cudaSuccess) { cleanup(); return fail(LBM_ERR_NOMEM, "cudaMalloc: %s", cudaGetErrorString(e)); }
+      if (e != cudaSuccess) {
+        cleanup();
+        return fail(LBM_ERR_NOMEM, "cudaMalloc: %s", cudaGetErrorString(e));
+      }
       osolid = true;
       cudaMemcpyAsync(dsolid, solid, nxy, cudaMemcpyHostToDevice, c->stream);
     }
   }
   const int g = grid1d((long long)nxy * 2);
-  k_mask_in<<<g, 256, 0, c->stream>>>(dsolid, c->mask, p.nx, p.ny, c->pitch);
+  k_link_in<<<grid1d((long long)nxy), 256, 0, c->stream>>>(dsolid, c->link, p.nx, p.ny,
+                                                           c->pitch, per_x, per_y);
   if (c->esize == 8) {
     k_pitch_in<double><<<g, 256, 0, c->stream>>>(dvel, (double*)c->vel, p.nx, p.ny, c->pitch, 2, 0.0);
     if (dk) k_pitch_in<double><<<g, 256, 0, c->stream>>>(dk, (double*)c->kf, p.nx, p.ny, c->pitch, 1, 0.0);
@@ -479,17 +623,32 @@ lbm_status init_impl(lbm_ctx* c, const uint8_t* solid, const double* vel,
   }
   if (p.dissolution)
     k_pitch_in<double><<<g, 256, 0, c->stream>>>(dmin, c->mineral, p.nx, p.ny, c->pitch, 1, 1.0);
+  k_count_solid<<<grid1d((long long)nxy), 256, 0, c->stream>>>(
+      c->link, p.nx, p.ny, c->pitch, (unsigned long long*)(c->counters + 1));
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) { cleanup(); return fail(LBM_ERR_CUDA, "input conversion: %s", cudaGetErrorString(e)); }
+  if (e != cudaSuccess) {
+    cleanup();
+    return fail(LBM_ERR_CUDA, "input conversion: %s", cudaGetErrorString(e));
+  }
   st = c->esize == 8 ? run_init<double>(c, du0) : run_init<float>(c, du0);
   cleanup();
   if (st != LBM_OK) return st;
   CK(cudaGetLastError());
+  if (c->esize == 4) TRY(setup_tma(c));
   return LBM_OK;
 }
 
 lbm_status check_ctx(const lbm_ctx* c) {
   if (!c) return fail(LBM_ERR_ARG, "null context");
+  return LBM_OK;
+}
+
+// Reads the device status word (waits for the stream).
+lbm_status check_status(lbm_ctx* c) {
+  int st = 0;
+  CK(cudaMemcpyAsync(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (st) return fail(LBM_ERR_TIMEOUT, "a kernel's bounded wait expired (status %d)", st);
   return LBM_OK;
 }
 
@@ -502,7 +661,7 @@ int state_sections(lbm_ctx* c, Section* s) {
   int k = 0;
   const size_t plane_b = (size_t)c->plane * c->esize;
   s[k++] = {c->f[c->cur], 9 * plane_b};
-  s[k++] = {c->mask, (size_t)c->plane};
+  s[k++] = {c->link, (size_t)c->plane * sizeof(uint32_t)};
   s[k++] = {c->u, plane_b};
   s[k++] = {c->infeasible, (size_t)c->nedge * sizeof(long long)};
   s[k++] = {c->jnode, (size_t)c->p.ny * sizeof(double)};
@@ -515,9 +674,30 @@ size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 struct BlobHeader {
   unsigned long long magic;
   long long steps;
-  int nx, ny, precision, dissolution;
+  int nx, ny, precision, dissolution, nparts, pad;
 };
-const unsigned long long kMagic = 0x4C424D4144453031ull;  // "LBMADE01"
+const unsigned long long kMagic = 0x4C424D4144453033ull;  // "LBMADE03"
+
+// Copy a padded device field out to a caller array (host or device) of
+// `planes` [ny][nx] planes, converting to O.
+template <typename T, typename O>
+lbm_status field_out(lbm_ctx* c, const T* src, O* dst, int planes) {
+  const size_t bytes = (size_t)planes * c->p.nx * c->p.ny * sizeof(O);
+  const bool dev = on_device(dst);
+  O* d = dst;
+  if (!dev) {
+    TRY(ensure_scratch(c, bytes));
+    d = (O*)c->scratch;
+  }
+  k_pitch_out<T, O><<<grid1d((long long)planes * c->p.nx * c->p.ny), 256, 0, c->stream>>>(
+      src, d, c->p.nx, c->p.ny, c->pitch, planes);
+  CK(cudaGetLastError());
+  if (!dev) {
+    CK(cudaMemcpyAsync(dst, d, bytes, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  return LBM_OK;
+}
 
 }  // namespace
 
@@ -534,8 +714,8 @@ lbm_status lbm_init(lbm_ctx** out, const lbm_params* p, const uint8_t* solid,
   if (!out || !p) return fail(LBM_ERR_ARG, "lbm_init: null out or params");
   *out = nullptr;
   if (p->nx < 2 || p->ny < 2) return fail(LBM_ERR_ARG, "lbm_init: nx, ny must be >= 2");
-  if ((long long)((p->nx + 31) / 32 * 32) * p->ny > INT_MAX)
-    return fail(LBM_ERR_ARG, "lbm_init: lattice too large (pitch*ny > INT_MAX)");
+  if ((long long)lbm::padded_pitch(p->nx) * lbm::padded_rows(p->ny) > INT_MAX)
+    return fail(LBM_ERR_ARG, "lbm_init: lattice too large (padded plane > INT_MAX)");
   if (p->precision != 32 && p->precision != 64)
     return fail(LBM_ERR_ARG, "lbm_init: precision must be 32 or 64");
   if (!(p->tau > 0.5) || !std::isfinite(p->tau))
@@ -564,7 +744,7 @@ lbm_status lbm_init(lbm_ctx** out, const lbm_params* p, const uint8_t* solid,
 
 lbm_status lbm_substeps(lbm_ctx* c, int n, int eta, const double* u_dir_t0,
                         const double* u_dir_t1, const double* q_neu) {
-  if (check_ctx(c)) return LBM_ERR_ARG;
+  TRY(check_ctx(c));
   if (n < 0 || eta < 1) return fail(LBM_ERR_ARG, "lbm_substeps: need n >= 0, eta >= 1");
   if (n == 0) return LBM_OK;
   const size_t eb = (size_t)c->nedge * sizeof(double);
@@ -584,7 +764,7 @@ lbm_status lbm_substeps(lbm_ctx* c, int n, int eta, const double* u_dir_t0,
 }
 
 lbm_status lbm_interface_trace(lbm_ctx* c, int npts, const double* xy, double* u_out) {
-  if (check_ctx(c)) return LBM_ERR_ARG;
+  TRY(check_ctx(c));
   if (npts < 0 || (npts > 0 && (!xy || !u_out)))
     return fail(LBM_ERR_ARG, "lbm_interface_trace: bad arguments");
   if (npts == 0) return LBM_OK;
@@ -592,10 +772,7 @@ lbm_status lbm_interface_trace(lbm_ctx* c, int npts, const double* xy, double* u
   const double* dxy = xy;
   double* dout = u_out;
   const size_t in_b = 2 * (size_t)npts * sizeof(double), out_b = (size_t)npts * sizeof(double);
-  if (!xy_dev || !out_dev) {
-    lbm_status s = ensure_scratch(c, align256(in_b) + out_b);
-    if (s != LBM_OK) return s;
-  }
+  if (!xy_dev || !out_dev) TRY(ensure_scratch(c, align256(in_b) + out_b));
   if (!xy_dev) {
     CK(cudaMemcpyAsync(c->scratch, xy, in_b, cudaMemcpyHostToDevice, c->stream));
     dxy = (const double*)c->scratch;
@@ -604,9 +781,11 @@ lbm_status lbm_interface_trace(lbm_ctx* c, int npts, const double* xy, double* u
   const int per_x = c->p.edge[0] == LBM_EDGE_PERIODIC, per_y = c->p.edge[2] == LBM_EDGE_PERIODIC;
   const int g = (npts + 255) / 256;
   if (c->esize == 8)
-    k_trace<double><<<g, 256, 0, c->stream>>>((const double*)c->u, c->p.nx, c->p.ny, c->pitch, per_x, per_y, dxy, npts, dout);
+    k_trace<double><<<g, 256, 0, c->stream>>>((const double*)c->u, c->p.nx, c->p.ny, c->pitch,
+                                              per_x, per_y, dxy, npts, dout);
   else
-    k_trace<float><<<g, 256, 0, c->stream>>>((const float*)c->u, c->p.nx, c->p.ny, c->pitch, per_x, per_y, dxy, npts, dout);
+    k_trace<float><<<g, 256, 0, c->stream>>>((const float*)c->u, c->p.nx, c->p.ny, c->pitch,
+                                             per_x, per_y, dxy, npts, dout);
   CK(cudaGetLastError());
   if (!out_dev) {
     CK(cudaMemcpyAsync(u_out, dout, out_b, cudaMemcpyDeviceToHost, c->stream));
@@ -614,105 +793,82 @@ lbm_status lbm_interface_trace(lbm_ctx* c, int npts, const double* xy, double* u
   } else if (!xy_dev) {
     CK(cudaStreamSynchronize(c->stream));
   }
-  return LBM_OK;
+  return check_status(c);
 }
-
-}  // extern "C"
-
-namespace {
-// Copy a pitched device field out to a caller array (host or device) of
-// `planes` [ny][nx] planes, converting to O.
-template <typename T, typename O>
-lbm_status field_out(lbm_ctx* c, const T* src, O* dst, int planes) {
-  const size_t bytes = (size_t)planes * c->p.nx * c->p.ny * sizeof(O);
-  const bool dev = on_device(dst);
-  O* d = dst;
-  if (!dev) {
-    lbm_status s = ensure_scratch(c, bytes);
-    if (s != LBM_OK) return s;
-    d = (O*)c->scratch;
-  }
-  k_pitch_out<T, O><<<grid1d((long long)planes * c->p.nx * c->p.ny), 256, 0, c->stream>>>(
-      src, d, c->p.nx, c->p.ny, c->pitch, planes);
-  CK(cudaGetLastError());
-  if (!dev) {
-    CK(cudaMemcpyAsync(dst, d, bytes, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-  }
-  return LBM_OK;
-}
-}  // namespace
-
-extern "C" {
 
 lbm_status lbm_get_concentration(lbm_ctx* c, void* out, int out_precision) {
-  if (check_ctx(c)) return LBM_ERR_ARG;
+  TRY(check_ctx(c));
   if (!out || (out_precision != 32 && out_precision != 64))
     return fail(LBM_ERR_ARG, "lbm_get_concentration: bad arguments");
   if (c->esize == 8)
-    return out_precision == 64 ? field_out<double, double>(c, (const double*)c->u, (double*)out, 1)
-                               : field_out<double, float>(c, (const double*)c->u, (float*)out, 1);
-  return out_precision == 64 ? field_out<float, double>(c, (const float*)c->u, (double*)out, 1)
-                             : field_out<float, float>(c, (const float*)c->u, (float*)out, 1);
+    TRY(out_precision == 64
+            ? field_out<double, double>(c, (const double*)c->u, (double*)out, 1)
+            : field_out<double, float>(c, (const double*)c->u, (float*)out, 1));
+  else
+    TRY(out_precision == 64 ? field_out<float, double>(c, (const float*)c->u, (double*)out, 1)
+                            : field_out<float, float>(c, (const float*)c->u, (float*)out, 1));
+  return check_status(c);
 }
 
 lbm_status lbm_get_populations(lbm_ctx* c, double* out) {
-  if (check_ctx(c)) return LBM_ERR_ARG;
+  TRY(check_ctx(c));
   if (!out) return fail(LBM_ERR_ARG, "lbm_get_populations: null out");
-  if (c->esize == 8) return field_out<double, double>(c, (const double*)c->f[c->cur], out, 9);
-  return field_out<float, double>(c, (const float*)c->f[c->cur], out, 9);
+  if (c->esize == 8) TRY(field_out<double, double>(c, (const double*)c->f[c->cur], out, 9));
+  else TRY(field_out<float, double>(c, (const float*)c->f[c->cur], out, 9));
+  return check_status(c);
 }
 
 lbm_status lbm_get_solid(lbm_ctx* c, uint8_t* out) {
-  if (check_ctx(c)) return LBM_ERR_ARG;
+  TRY(check_ctx(c));
   if (!out) return fail(LBM_ERR_ARG, "lbm_get_solid: null out");
   const size_t bytes = (size_t)c->p.nx * c->p.ny;
   const bool dev = on_device(out);
   uint8_t* d = out;
   if (!dev) {
-    lbm_status s = ensure_scratch(c, bytes);
-    if (s != LBM_OK) return s;
+    TRY(ensure_scratch(c, bytes));
     d = (uint8_t*)c->scratch;
   }
-  k_solid_out<<<grid1d((long long)bytes), 256, 0, c->stream>>>(c->mask, d, c->p.nx, c->p.ny, c->pitch);
+  k_solid_out<<<grid1d((long long)bytes), 256, 0, c->stream>>>(c->link, d, c->p.nx, c->p.ny,
+                                                               c->pitch);
   CK(cudaGetLastError());
   if (!dev) {
     CK(cudaMemcpyAsync(out, d, bytes, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
   }
-  return LBM_OK;
+  return check_status(c);
 }
 
 lbm_status lbm_get_mineral(lbm_ctx* c, double* out) {
-  if (check_ctx(c)) return LBM_ERR_ARG;
+  TRY(check_ctx(c));
   if (!out) return fail(LBM_ERR_ARG, "lbm_get_mineral: null out");
   if (!c->p.dissolution) return fail(LBM_ERR_STATE, "lbm_get_mineral: dissolution is off");
-  return field_out<double, double>(c, c->mineral, out, 1);
+  TRY(field_out<double, double>(c, c->mineral, out, 1));
+  return check_status(c);
 }
 
 lbm_status lbm_diagnostics(lbm_ctx* c, lbm_diag* out) {
-  if (check_ctx(c)) return LBM_ERR_ARG;
+  TRY(check_ctx(c));
   if (!out) return fail(LBM_ERR_ARG, "lbm_diagnostics: null out");
-  k_diag<<<1, 256, 0, c->stream>>>(c->partial, (int)(c->grid.x * c->grid.y), c->jnode,
-                                   c->p.ny, c->infeasible, c->nedge, c->mask, c->p.nx,
-                                   c->pitch, c->diag);
+  k_diag<<<1, 256, 0, c->stream>>>(c->partial, c->nparts, c->jnode, c->p.ny, c->infeasible,
+                                   c->nedge, c->diag);
   CK(cudaGetLastError());
   DiagDev h;
   long long ctr[4];
   CK(cudaMemcpyAsync(&h, c->diag, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaMemcpyAsync(ctr, c->counters, sizeof(ctr), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
+  TRY(check_status(c));
   out->mass = h.mass;
   out->outlet_J = h.J;
   out->steps = c->steps;
   out->bc_infeasible = h.infeasible;
   out->flips = ctr[0];
-  out->n_solid = h.n_solid;
+  out->n_solid = ctr[1] - ctr[0];
   return LBM_OK;
 }
 
 lbm_status lbm_state_bytes(lbm_ctx* c, size_t* bytes) {
-  if (check_ctx(c)) return LBM_ERR_ARG;
+  TRY(check_ctx(c));
   if (!bytes) return fail(LBM_ERR_ARG, "lbm_state_bytes: null out");
   Section s[16];
   const int k = state_sections(c, s);
@@ -724,13 +880,13 @@ lbm_status lbm_state_bytes(lbm_ctx* c, size_t* bytes) {
 
 lbm_status lbm_save(lbm_ctx* c, void* buf, size_t bytes) {
   size_t need = 0;
-  lbm_status st = lbm_state_bytes(c, &need);
-  if (st != LBM_OK) return st;
+  TRY(lbm_state_bytes(c, &need));
   if (!buf || bytes < need) return fail(LBM_ERR_ARG, "lbm_save: buffer smaller than lbm_state_bytes");
   const bool dev = on_device(buf);
   const cudaMemcpyKind k = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-  BlobHeader h{kMagic, c->steps, c->p.nx, c->p.ny, c->p.precision, c->p.dissolution};
-  CK(cudaMemcpyAsync(buf, &h, sizeof(h), dev ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, c->stream));
+  BlobHeader h{kMagic, c->steps, c->p.nx, c->p.ny, c->p.precision, c->p.dissolution, c->nparts, 0};
+  CK(cudaMemcpyAsync(buf, &h, sizeof(h), dev ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost,
+                     c->stream));
   Section s[16];
   const int n = state_sections(c, s);
   size_t off = align256(sizeof(BlobHeader));
@@ -739,17 +895,17 @@ lbm_status lbm_save(lbm_ctx* c, void* buf, size_t bytes) {
     off += align256(s[i].bytes);
   }
   CK(cudaStreamSynchronize(c->stream));  // the header lives on this stack frame
-  return LBM_OK;
+  return check_status(c);
 }
 
 lbm_status lbm_restore(lbm_ctx* c, const void* buf, size_t bytes) {
   size_t need = 0;
-  lbm_status st = lbm_state_bytes(c, &need);
-  if (st != LBM_OK) return st;
+  TRY(lbm_state_bytes(c, &need));
   if (!buf || bytes < need) return fail(LBM_ERR_ARG, "lbm_restore: buffer smaller than lbm_state_bytes");
   const bool dev = on_device(buf);
   BlobHeader h;
-  CK(cudaMemcpyAsync(&h, buf, sizeof(h), dev ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, c->stream));
+  CK(cudaMemcpyAsync(&h, buf, sizeof(h), dev ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost,
+                     c->stream));
   CK(cudaStreamSynchronize(c->stream));
   if (h.magic != kMagic || h.nx != c->p.nx || h.ny != c->p.ny ||
       h.precision != c->p.precision || h.dissolution != c->p.dissolution)
@@ -763,15 +919,15 @@ lbm_status lbm_restore(lbm_ctx* c, const void* buf, size_t bytes) {
     off += align256(s[i].bytes);
   }
   c->steps = h.steps;
+  c->nparts = h.nparts;
   if (!dev) CK(cudaStreamSynchronize(c->stream));
   return LBM_OK;
 }
 
 lbm_status lbm_kernel_timing(lbm_ctx* c, int enable) {
-  if (check_ctx(c)) return LBM_ERR_ARG;
+  TRY(check_ctx(c));
   for (int w = 0; w < 2; ++w) {
-    lbm_status s = fold_times(c, w);
-    if (s != LBM_OK) return s;
+    TRY(fold_times(c, w));
     c->ms_sum[w] = 0.0;
     c->launches[w] = 0;
   }
@@ -781,11 +937,8 @@ lbm_status lbm_kernel_timing(lbm_ctx* c, int enable) {
 
 lbm_status lbm_kernel_times_read(lbm_ctx* c, double* step_ms, long long* step_launches,
                                  double* dissolve_ms, long long* dissolve_launches) {
-  if (check_ctx(c)) return LBM_ERR_ARG;
-  for (int w = 0; w < 2; ++w) {
-    lbm_status s = fold_times(c, w);
-    if (s != LBM_OK) return s;
-  }
+  TRY(check_ctx(c));
+  for (int w = 0; w < 2; ++w) TRY(fold_times(c, w));
   if (step_ms) *step_ms = c->ms_sum[0];
   if (step_launches) *step_launches = c->launches[0];
   if (dissolve_ms) *dissolve_ms = c->ms_sum[1];
@@ -794,16 +947,15 @@ lbm_status lbm_kernel_times_read(lbm_ctx* c, double* step_ms, long long* step_la
 }
 
 lbm_status lbm_set_stream(lbm_ctx* c, void* stream) {
-  if (check_ctx(c)) return LBM_ERR_ARG;
+  TRY(check_ctx(c));
   CK(cudaStreamSynchronize(c->stream));
   c->stream = (cudaStream_t)stream;
   return LBM_OK;
 }
 
 lbm_status lbm_synchronize(lbm_ctx* c) {
-  if (check_ctx(c)) return LBM_ERR_ARG;
-  CK(cudaStreamSynchronize(c->stream));
-  return LBM_OK;
+  TRY(check_ctx(c));
+  return check_status(c);
 }
 
 void lbm_destroy(lbm_ctx* c) {

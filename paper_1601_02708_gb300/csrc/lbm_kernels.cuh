@@ -1,14 +1,19 @@
 // lbm_kernels.cuh -- the fused D2Q9 ADE-LBM step and its companions.
 //
 // State between steps: post-collision populations f* in SoA planes
-// [9][ny][pitch] (pitch = nx rounded up to 32 elements), two buffers
-// swapped every step.  One step (kernel lbm_step) pulls f_i(x) = f*_i(x - e_i)
+// [9][rows][pitch] (padded layout with ghost cells, see lbm_lattice.cuh),
+// two buffers swapped every step.  One step pulls f_i(x) = f*_i(x - e_i)
 // (Eq. "LBE"), replaces pulls from solid nodes by halfway bounce-back, sets
 // the populations pulled from outside the lattice by the maximum-entropy
 // conditions (Sec. 4.1.1), takes u = sum f (Eq. "LBM_Macro"), and collides
 // with the BGK operator (Eq. "Collision", "LBM_feq") plus the first-order
 // sink.  The sequence of states equals the paper's collide -> stream -> BC
 // order shifted by half a step: the stored f* is what the next stream moves.
+//
+// The node update (step_node) is written once and reads its inputs through a
+// source object: GlobalSrc reads the padded arrays directly (FP64 mode and
+// the generic kernel), the TMA kernel of lbm_tma.cuh reads a shared-memory
+// tile.
 #pragma once
 #include <cstdint>
 
@@ -16,25 +21,26 @@
 
 namespace lbm {
 
-constexpr int kBX = 32;  // threads along x per block (one warp per row)
-constexpr int kBY = 8;   // rows per block
+constexpr int kBX = 32;  // generic kernel: threads along x per block
+constexpr int kBY = 8;   // generic kernel: rows per block
 
 template <typename Real>
 struct StepArgs {
   const Real* __restrict__ fin;  // f* of the previous step
   Real* __restrict__ fout;       // f* of this step
-  const uint8_t* __restrict__ mask;
-  const Real* __restrict__ vel;  // [2][ny][pitch]
-  const Real* __restrict__ kf;   // [ny][pitch] or null
-  Real* __restrict__ u_out;      // [ny][pitch], written on the final substep
-  Real* __restrict__ ureact;     // [ny][pitch], k u / W_s at reactive nodes (dissolution)
+  const uint32_t* __restrict__ link;  // [rows][pitch] link words
+  const Real* __restrict__ vel;  // [2][rows][pitch]
+  const Real* __restrict__ kf;   // [rows][pitch] or null
+  Real* __restrict__ u_out;      // [rows][pitch], written on the final substep
+  Real* __restrict__ ureact;     // [rows][pitch], k u / W_s at reactive nodes
   const double* __restrict__ ua;  // edge data, start of the coarse step
   const double* __restrict__ ub;  // edge data, end of the coarse step
   const double* __restrict__ q;   // Neumann data
   long long* __restrict__ infeasible;  // per edge slot
   double* __restrict__ jnode;          // per east-edge row: sum_t u
   double* __restrict__ partial;        // per block: sum u (final substep)
-  long long plane;  // pitch * ny
+  int* __restrict__ status;            // device error word (0 = fine)
+  long long plane;  // pitch * rows
   int nx, ny, pitch;
   int per_x, per_y;
   int edge[4];
@@ -51,6 +57,7 @@ __device__ __forceinline__ double block_sum(double v, double* smem) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   const int lane = tid & 31, wid = tid >> 5;
+  __syncthreads();
   if (lane == 0) smem[wid] = v;
   __syncthreads();
   double s = 0.0;
@@ -82,120 +89,173 @@ __device__ __forceinline__ void equilibrium(Real (&feq)[9], Real u, Real vx, Rea
   feq[0] = rest;
 }
 
+// Collision written for the fewest operations: with P_i = 1 + 3 e.v +
+// 4.5 (e.v)^2 - 1.5 v.v, f*_i = (1 - omega) f_i + w_i u (omega P_i - k) for the
+// moving populations, and the rest population takes the remainder
+// f*_0 = (1 - k) u - sum_{i>0} f*_i, which is the same value in exact
+// arithmetic (sum_i f*_i = (1 - k) u) and keeps the stored populations
+// summing to the post-reaction mass in FP32.
 template <typename Real>
-__device__ __forceinline__ void collide_store(const Real (&f)[9], Real u, Real vx,
-                                              Real vy, Real omega, Real kr,
-                                              Real* __restrict__ out, long long plane,
-                                              long long n) {
-  Real feq[9];
-  equilibrium(feq, u, vx, vy);
-  const Real sink = kr * u;
-  Real sink0 = sink;
+__device__ __forceinline__ void collide(Real (&f)[9], Real u, Real vx, Real vy,
+                                        Real omega, Real kr) {
+  const Real base = (Real)1 - (Real)1.5 * (vx * vx + vy * vy);
+  const Real om1 = (Real)1 - omega;
+  const Real wu1 = (Real)w_of(1) * u, wu2 = (Real)w_of(5) * u;
+  Real rest = u - kr * u;
 #pragma unroll
   for (int i = 1; i < 9; ++i) {
-    const Real si = (Real)w_of(i) * sink;
-    sink0 -= si;
-    out[i * plane + n] = f[i] + omega * (feq[i] - f[i]) - si;
+    const Real ev = (Real)cx_of(i) * vx + (Real)cy_of(i) * vy;
+    const Real P = ev * ((Real)4.5 * ev + (Real)3) + base;
+    const Real g = (i <= 4 ? wu1 : wu2) * (omega * P - kr);
+    f[i] = om1 * f[i] + g;
+    rest -= f[i];
   }
-  out[n] = f[0] + omega * (feq[0] - f[0]) - sink0;
+  f[0] = rest;
 }
 
+// Store a node value and, at nodes on a periodic side, its ghost images.
+template <typename Real>
+__device__ __forceinline__ void store_node(Real* __restrict__ base, long long n, Real v,
+                                           bool ghosts, int x, int y, int nx, int ny,
+                                           int pitch, int per_x, int per_y) {
+  base[n] = v;
+  if (ghosts)
+    for_each_ghost(x, y, nx, ny, per_x, per_y, [&](int gx, int gy) {
+      base[(long long)gy * pitch + gx] = v;
+    });
+}
+
+// Inputs of one node read straight from the padded global arrays.
+template <typename Real>
+struct GlobalSrc {
+  const StepArgs<Real>& a;
+  long long n;
+  __device__ __forceinline__ long long up(int i) const {  // index of x - e_i
+    return n - (long long)cx_of(i) - (long long)cy_of(i) * a.pitch;
+  }
+  __device__ __forceinline__ uint32_t word() const { return a.link[n]; }
+  __device__ __forceinline__ Real pull(int i) const { return a.fin[i * a.plane + up(i)]; }
+  __device__ __forceinline__ Real own(int i) const { return a.fin[i * a.plane + n]; }
+  __device__ __forceinline__ Real vx() const { return a.vel[n]; }
+  __device__ __forceinline__ Real vy() const { return a.vel[a.plane + n]; }
+  __device__ __forceinline__ Real kf() const { return a.kf[n]; }
+};
+
+// One node's step.  (x, y) interior coordinates, n its padded index.  Writes
+// f* (and ghost images), ureact, jnode, u_out; returns u (0 at solid nodes)
+// for the mass reduction.
+// kEdge false: the caller guarantees the node is at least one node away
+// from every side, so no pull leaves the lattice, no ghost image exists and
+// the node is not on the outlet; the boundary code is then compiled out.
+template <typename Real, bool kFinal, bool kEdge, class Src>
+__device__ __forceinline__ double step_node(const StepArgs<Real>& a, const Src& src,
+                                            int x, int y, long long n) {
+  const uint32_t w = src.word();
+  const bool ghosts =
+      kEdge && ((x == 0) | (x == a.nx - 1) | (y == 0) | (y == a.ny - 1)) &&
+      (a.per_x | a.per_y);
+  if (w & kOwnSolid) {
+    if (w & kOwnPending) {  // became fluid with zero populations
+#pragma unroll
+      for (int i = 0; i < 9; ++i)
+        store_node(a.fout + i * a.plane, n, (Real)0, ghosts, x, y, a.nx, a.ny, a.pitch,
+                   a.per_x, a.per_y);
+      if (a.dissolution)
+        store_node(a.ureact, n, (Real)0, ghosts, x, y, a.nx, a.ny, a.pitch, a.per_x,
+                   a.per_y);
+    }
+    if (kFinal) a.u_out[n] = (Real)0;
+    return 0.0;
+  }
+  Real f[9];
+  f[0] = src.own(0);
+#pragma unroll
+  for (int i = 1; i < 9; ++i)
+    f[i] = (w & up_bit(kUpSolidShift, i)) ? src.own(opp_of(i)) : src.pull(i);
+  if (kEdge) {
+    const unsigned unknown = ((w >> kUpOutShift) & 0xFFu) << 1;  // bit i: direction i
+    if (unknown) {
+      // Boundary node: Dirichlet wins at corners, else Neumann.
+      const bool on[4] = {x == 0 && a.edge[0] != kPeriodic,
+                          x == a.nx - 1 && a.edge[1] != kPeriodic,
+                          y == 0 && a.edge[2] != kPeriodic,
+                          y == a.ny - 1 && a.edge[3] != kPeriodic};
+      int dside = -1, nside = -1, sx = 0, sy = 0;
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        if (!on[s]) continue;
+        if (a.edge[s] == kDirichlet && dside < 0) dside = s;
+        if (a.edge[s] == kNeumann) {
+          if (nside < 0) nside = s;
+          sx += (s == 0) ? -1 : (s == 1) ? 1 : 0;
+          sy += (s == 2) ? -1 : (s == 3) ? 1 : 0;
+        }
+      }
+      bool bad;
+      int slot;
+      if (dside >= 0) {
+        slot = edge_slot(dside, x, y, a.nx, a.ny);
+        const double up = (1.0 - a.frac) * a.ua[slot] + a.frac * a.ub[slot];
+        bad = maxent_dirichlet(f, unknown, up);
+      } else {
+        slot = edge_slot(nside, x, y, a.nx, a.ny);
+        Real fbb[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+          fbb[i] = (unknown & (1u << opp_of(i))) ? src.own(i) : (Real)0;
+        bad = maxent_neumann(f, unknown, sx, sy, a.q[slot], fbb);
+      }
+      if (bad) a.infeasible[slot] += 1;
+    }
+  }
+  Real u = f[0];
+#pragma unroll
+  for (int i = 1; i < 9; ++i) u += f[i];
+  // links to solid neighbours after this step's flips: axis links weigh 1/9,
+  // diagonal links 1/36
+  const uint32_t post = (w >> kUpPostShift) & 0xFFu;
+  const bool near_solid = post != 0u;
+  Real kr = (Real)0;
+  if (a.react_mode == kReactBulk || (a.react_mode == kReactSurface && near_solid))
+    kr = a.kf ? src.kf() : a.k_scalar;
+  collide(f, u, src.vx(), src.vy(), a.omega, kr);
+#pragma unroll
+  for (int i = 0; i < 9; ++i)
+    store_node(a.fout + i * a.plane, n, f[i], ghosts, x, y, a.nx, a.ny, a.pitch,
+               a.per_x, a.per_y);
+  // mass this node takes from each solid neighbour per unit link weight
+  if (a.dissolution && near_solid) {
+    const Real wsolid = (Real)__popc(post & 0x0Fu) * (Real)w_of(1) +
+                        (Real)__popc(post & 0xF0u) * (Real)w_of(5);
+    store_node(a.ureact, n, kr * u / wsolid, ghosts, x, y, a.nx, a.ny, a.pitch, a.per_x,
+               a.per_y);
+  }
+  if (kEdge && x == a.nx - 1) a.jnode[y] += (double)u;
+  if (kFinal) a.u_out[n] = u;
+  return (double)u;
+}
+
+// True when every node of the box [x0, x0 + w) x [y0, y0 + h) is one node
+// or more away from each side of the lattice.
+__device__ __forceinline__ bool box_is_interior(int x0, int y0, int w, int h, int nx, int ny) {
+  return x0 >= 1 && y0 >= 1 && x0 + w <= nx - 1 && y0 + h <= ny - 1;
+}
+
+// Generic step: one thread per node, inputs from global memory.  Used in
+// FP64 mode; the FP32 path runs the TMA kernel instead.
 template <typename Real, bool kFinal>
-__global__ void __launch_bounds__(kBX * kBY)
-    lbm_step(const StepArgs<Real> a) {
+__global__ void __launch_bounds__(kBX * kBY) lbm_step(const StepArgs<Real> a) {
   __shared__ double red[kBX * kBY / 32];
   const int x = blockIdx.x * kBX + threadIdx.x;
   const int y = blockIdx.y * kBY + threadIdx.y;
   double my_u = 0.0;
   if (x < a.nx && y < a.ny) {
-    const long long n = (long long)y * a.pitch + x;
-    const uint8_t mk = a.mask[n];
-    if (mk & kSolid) {
-      if (mk & kPending) {  // became fluid with zero populations
-#pragma unroll
-        for (int i = 0; i < 9; ++i) a.fout[i * a.plane + n] = (Real)0;
-        if (a.dissolution) a.ureact[n] = (Real)0;
-      }
-      if (kFinal) a.u_out[n] = (Real)0;
-    } else {
-      Real f[9];
-      unsigned unknown = 0;
-      bool near_solid = false;
-      Real wsolid = (Real)0;  // sum of w_i over links to solid neighbours
-      f[0] = a.fin[n];
-#pragma unroll
-      for (int i = 1; i < 9; ++i) {
-        // upstream neighbour x - e_i, wrapped through periodic sides
-        int sx = x - cx_of(i), sy = y - cy_of(i);
-        bool out = false;
-        if (sx < 0) { if (a.per_x) sx += a.nx; else out = true; }
-        else if (sx >= a.nx) { if (a.per_x) sx -= a.nx; else out = true; }
-        if (sy < 0) { if (a.per_y) sy += a.ny; else out = true; }
-        else if (sy >= a.ny) { if (a.per_y) sy -= a.ny; else out = true; }
-        if (out) {
-          unknown |= 1u << i;
-          f[i] = (Real)0;
-        } else {
-          const long long s = (long long)sy * a.pitch + sx;
-          const uint8_t ms = a.mask[s];
-          if (solid_post(ms)) {
-            near_solid = true;
-            wsolid += (Real)w_of(opp_of(i));  // the link x -> x - e_i
-          }
-          f[i] = (ms & kSolid) ? a.fin[opp_of(i) * a.plane + n]
-                               : a.fin[i * a.plane + s];
-        }
-      }
-      if (unknown) {
-        // Boundary node: Dirichlet wins at corners, else Neumann.
-        const bool on[4] = {x == 0 && a.edge[0] != kPeriodic,
-                            x == a.nx - 1 && a.edge[1] != kPeriodic,
-                            y == 0 && a.edge[2] != kPeriodic,
-                            y == a.ny - 1 && a.edge[3] != kPeriodic};
-        int dside = -1, nside = -1, sx = 0, sy = 0;
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-          if (!on[s]) continue;
-          if (a.edge[s] == kDirichlet && dside < 0) dside = s;
-          if (a.edge[s] == kNeumann) {
-            if (nside < 0) nside = s;
-            sx += (s == 0) ? -1 : (s == 1) ? 1 : 0;
-            sy += (s == 2) ? -1 : (s == 3) ? 1 : 0;
-          }
-        }
-        bool bad;
-        int slot;
-        if (dside >= 0) {
-          slot = edge_slot(dside, x, y, a.nx, a.ny);
-          const double up = (1.0 - a.frac) * a.ua[slot] + a.frac * a.ub[slot];
-          bad = maxent_dirichlet(f, unknown, up);
-        } else {
-          slot = edge_slot(nside, x, y, a.nx, a.ny);
-          Real fbb[9];
-#pragma unroll
-          for (int i = 0; i < 9; ++i)
-            fbb[i] = (unknown & (1u << opp_of(i))) ? a.fin[i * a.plane + n] : (Real)0;
-          bad = maxent_neumann(f, unknown, sx, sy, a.q[slot], fbb);
-        }
-        if (bad) a.infeasible[slot] += 1;
-        // neighbours across the boundary are not solid; the reactive test
-        // already saw every in-lattice neighbour
-      }
-      Real u = f[0];
-#pragma unroll
-      for (int i = 1; i < 9; ++i) u += f[i];
-      Real kr = (Real)0;
-      if (a.react_mode == kReactBulk ||
-          (a.react_mode == kReactSurface && near_solid))
-        kr = a.kf ? a.kf[n] : a.k_scalar;
-      const Real vx = a.vel[n], vy = a.vel[a.plane + n];
-      collide_store(f, u, vx, vy, a.omega, kr, a.fout, a.plane, n);
-      // mass this node takes from each solid neighbour per unit link weight
-      if (a.dissolution && near_solid) a.ureact[n] = kr * u / wsolid;
-      if (x == a.nx - 1) a.jnode[y] += (double)u;
-      if (kFinal) a.u_out[n] = u;
-      my_u = (double)u;
-    }
+    const long long n = (long long)(y + kYO) * a.pitch + (x + kXO);
+    GlobalSrc<Real> src{a, n};
+    if (box_is_interior(blockIdx.x * kBX, blockIdx.y * kBY, kBX, kBY, a.nx, a.ny))
+      my_u = step_node<Real, kFinal, false>(a, src, x, y, n);
+    else
+      my_u = step_node<Real, kFinal, true>(a, src, x, y, n);
   }
   if (kFinal) {
     const double s = block_sum(my_u, red);
@@ -206,6 +266,7 @@ __global__ void __launch_bounds__(kBX * kBY)
 
 // Initialisation, Sec. 6.2 (i): f = f^eq(u0), then the collision of the
 // first step, so that the stored state is post-collision like every other.
+// u0 is a plain [ny][nx] array.
 template <typename Real>
 __global__ void __launch_bounds__(kBX * kBY)
     lbm_init_kernel(const StepArgs<Real> a, const double* __restrict__ u0) {
@@ -214,38 +275,32 @@ __global__ void __launch_bounds__(kBX * kBY)
   const int y = blockIdx.y * kBY + threadIdx.y;
   double my_u = 0.0;
   if (x < a.nx && y < a.ny) {
-    const long long n = (long long)y * a.pitch + x;
-    const uint8_t mk = a.mask[n];
-    if (mk & kSolid) {
-#pragma unroll
-      for (int i = 0; i < 9; ++i) a.fout[i * a.plane + n] = (Real)0;
+    const long long n = (long long)(y + kYO) * a.pitch + (x + kXO);
+    const bool ghosts = ((x == 0) | (x == a.nx - 1) | (y == 0) | (y == a.ny - 1)) &&
+                        (a.per_x | a.per_y);
+    const uint32_t w = a.link[n];
+    if (w & kOwnSolid) {
       a.u_out[n] = (Real)0;
     } else {
       const Real vx = a.vel[n], vy = a.vel[a.plane + n];
       const Real u = u0 ? (Real)u0[(long long)y * a.nx + x] : (Real)0;
       Real f[9];
       equilibrium(f, u, vx, vy);
-      bool near_solid = false;
-      Real wsolid = (Real)0;
-#pragma unroll
-      for (int i = 1; i < 9; ++i) {
-        int sx = x + cx_of(i), sy = y + cy_of(i);
-        bool out = false;
-        if (sx < 0) { if (a.per_x) sx += a.nx; else out = true; }
-        else if (sx >= a.nx) { if (a.per_x) sx -= a.nx; else out = true; }
-        if (sy < 0) { if (a.per_y) sy += a.ny; else out = true; }
-        else if (sy >= a.ny) { if (a.per_y) sy -= a.ny; else out = true; }
-        if (!out && solid_post(a.mask[(long long)sy * a.pitch + sx])) {
-          near_solid = true;
-          wsolid += (Real)w_of(i);
-        }
-      }
+      const uint32_t post = (w >> kUpPostShift) & 0xFFu;
+      const bool near_solid = post != 0u;
+      const Real wsolid = (Real)__popc(post & 0x0Fu) * (Real)w_of(1) +
+                          (Real)__popc(post & 0xF0u) * (Real)w_of(5);
       Real kr = (Real)0;
-      if (a.react_mode == kReactBulk ||
-          (a.react_mode == kReactSurface && near_solid))
+      if (a.react_mode == kReactBulk || (a.react_mode == kReactSurface && near_solid))
         kr = a.kf ? a.kf[n] : a.k_scalar;
-      collide_store(f, u, vx, vy, a.omega, kr, a.fout, a.plane, n);
-      if (a.dissolution && near_solid) a.ureact[n] = kr * u / wsolid;
+      collide(f, u, vx, vy, a.omega, kr);
+#pragma unroll
+      for (int i = 0; i < 9; ++i)
+        store_node(a.fout + i * a.plane, n, f[i], ghosts, x, y, a.nx, a.ny, a.pitch,
+                   a.per_x, a.per_y);
+      if (a.dissolution && near_solid)
+        store_node(a.ureact, n, kr * u / wsolid, ghosts, x, y, a.nx, a.ny, a.pitch,
+                   a.per_x, a.per_y);
       a.u_out[n] = u;
       my_u = (double)u;
     }
@@ -256,7 +311,7 @@ __global__ void __launch_bounds__(kBX * kBY)
 }
 
 struct DissolveArgs {
-  uint8_t* mask;
+  uint32_t* link;
   double* mineral;
   int* flip_list;
   int* flip_count;
@@ -266,50 +321,73 @@ struct DissolveArgs {
   int check_all;  // also flip untouched solid nodes whose mineral is <= 0
 };
 
+// Atomically clear bit `shift + i - 1` in the link word of every in-lattice
+// neighbour z = y + e_i of node (x, y), i.e. the bit that describes y as z's
+// upstream node in direction i.
+__device__ __forceinline__ void clear_in_neighbours(const DissolveArgs& d, int x, int y,
+                                                    int shift) {
+#pragma unroll
+  for (int i = 1; i < 9; ++i) {
+    int zx = x + cx_of(i), zy = y + cy_of(i);
+    if (zx < 0 || zx >= d.nx) {
+      if (!d.per_x) continue;
+      zx = zx < 0 ? zx + d.nx : zx - d.nx;
+    }
+    if (zy < 0 || zy >= d.ny) {
+      if (!d.per_y) continue;
+      zy = zy < 0 ? zy + d.ny : zy - d.ny;
+    }
+    atomicAnd(d.link + (long long)(zy + kYO) * d.pitch + (zx + kXO), ~up_bit(shift, i));
+  }
+}
+
 // Dissolution after a step: every solid node y gathers the mineral it loses,
 //   m(y) -= sum_j w_j r(s),  s = y - e_j a fluid neighbour,
 // where the step stored r(s) = k(s) u(s) / W_s(s) at every fluid node with a
 // solid neighbour (W_s = sum of the weights of s's links to solid nodes), so
 // the node's sink k u is shared among its solid links in proportion to w_j.
 // The order of the sum is fixed: the result is deterministic.  Nodes that
-// turned fluid before this step's collision (kPending) are cleared to fluid;
-// nodes whose mineral is used up are collected and, by the last block to
-// finish, marked kSolid | kPending: solid for the next step's streaming,
-// fluid (with zero populations) for its collision.
+// turned fluid before this step's collision (pending) become plain fluid and
+// stop being solid upstream for their neighbours; nodes whose mineral is
+// used up are collected and, by the last block to finish, marked pending:
+// solid for the next step's streaming, fluid (with zero populations) for its
+// collision, which their neighbours learn through their post-flip bits.
+// Link-word edits are atomic bit operations on disjoint bits of concurrently
+// read words, so no reader sees a bit it depends on change.
+constexpr int kDThreads = 256;
+
 template <typename Real>
-__global__ void __launch_bounds__(kBX * kBY)
+__global__ void __launch_bounds__(kDThreads)
     lbm_dissolve(const DissolveArgs d, const Real* __restrict__ rlink) {
-  const int x = blockIdx.x * kBX + threadIdx.x;
-  const int y = blockIdx.y * kBY + threadIdx.y;
+  const int tid = threadIdx.x;
   bool flipped = false;
-  if (x < d.nx && y < d.ny) {
-    const long long n = (long long)y * d.pitch + x;
-    const uint8_t mk = d.mask[n];
-    if (mk & kPending) {
-      d.mask[n] = 0;  // solid_post() reads the same before and after
-    } else if (mk & kSolid) {
-      double take = 0.0;
-      bool touched = false;
+  const long long total = (long long)d.nx * d.ny;
+  for (long long id = blockIdx.x * (long long)kDThreads + tid; id < total;
+       id += (long long)gridDim.x * kDThreads) {
+    const int y = (int)(id / d.nx), x = (int)(id % d.nx);
+    const long long n = (long long)(y + kYO) * d.pitch + (x + kXO);
+    const uint32_t w = d.link[n];
+    if (!(w & kOwnSolid)) continue;
+    if (w & kOwnPending) {
+      atomicAnd(d.link + n, ~(kOwnSolid | kOwnPending));
+      clear_in_neighbours(d, x, y, kUpSolidShift);
+      continue;
+    }
+    // fluid (after this step's flips) in-lattice neighbours s = y - e_j
+    const uint32_t fluid = ~((w >> kUpPostShift) | (w >> kUpOutShift)) & 0xFFu;
+    if (!fluid && !d.check_all) continue;
+    // the per-link amounts are summed in the working precision (FP64
+    // throughput is scarce); the mineral itself is kept in FP64
+    Real take = (Real)0;
 #pragma unroll
-      for (int j = 1; j < 9; ++j) {
-        int sx = x - cx_of(j), sy = y - cy_of(j);
-        if (sx < 0) { if (!d.per_x) continue; sx += d.nx; }
-        else if (sx >= d.nx) { if (!d.per_x) continue; sx -= d.nx; }
-        if (sy < 0) { if (!d.per_y) continue; sy += d.ny; }
-        else if (sy >= d.ny) { if (!d.per_y) continue; sy -= d.ny; }
-        const long long s = (long long)sy * d.pitch + sx;
-        if (solid_post(d.mask[s])) continue;
-        take += w_of(j) * (double)rlink[s];
-        touched = true;
-      }
-      if (touched || d.check_all) {
-        const double m = d.mineral[n] - take;
-        if (touched) d.mineral[n] = m;
-        if (m <= 0.0) {
-          d.flip_list[atomicAdd(d.flip_count, 1)] = (int)n;
-          flipped = true;
-        }
-      }
+    for (int j = 1; j < 9; ++j)
+      if (fluid & (1u << (j - 1)))
+        take += (Real)w_of(j) * rlink[n - cx_of(j) - (long long)cy_of(j) * d.pitch];
+    const double m = d.mineral[n] - (double)take;
+    if (fluid) d.mineral[n] = m;
+    if (m <= 0.0) {
+      d.flip_list[atomicAdd(d.flip_count, 1)] = (int)id;
+      flipped = true;
     }
   }
   // The last block to finish applies the collected flips.  Only threads that
@@ -317,18 +395,21 @@ __global__ void __launch_bounds__(kBX * kBY)
   __shared__ bool last;
   if (flipped) __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0 && threadIdx.y == 0) {
+  if (tid == 0) {
     __threadfence();
     const unsigned ticket = atomicAdd(d.done, 1u);
-    last = (ticket == gridDim.x * gridDim.y - 1);
+    last = (ticket == gridDim.x - 1);
   }
   __syncthreads();
   if (!last) return;
   __threadfence();
   const int cnt = *((volatile int*)d.flip_count);
-  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-  for (int k = tid; k < cnt; k += blockDim.x * blockDim.y)
-    d.mask[((volatile int*)d.flip_list)[k]] = kSolid | kPending;
+  for (int k = tid; k < cnt; k += kDThreads) {
+    const int id = ((volatile int*)d.flip_list)[k];
+    const int x = id % d.nx, y = id / d.nx;
+    atomicOr(d.link + (long long)(y + kYO) * d.pitch + (x + kXO), kOwnPending);
+    clear_in_neighbours(d, x, y, kUpPostShift);
+  }
   __syncthreads();
   if (tid == 0) {
     *d.flips_total += cnt;

@@ -21,18 +21,60 @@ __host__ __device__ constexpr double w_of(int i) {
   return i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
 }
 
-enum : uint8_t {
-  kSolid = 1,    // solid while this step streams (pull / bounce-back)
-  kPending = 2   // turns fluid before this step collides (dissolution)
-};
+// Link word of a node (one uint32 per node).  Byte k of the low three bytes
+// has bit i-1 set for direction i = 1..8 when the upstream neighbour x - e_i
+//   byte 0: is solid while this step streams (pull -> halfway bounce-back),
+//   byte 1: is solid after this step's dissolution flips (reaction, W_s),
+//   byte 2: lies outside the lattice across a non-periodic side (unknown);
+// bit 24 marks the node itself solid while streaming, bit 25 marks a solid
+// node that turns fluid before this step collides (dissolution).  The words
+// change only when a node dissolves, so a step decodes its neighbourhood with
+// bit tests on one word.
+constexpr uint32_t kOwnSolid = 1u << 24;
+constexpr uint32_t kOwnPending = 1u << 25;
+constexpr int kUpSolidShift = 0;
+constexpr int kUpPostShift = 8;
+constexpr int kUpOutShift = 16;
+__host__ __device__ constexpr uint32_t up_bit(int shift, int i) { return 1u << (shift + i - 1); }
+
+// Padded layout of every node field: interior node (x, y) lives at column
+// x + kXO and row y + kYO of a [rows][pitch] array, pitch a multiple of 32
+// with pitch >= nx + 8, rows >= ny + 2.  Column kXO - 1, column nx + kXO,
+// row 0 and row ny + 1 are ghost cells: across a periodic side the population
+// and reaction fields hold there the image of the wrapped node (written
+// through by the node itself).  Four columns on the left keep every tile's
+// halo box 16-byte aligned for TMA, and the minimum sizes (160 columns, 10
+// rows) let one halo box fit the array.
+constexpr int kXO = 4;
+constexpr int kYO = 1;
+
+__host__ __device__ constexpr int padded_pitch(int nx) {
+  return (nx + 8 + 31) / 32 * 32 < 160 ? 160 : (nx + 8 + 31) / 32 * 32;
+}
+__host__ __device__ constexpr int padded_rows(int ny) { return ny + 2 < 10 ? 10 : ny + 2; }
+
+// Calls fn(gx, gy) for every ghost image of interior node (x, y) (padded
+// coordinates), i.e. its copies across periodic sides within one cell of the
+// lattice.
+template <class Fn>
+__device__ __forceinline__ void for_each_ghost(int x, int y, int nx, int ny, int per_x,
+                                               int per_y, Fn&& fn) {
+  const int xs[2] = {x, per_x ? (x == 0 ? nx : (x == nx - 1 ? -1 : x)) : x};
+  const int ys[2] = {y, per_y ? (y == 0 ? ny : (y == ny - 1 ? -1 : y)) : y};
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      if (a == 0 && b == 0) continue;
+      const int gx = xs[a], gy = ys[b];
+      if ((a == 1 && gx == x) || (b == 1 && gy == y)) continue;
+      fn(gx + kXO, gy + kYO);
+    }
+}
 
 enum { kPeriodic = 0, kDirichlet = 1, kNeumann = 2 };
 enum { kReactNone = 0, kReactSurface = 1, kReactBulk = 2 };
 
-// Solid as seen by the collision of the current step (after dissolution).
-__device__ __forceinline__ bool solid_post(uint8_t m) {
-  return (m & kSolid) && !(m & kPending);
-}
 
 // Index of edge node (x, y) of side s in the edge layout [W|E|S|N].
 __device__ __forceinline__ int edge_slot(int s, int x, int y, int nx, int ny) {

@@ -1,0 +1,226 @@
+// lbm_tma.cuh -- the FP32 fused step as a persistent, TMA-fed tile pipeline.
+//
+// One CTA per SM walks the lattice in 128 x 8 node tiles (tile t, t + grid,
+// ...).  For each tile one cp.async.bulk.tensor 3-D box brings all nine
+// population planes with a one-node halo (136 x 10 x 9 floats), and two more
+// bring the velocity (128 x 8 x 2) and the link words (128 x 8), optionally
+// the rate field; an mbarrier per stage counts the bytes in.  Three stages
+// keep two tiles in flight while the CTA updates the third from shared memory
+// with step_node(), which is shared with the generic kernel, and stores f*
+// with coalesced row writes.  Every wait on an mbarrier has an iteration
+// limit: on expiry the CTA records a status, drains its copies in flight
+// (again with a limit) and returns.
+#pragma once
+#include <cuda.h>
+
+#include "lbm_kernels.cuh"
+
+namespace lbm {
+
+constexpr int kTW = 128;           // tile width (nodes)
+constexpr int kTH = 8;             // tile height (rows)
+constexpr int kBoxW = kTW + 8;     // halo box width: 4 columns each side (16 B aligned)
+constexpr int kBoxH = kTH + 2;     // halo box height: one row each side
+constexpr int kStages = 3;
+constexpr int kTmaThreads = 512;   // consumer threads: 16 warps, two per tile row,
+                                   // two nodes per lane (plus one producer warp)
+constexpr long long kSpinLimit = 1ll << 24;
+
+constexpr int round128(int b) { return (b + 127) / 128 * 128; }
+constexpr int kPopBytes = 9 * kBoxH * kBoxW * 4;
+constexpr int kVelBytes = 2 * kTH * kTW * 4;
+constexpr int kKBytes = kTH * kTW * 4;
+constexpr int kWordBytes = kTH * kTW * 4;
+constexpr int kOffVel = round128(kPopBytes);
+constexpr int kOffK = kOffVel + round128(kVelBytes);
+constexpr int kOffWord = kOffK + round128(kKBytes);
+constexpr int kStageBytes = kOffWord + round128(kWordBytes);
+constexpr int kTmaSmem = kStages * kStageBytes;
+static_assert(kTmaSmem <= 227 * 1024, "stages exceed shared memory");
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait; false if the phase did not complete within kSpinLimit polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (long long i = 0; i < kSpinLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0,
+                                            int c1, int c2, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int c0,
+                                            int c1, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// Inputs of one node read from the shared-memory tile of its stage.
+struct SmemSrc {
+  const float* pop;      // [9][kBoxH][kBoxW]
+  const float* vel;      // [2][kTH][kTW]
+  const float* kfield;   // [kTH][kTW]
+  const uint32_t* words; // [kTH][kTW] link words
+  int r, c;              // node's row in the tile, column in the halo box (xl + 4)
+  __device__ __forceinline__ int at(int i) const {  // box offset of x - e_i
+    return (r + 1 - cy_of(i)) * kBoxW + (c - cx_of(i));
+  }
+  __device__ __forceinline__ uint32_t word() const { return words[r * kTW + (c - 4)]; }
+  __device__ __forceinline__ float pull(int i) const { return pop[i * kBoxH * kBoxW + at(i)]; }
+  __device__ __forceinline__ float own(int i) const {
+    return pop[i * kBoxH * kBoxW + (r + 1) * kBoxW + c];
+  }
+  __device__ __forceinline__ float vx() const { return vel[r * kTW + (c - 4)]; }
+  __device__ __forceinline__ float vy() const { return vel[(kTH + r) * kTW + (c - 4)]; }
+  __device__ __forceinline__ float kf() const { return kfield[r * kTW + (c - 4)]; }
+};
+
+struct TmaMaps {
+  CUtensorMap pop;   // fin: [9][rows][pitch] float, box {136, 10, 9}
+  CUtensorMap vel;   // [2][rows][pitch] float, box {128, 8, 2}
+  CUtensorMap link;  // [rows][pitch] uint32 link words, box {128, 8}
+  CUtensorMap kf;    // [rows][pitch] float, box {128, 8} (valid if a.kf)
+};
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// Warp-specialised pipeline: warp 0 is the producer (one lane issues the TMA
+// boxes of tile k into stage k % kStages once all consumer warps have
+// released that stage), warps 1..16 are consumers (each updates its half of
+// one tile row and releases the stage with one arrival).  No CTA-wide barrier
+// sits inside the tile loop.
+template <bool kFinal>
+__global__ void __launch_bounds__(kTmaThreads + 32, 1)
+    lbm_step_tma(const StepArgs<float> a, const __grid_constant__ TmaMaps maps, int ntx,
+                 int nty) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t full[kStages];
+  __shared__ __align__(8) uint64_t empty[kStages];
+  __shared__ double red[kTmaThreads / 32 + 1];
+  __shared__ int abort_flag;
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int ntiles = ntx * nty;
+  const uint32_t bytes = kPopBytes + kVelBytes + kWordBytes + (a.kf ? kKBytes : 0);
+
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kTmaThreads / 32);
+    }
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  double my_u = 0.0;
+  if (warp == 0) {
+    // ---- producer ------------------------------------------------------
+    if (lane == 0) {
+      int k = 0;
+      for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
+        const int s = k % kStages;
+        if (k >= kStages &&
+            !mbar_wait(&empty[s], (uint32_t)(((k / kStages) - 1) & 1))) {
+          atomicExch(&abort_flag, 1);
+          break;
+        }
+        if (*(volatile int*)&abort_flag) break;
+        unsigned char* st = smem + s * kStageBytes;
+        const int x0 = (t % ntx) * kTW, y0 = (t / ntx) * kTH;
+        mbar_expect_tx(&full[s], bytes);
+        tma_load_3d(st, &maps.pop, x0, y0, 0, &full[s]);
+        tma_load_3d(st + kOffVel, &maps.vel, x0 + kXO, y0 + kYO, 0, &full[s]);
+        tma_load_2d(st + kOffWord, &maps.link, x0 + kXO, y0 + kYO, &full[s]);
+        if (a.kf) tma_load_2d(st + kOffK, &maps.kf, x0 + kXO, y0 + kYO, &full[s]);
+      }
+      if (*(volatile int*)&abort_flag) {
+        // drain: every issued box must land before shared memory goes away
+        for (int kk = (k >= kStages ? k - kStages : 0); kk < k; ++kk)
+          (void)mbar_wait(&full[kk % kStages], (uint32_t)((kk / kStages) & 1));
+      }
+    }
+  } else {
+    // ---- consumers ------------------------------------------------------
+    const int cw = warp - 1;                  // 0..15
+    const int r = cw >> 1;                    // tile row of this warp
+    const int cbase = (cw & 1) * 64 + lane;   // first column (of two) of this lane
+    int k = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
+      const int s = k % kStages;
+      if (!mbar_wait(&full[s], (uint32_t)((k / kStages) & 1))) {
+        atomicExch(&abort_flag, 1);
+        break;
+      }
+      if (*(volatile int*)&abort_flag) break;
+      const unsigned char* st = smem + s * kStageBytes;
+      SmemSrc src{(const float*)st, (const float*)(st + kOffVel), (const float*)(st + kOffK),
+                  (const uint32_t*)(st + kOffWord), r, 0};
+      const int x0 = (t % ntx) * kTW, y0 = (t / ntx) * kTH, y = y0 + r;
+      if (box_is_interior(x0, y0, kTW, kTH, a.nx, a.ny)) {
+#pragma unroll 1
+        for (int j = 0; j < 2; ++j) {
+          const int xl = cbase + 32 * j;
+          src.c = xl + 4;
+          const long long n = (long long)(y + kYO) * a.pitch + (x0 + xl + kXO);
+          my_u += step_node<float, kFinal, false>(a, src, x0 + xl, y, n);
+        }
+      } else {
+#pragma unroll 1
+        for (int j = 0; j < 2; ++j) {
+          const int xl = cbase + 32 * j;
+          const int x = x0 + xl;
+          if (x < a.nx && y < a.ny) {
+            src.c = xl + 4;
+            const long long n = (long long)(y + kYO) * a.pitch + (x + kXO);
+            my_u += step_node<float, kFinal, true>(a, src, x, y, n);
+          }
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[s]);
+    }
+  }
+  __syncthreads();
+  if (abort_flag) {
+    if (tid == 0) atomicExch(a.status, 1);
+    return;
+  }
+  if (kFinal) {
+    const double s = block_sum(my_u, red);
+    if (tid == 0) a.partial[blockIdx.x] = s;
+  }
+}
+
+}  // namespace lbm
