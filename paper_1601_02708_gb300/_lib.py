@@ -68,6 +68,7 @@ def load():
             "lbm_set_stream": [P, P],
             "lbm_synchronize": [P],
             "lbm_kernel_timing": [P, I],
+            "lbm_set_kernel": [P, I],
             "lbm_kernel_times_read": [P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong),
                                       ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong)],
         }

@@ -264,7 +264,8 @@ struct lbm_ctx {
   int nedge = 0;
   dim3 grid, block;
   int dgrid = 0;  // persistent blocks of the dissolution pass
-  bool use_tma = false;
+  bool use_tma = false;  // the FP32 step runs the tile pipeline
+  bool tma_ready = false;
   int tma_grid = 0, ntx = 0, nty = 0;
   lbm::TmaMaps maps[2];  // pop map of f[0] / f[1]; other maps identical
   // kernel timing (lbm_kernel_timing): event pairs per launch, folded into
@@ -519,6 +520,7 @@ lbm_status setup_tma(lbm_ctx* c) {
   const int ntiles = c->ntx * c->nty;
   c->tma_grid = ntiles < c->num_sms ? ntiles : c->num_sms;
   c->use_tma = true;
+  c->tma_ready = true;
   return LBM_OK;
 }
 
@@ -537,7 +539,7 @@ lbm_status init_impl(lbm_ctx* c, const uint8_t* solid, const double* vel,
   CK(cudaGetDevice(&c->device));
   CK(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
   {
-    const long long blocks = ((long long)p.nx * p.ny + lbm::kDThreads - 1) / lbm::kDThreads;
+    const long long blocks = (long long)((p.nx + 127) / 128) * ((p.ny + 7) / 8);  // tiles
     const long long cap = 8LL * c->num_sms;  // 8 resident blocks of 256 per SM
     c->dgrid = (int)(blocks < cap ? blocks : cap);
   }
@@ -944,6 +946,24 @@ lbm_status lbm_kernel_times_read(lbm_ctx* c, double* step_ms, long long* step_la
   if (dissolve_ms) *dissolve_ms = c->ms_sum[1];
   if (dissolve_launches) *dissolve_launches = c->launches[1];
   return LBM_OK;
+}
+
+lbm_status lbm_set_kernel(lbm_ctx* c, int variant) {
+  TRY(check_ctx(c));
+  switch (variant) {
+    case LBM_KERNEL_AUTO:
+      c->use_tma = c->tma_ready;
+      return LBM_OK;
+    case LBM_KERNEL_GENERIC:
+      c->use_tma = false;
+      return LBM_OK;
+    case LBM_KERNEL_TMA:
+      if (!c->tma_ready) return fail(LBM_ERR_ARG, "lbm_set_kernel: the tile pipeline is FP32 only");
+      c->use_tma = true;
+      return LBM_OK;
+    default:
+      return fail(LBM_ERR_ARG, "lbm_set_kernel: unknown variant %d", variant);
+  }
 }
 
 lbm_status lbm_set_stream(lbm_ctx* c, void* stream) {

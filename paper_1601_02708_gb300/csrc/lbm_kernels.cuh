@@ -91,7 +91,8 @@ __device__ __forceinline__ void equilibrium(Real (&feq)[9], Real u, Real vx, Rea
 
 // Collision written for the fewest operations: with P_i = 1 + 3 e.v +
 // 4.5 (e.v)^2 - 1.5 v.v, f*_i = (1 - omega) f_i + w_i u (omega P_i - k) for the
-// moving populations, and the rest population takes the remainder
+// moving populations, evaluated per opposite pair (i, opp i), whose P differ
+// only in the sign of 3 e.v; the rest population takes the remainder
 // f*_0 = (1 - k) u - sum_{i>0} f*_i, which is the same value in exact
 // arithmetic (sum_i f*_i = (1 - k) u) and keeps the stored populations
 // summing to the post-reaction mass in FP32.
@@ -100,18 +101,26 @@ __device__ __forceinline__ void collide(Real (&f)[9], Real u, Real vx, Real vy,
                                         Real omega, Real kr) {
   const Real base = (Real)1 - (Real)1.5 * (vx * vx + vy * vy);
   const Real om1 = (Real)1 - omega;
-  const Real wu1 = (Real)w_of(1) * u, wu2 = (Real)w_of(5) * u;
   Real rest = u - kr * u;
 #pragma unroll
-  for (int i = 1; i < 9; ++i) {
+  for (int p = 0; p < 4; ++p) {
+    const int i = p < 2 ? p + 1 : p + 3;  // 1, 2, 5, 6; opposites 3, 4, 7, 8
+    const int o = opp_of(i);
+    const Real wu = (Real)w_of(i) * u;
     const Real ev = (Real)cx_of(i) * vx + (Real)cy_of(i) * vy;
-    const Real P = ev * ((Real)4.5 * ev + (Real)3) + base;
-    const Real g = (i <= 4 ? wu1 : wu2) * (omega * P - kr);
-    f[i] = om1 * f[i] + g;
-    rest -= f[i];
+    const Real sym = wu * (omega * ((Real)4.5 * ev * ev + base) - kr);
+    const Real anti = wu * omega * (Real)3 * ev;
+    f[i] = om1 * f[i] + (sym + anti);
+    f[o] = om1 * f[o] + (sym - anti);
+    rest -= f[i] + f[o];
   }
   f[0] = rest;
 }
+
+// a / b for the reaction split: exact in FP64; the fast reciprocal-based
+// quotient in FP32 (the value only feeds the FP64 mineral sum).
+__device__ __forceinline__ double share(double a, double b) { return a / b; }
+__device__ __forceinline__ float share(float a, float b) { return __fdividef(a, b); }
 
 // Store a node value and, at nodes on a periodic side, its ghost images.
 template <typename Real>
@@ -136,6 +145,11 @@ struct GlobalSrc {
   __device__ __forceinline__ uint32_t word() const { return a.link[n]; }
   __device__ __forceinline__ Real pull(int i) const { return a.fin[i * a.plane + up(i)]; }
   __device__ __forceinline__ Real own(int i) const { return a.fin[i * a.plane + n]; }
+  // pull of direction i, or halfway bounce-back of the node's own opposite
+  // population: one load from the chosen address
+  __device__ __forceinline__ Real pull_or_bounce(int i, bool bounce) const {
+    return a.fin[bounce ? (long long)opp_of(i) * a.plane + n : i * a.plane + up(i)];
+  }
   __device__ __forceinline__ Real vx() const { return a.vel[n]; }
   __device__ __forceinline__ Real vy() const { return a.vel[a.plane + n]; }
   __device__ __forceinline__ Real kf() const { return a.kf[n]; }
@@ -154,13 +168,22 @@ __device__ __forceinline__ double step_node(const StepArgs<Real>& a, const Src& 
   const bool ghosts =
       kEdge && ((x == 0) | (x == a.nx - 1) | (y == 0) | (y == a.ny - 1)) &&
       (a.per_x | a.per_y);
+  // Solid nodes hold no populations, but a solid node whose 32-byte sector
+  // (8 FP32 nodes, aligned since kXO = 8) holds fluid nodes writes zeros, so
+  // every sector the warp touches is written whole.  A node that turns
+  // fluid before this step collides (pending) gets zero populations anyway.
+  const bool solid = (w & kOwnSolid) && !(w & kOwnPending);
+  const unsigned active = __activemask();
+  const unsigned fluid_lanes = __ballot_sync(active, !solid);
+  const unsigned lane = threadIdx.x & 31u;
+  const bool fill = ((fluid_lanes >> (lane & 24u)) & 0xFFu) != 0u;
   if (w & kOwnSolid) {
-    if (w & kOwnPending) {  // became fluid with zero populations
+    if ((w & kOwnPending) || (sizeof(Real) == 4 && fill)) {
 #pragma unroll
       for (int i = 0; i < 9; ++i)
         store_node(a.fout + i * a.plane, n, (Real)0, ghosts, x, y, a.nx, a.ny, a.pitch,
                    a.per_x, a.per_y);
-      if (a.dissolution)
+      if (a.dissolution && (w & kOwnPending))
         store_node(a.ureact, n, (Real)0, ghosts, x, y, a.nx, a.ny, a.pitch, a.per_x,
                    a.per_y);
     }
@@ -170,8 +193,7 @@ __device__ __forceinline__ double step_node(const StepArgs<Real>& a, const Src& 
   Real f[9];
   f[0] = src.own(0);
 #pragma unroll
-  for (int i = 1; i < 9; ++i)
-    f[i] = (w & up_bit(kUpSolidShift, i)) ? src.own(opp_of(i)) : src.pull(i);
+  for (int i = 1; i < 9; ++i) f[i] = src.pull_or_bounce(i, w & up_bit(kUpSolidShift, i));
   if (kEdge) {
     const unsigned unknown = ((w >> kUpOutShift) & 0xFFu) << 1;  // bit i: direction i
     if (unknown) {
@@ -227,8 +249,8 @@ __device__ __forceinline__ double step_node(const StepArgs<Real>& a, const Src& 
   if (a.dissolution && near_solid) {
     const Real wsolid = (Real)__popc(post & 0x0Fu) * (Real)w_of(1) +
                         (Real)__popc(post & 0xF0u) * (Real)w_of(5);
-    store_node(a.ureact, n, kr * u / wsolid, ghosts, x, y, a.nx, a.ny, a.pitch, a.per_x,
-               a.per_y);
+    store_node(a.ureact, n, share(kr * u, wsolid), ghosts, x, y, a.nx, a.ny, a.pitch,
+               a.per_x, a.per_y);
   }
   if (kEdge && x == a.nx - 1) a.jnode[y] += (double)u;
   if (kFinal) a.u_out[n] = u;
@@ -244,7 +266,8 @@ __device__ __forceinline__ bool box_is_interior(int x0, int y0, int w, int h, in
 // Generic step: one thread per node, inputs from global memory.  Used in
 // FP64 mode; the FP32 path runs the TMA kernel instead.
 template <typename Real, bool kFinal>
-__global__ void __launch_bounds__(kBX * kBY) lbm_step(const StepArgs<Real> a) {
+__global__ void __launch_bounds__(kBX * kBY, sizeof(Real) == 4 ? 4 : 4)
+    lbm_step(const StepArgs<Real> a) {
   __shared__ double red[kBX * kBY / 32];
   const int x = blockIdx.x * kBX + threadIdx.x;
   const int y = blockIdx.y * kBY + threadIdx.y;
@@ -361,33 +384,45 @@ __global__ void __launch_bounds__(kDThreads)
     lbm_dissolve(const DissolveArgs d, const Real* __restrict__ rlink) {
   const int tid = threadIdx.x;
   bool flipped = false;
-  const long long total = (long long)d.nx * d.ny;
-  for (long long id = blockIdx.x * (long long)kDThreads + tid; id < total;
-       id += (long long)gridDim.x * kDThreads) {
-    const int y = (int)(id / d.nx), x = (int)(id % d.nx);
-    const long long n = (long long)(y + kYO) * d.pitch + (x + kXO);
-    const uint32_t w = d.link[n];
-    if (!(w & kOwnSolid)) continue;
-    if (w & kOwnPending) {
-      atomicAnd(d.link + n, ~(kOwnSolid | kOwnPending));
-      clear_in_neighbours(d, x, y, kUpSolidShift);
-      continue;
-    }
-    // fluid (after this step's flips) in-lattice neighbours s = y - e_j
-    const uint32_t fluid = ~((w >> kUpPostShift) | (w >> kUpOutShift)) & 0xFFu;
-    if (!fluid && !d.check_all) continue;
-    // the per-link amounts are summed in the working precision (FP64
-    // throughput is scarce); the mineral itself is kept in FP64
-    Real take = (Real)0;
+  // persistent blocks walk 128 x 8 tiles; a thread takes four nodes of its
+  // row 32 apart and loads their link words before using any of them
+  const int ntx = (d.nx + 127) >> 7, ntiles = ntx * ((d.ny + 7) >> 3);
+  const int ty = tid >> 5, tx = tid & 31;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int y = (t / ntx) * 8 + ty, xb = (t % ntx) * 128 + tx;
+    if (y >= d.ny) continue;
+    const long long row = (long long)(y + kYO) * d.pitch + kXO;
+    uint32_t w4[4];
 #pragma unroll
-    for (int j = 1; j < 9; ++j)
-      if (fluid & (1u << (j - 1)))
-        take += (Real)w_of(j) * rlink[n - cx_of(j) - (long long)cy_of(j) * d.pitch];
-    const double m = d.mineral[n] - (double)take;
-    if (fluid) d.mineral[n] = m;
-    if (m <= 0.0) {
-      d.flip_list[atomicAdd(d.flip_count, 1)] = (int)id;
-      flipped = true;
+    for (int j = 0; j < 4; ++j) w4[j] = (xb + 32 * j < d.nx) ? d.link[row + xb + 32 * j] : 0u;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t w = w4[j];
+      if (!(w & kOwnSolid)) continue;
+      const int x = xb + 32 * j;
+      const long long n = row + x;
+      const int id = y * d.nx + x;
+      if (w & kOwnPending) {
+        atomicAnd(d.link + n, ~(kOwnSolid | kOwnPending));
+        clear_in_neighbours(d, x, y, kUpSolidShift);
+        continue;
+      }
+      // fluid (after this step's flips) in-lattice neighbours s = y - e_j
+      const uint32_t fluid = ~((w >> kUpPostShift) | (w >> kUpOutShift)) & 0xFFu;
+      if (!fluid && !d.check_all) continue;
+      // the per-link amounts are summed in the working precision (FP64
+      // throughput is scarce); the mineral itself is kept in FP64
+      Real take = (Real)0;
+#pragma unroll
+      for (int jj = 1; jj < 9; ++jj)
+        if (fluid & (1u << (jj - 1)))
+          take += (Real)w_of(jj) * rlink[n - cx_of(jj) - (long long)cy_of(jj) * d.pitch];
+      const double m = d.mineral[n] - (double)take;
+      if (fluid) d.mineral[n] = m;
+      if (m <= 0.0) {
+        d.flip_list[atomicAdd(d.flip_count, 1)] = id;
+        flipped = true;
+      }
     }
   }
   // The last block to finish applies the collected flips.  Only threads that

@@ -39,17 +39,18 @@ __host__ __device__ constexpr uint32_t up_bit(int shift, int i) { return 1u << (
 
 // Padded layout of every node field: interior node (x, y) lives at column
 // x + kXO and row y + kYO of a [rows][pitch] array, pitch a multiple of 32
-// with pitch >= nx + 8, rows >= ny + 2.  Column kXO - 1, column nx + kXO,
+// with pitch >= nx + 16, rows >= ny + 2.  Column kXO - 1, column nx + kXO,
 // row 0 and row ny + 1 are ghost cells: across a periodic side the population
 // and reaction fields hold there the image of the wrapped node (written
-// through by the node itself).  Four columns on the left keep every tile's
-// halo box 16-byte aligned for TMA, and the minimum sizes (160 columns, 10
-// rows) let one halo box fit the array.
-constexpr int kXO = 4;
+// through by the node itself).  Eight columns on the left put interior
+// x = 0 on a 32-byte sector boundary (8 consecutive FP32 nodes per sector)
+// and keep every tile's halo box 16-byte aligned for TMA; the minimum sizes
+// (160 columns, 10 rows) let one halo box fit the array.
+constexpr int kXO = 8;
 constexpr int kYO = 1;
 
 __host__ __device__ constexpr int padded_pitch(int nx) {
-  return (nx + 8 + 31) / 32 * 32 < 160 ? 160 : (nx + 8 + 31) / 32 * 32;
+  return (nx + 16 + 31) / 32 * 32 < 160 ? 160 : (nx + 16 + 31) / 32 * 32;
 }
 __host__ __device__ constexpr int padded_rows(int ny) { return ny + 2 < 10 ? 10 : ny + 2; }
 

@@ -99,6 +99,10 @@ struct SmemSrc {
   __device__ __forceinline__ float own(int i) const {
     return pop[i * kBoxH * kBoxW + (r + 1) * kBoxW + c];
   }
+  __device__ __forceinline__ float pull_or_bounce(int i, bool bounce) const {
+    return pop[bounce ? opp_of(i) * kBoxH * kBoxW + (r + 1) * kBoxW + c
+                      : i * kBoxH * kBoxW + at(i)];
+  }
   __device__ __forceinline__ float vx() const { return vel[r * kTW + (c - 4)]; }
   __device__ __forceinline__ float vy() const { return vel[(kTH + r) * kTW + (c - 4)]; }
   __device__ __forceinline__ float kf() const { return kfield[r * kTW + (c - 4)]; }
@@ -160,7 +164,7 @@ __global__ void __launch_bounds__(kTmaThreads + 32, 1)
         unsigned char* st = smem + s * kStageBytes;
         const int x0 = (t % ntx) * kTW, y0 = (t / ntx) * kTH;
         mbar_expect_tx(&full[s], bytes);
-        tma_load_3d(st, &maps.pop, x0, y0, 0, &full[s]);
+        tma_load_3d(st, &maps.pop, x0 + kXO - 4, y0, 0, &full[s]);
         tma_load_3d(st + kOffVel, &maps.vel, x0 + kXO, y0 + kYO, 0, &full[s]);
         tma_load_2d(st + kOffWord, &maps.link, x0 + kXO, y0 + kYO, &full[s]);
         if (a.kf) tma_load_2d(st + kOffK, &maps.kf, x0 + kXO, y0 + kYO, &full[s]);

@@ -161,6 +161,13 @@ class LBM:
         check(self._lib.lbm_substeps(self.handle, int(n), int(eta), a, b, q))
         self._keep = keep  # device inputs stay referenced until the next call
 
+    KERNELS = {"auto": 0, "generic": 1, "tma": 2}
+
+    def set_kernel(self, variant="auto"):
+        """Step kernel: "auto", "generic" (thread per node) or "tma" (FP32
+        tile pipeline); every variant computes the same update."""
+        check(self._lib.lbm_set_kernel(self.handle, self.KERNELS[variant]))
+
     def kernel_timing(self, enable=True):
         """Record CUDA events around every step and dissolution launch."""
         check(self._lib.lbm_kernel_timing(self.handle, int(bool(enable))))

@@ -70,12 +70,13 @@ def test_periodic_reactive_fourier_lattice(gb, oracle_mod, prec):
     assert abs(d["mass"] - ref.diag()["mass"]) <= TOL[prec] * ref.diag()["mass"]
 
 
-@pytest.mark.parametrize("prec", [64, 32])
-@pytest.mark.parametrize("shape", [(97, 61), (33, 9), (128, 64)])
-def test_porous_dissolution_parity(gb, oracle_mod, prec, shape):
+@pytest.mark.parametrize("prec,kernel", [(64, "auto"), (32, "tma"), (32, "generic")])
+@pytest.mark.parametrize("shape", [(97, 61), (33, 9), (128, 64), (300, 37)])
+def test_porous_dissolution_parity(gb, oracle_mod, prec, kernel, shape):
     """Disks, stream-function velocity, surface reaction with dissolution
     (mineral small enough that nodes flip), Dirichlet inlet, Neumann outlet,
-    periodic y; ragged shapes that leave partial tiles."""
+    periodic y; ragged shapes that leave partial tiles, interior tiles
+    (300 x 37) and lattices smaller than one tile; both FP32 step kernels."""
     nx, ny = shape
     steps = 150
     kw = _porous(nx, ny, seed=nx * 7 + ny)
@@ -84,6 +85,7 @@ def test_porous_dissolution_parity(gb, oracle_mod, prec, shape):
     ref = oracle_mod.LBMOracle(nx, ny, 0.7, **kw)
     ref.substeps(steps, 1, ud, ud, q)
     lat = gb.LBM(nx, ny, 0.7, precision=prec, **kw)
+    lat.set_kernel(kernel)
     lat.substeps(steps, 1, ud, ud, q)
     d_ref = ref.diag()
     u_ref, solid_ref, fpost_ref = ref.u(), ref.solid(), ref.fpost()
@@ -106,7 +108,7 @@ def test_porous_dissolution_parity(gb, oracle_mod, prec, shape):
         # infeasible Neumann solves (R > 0 by a hair) is only comparable in FP64
         assert d["bc_infeasible"] == d_ref["bc_infeasible"]
     assert d["flips"] == ref.diag()["flips"]  # flips decided one step ahead
-    if shape == (97, 61):
+    if shape in ((97, 61), (300, 37)):
         assert d["flips"] > 0
 
 
@@ -258,6 +260,8 @@ def test_edge_cases(gb, oracle_mod):
         gb.LBM(1, 8, 0.8)
     with pytest.raises(gb.LBMError):
         lat.substeps(-1)
+    with pytest.raises(gb.LBMError):
+        lat.set_kernel("tma")  # the tile pipeline is FP32 only
 
 
 def test_full_size_lattice_sampled_parity(gb, oracle_mod):
