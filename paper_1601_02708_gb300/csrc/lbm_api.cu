@@ -254,7 +254,9 @@ struct lbm_ctx {
   double* partial = nullptr;        // [max(blocks)]
   int nparts = 0;                   // partials written by the last final step
   int* flip_list = nullptr;
-  int* flip_count = nullptr;      // [0] count, [1] done counter
+  int* flip_count = nullptr;      // [0] count, [1] done counter, [2] surface list length
+  int* slist = nullptr;           // dissolution surface list (padded node indices)
+  double* smin = nullptr;         // mineral of the listed nodes
   long long* counters = nullptr;  // [0] flips total, [1] solid count at init
   int* status = nullptr;          // device error word
   DiagDev* diag = nullptr;
@@ -319,6 +321,9 @@ lbm::DissolveArgs dissolve_args(lbm_ctx* c) {
   d.flip_list = c->flip_list;
   d.flip_count = c->flip_count;
   d.done = (unsigned*)(c->flip_count + 1);
+  d.scount = c->flip_count + 2;
+  d.slist = c->slist;
+  d.smin = c->smin;
   d.flips_total = c->counters;
   d.nx = c->p.nx;
   d.ny = c->p.ny;
@@ -362,14 +367,34 @@ lbm_status time_end(lbm_ctx* c, int which) {
 }
 
 template <typename Real>
-lbm_status launch_dissolve(lbm_ctx* c, bool check_all = false) {
+lbm_status launch_dissolve(lbm_ctx* c) {
   TRY(time_begin(c, 1));
-  lbm::DissolveArgs d = dissolve_args(c);
-  d.check_all = check_all ? 1 : 0;
-  lbm::lbm_dissolve<Real><<<c->dgrid, lbm::kDThreads, 0, c->stream>>>(
-      d, (const Real*)c->ureact);
+  lbm::lbm_dissolve_list<Real><<<c->dgrid, lbm::kDThreads, 0, c->stream>>>(
+      dissolve_args(c), (const Real*)c->ureact);
   CK(cudaGetLastError());
   return time_end(c, 1);
+}
+
+// First dissolution pass after initialisation: over every node (it also
+// flips solid nodes given no mineral), then the surface list is built.
+template <typename Real>
+lbm_status first_dissolve(lbm_ctx* c) {
+  lbm::DissolveArgs d = dissolve_args(c);
+  d.check_all = 1;
+  lbm::lbm_dissolve_dense<Real><<<c->dgrid, lbm::kDThreads, 0, c->stream>>>(
+      d, (const Real*)c->ureact);
+  CK(cudaGetLastError());
+  lbm::lbm_list_build<<<c->dgrid, lbm::kDThreads, 0, c->stream>>>(dissolve_args(c));
+  CK(cudaGetLastError());
+  return LBM_OK;
+}
+
+// Dense mineral array up to date (the listed nodes keep theirs on the list).
+lbm_status sync_mineral(lbm_ctx* c) {
+  if (!c->p.dissolution) return LBM_OK;
+  lbm::lbm_list_scatter<<<c->dgrid, lbm::kDThreads, 0, c->stream>>>(dissolve_args(c));
+  CK(cudaGetLastError());
+  return LBM_OK;
 }
 
 template <typename Real>
@@ -431,8 +456,7 @@ lbm_status run_init(lbm_ctx* c, const double* u0dev) {
   CK(cudaGetLastError());
   c->nparts = (int)(c->grid.x * c->grid.y);
   c->cur = 0;
-  // the first pass also flips solid nodes given with no mineral at all
-  if (c->p.dissolution) return launch_dissolve<Real>(c, true);
+  if (c->p.dissolution) return first_dissolve<Real>(c);
   return LBM_OK;
 }
 
@@ -461,7 +485,7 @@ void free_ctx(lbm_ctx* c) {
   void* ptrs[] = {c->f[0],   c->f[1],     c->link,      c->vel,        c->kf,
                   c->u,      c->ureact,   c->mineral,   c->edge,       c->infeasible,
                   c->jnode,  c->partial,  c->flip_list, c->flip_count, c->counters,
-                  c->status, c->diag,     c->scratch};
+                  c->status, c->diag,     c->scratch,   c->slist,      c->smin};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c;
@@ -539,7 +563,7 @@ lbm_status init_impl(lbm_ctx* c, const uint8_t* solid, const double* vel,
   CK(cudaGetDevice(&c->device));
   CK(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
   {
-    const long long blocks = (long long)((p.nx + 127) / 128) * ((p.ny + 7) / 8);  // tiles
+    const long long blocks = ((long long)p.nx * p.ny + lbm::kDThreads - 1) / lbm::kDThreads;
     const long long cap = 8LL * c->num_sms;  // 8 resident blocks of 256 per SM
     c->dgrid = (int)(blocks < cap ? blocks : cap);
   }
@@ -563,6 +587,8 @@ lbm_status init_impl(lbm_ctx* c, const uint8_t* solid, const double* vel,
     CK(cudaMalloc((void**)&c->mineral, (size_t)c->plane * sizeof(double)));
     CK(cudaMemsetAsync(c->mineral, 0, (size_t)c->plane * sizeof(double), c->stream));
     CK(cudaMalloc((void**)&c->flip_list, nxy * sizeof(int)));
+    CK(cudaMalloc((void**)&c->slist, nxy * sizeof(int)));
+    CK(cudaMalloc((void**)&c->smin, nxy * sizeof(double)));
   }
   CK(cudaMalloc((void**)&c->flip_count, 4 * sizeof(int)));
   CK(cudaMemsetAsync(c->flip_count, 0, 4 * sizeof(int), c->stream));
@@ -669,7 +695,13 @@ int state_sections(lbm_ctx* c, Section* s) {
   s[k++] = {c->jnode, (size_t)c->p.ny * sizeof(double)};
   s[k++] = {c->partial, (size_t)c->grid.x * c->grid.y * sizeof(double)};
   s[k++] = {c->counters, 4 * sizeof(long long)};
-  if (c->p.dissolution) s[k++] = {c->mineral, (size_t)c->plane * sizeof(double)};
+  if (c->p.dissolution) {
+    const size_t nxy = (size_t)c->p.nx * c->p.ny;
+    s[k++] = {c->mineral, (size_t)c->plane * sizeof(double)};
+    s[k++] = {c->flip_count, 4 * sizeof(int)};
+    s[k++] = {c->slist, nxy * sizeof(int)};
+    s[k++] = {c->smin, nxy * sizeof(double)};
+  }
   return k;
 }
 size_t align256(size_t b) { return (b + 255) / 256 * 256; }
@@ -678,7 +710,7 @@ struct BlobHeader {
   long long steps;
   int nx, ny, precision, dissolution, nparts, pad;
 };
-const unsigned long long kMagic = 0x4C424D4144453033ull;  // "LBMADE03"
+const unsigned long long kMagic = 0x4C424D4144453034ull;  // "LBMADE04"
 
 // Copy a padded device field out to a caller array (host or device) of
 // `planes` [ny][nx] planes, converting to O.
@@ -844,6 +876,7 @@ lbm_status lbm_get_mineral(lbm_ctx* c, double* out) {
   TRY(check_ctx(c));
   if (!out) return fail(LBM_ERR_ARG, "lbm_get_mineral: null out");
   if (!c->p.dissolution) return fail(LBM_ERR_STATE, "lbm_get_mineral: dissolution is off");
+  TRY(sync_mineral(c));
   TRY(field_out<double, double>(c, c->mineral, out, 1));
   return check_status(c);
 }
@@ -886,6 +919,7 @@ lbm_status lbm_save(lbm_ctx* c, void* buf, size_t bytes) {
   if (!buf || bytes < need) return fail(LBM_ERR_ARG, "lbm_save: buffer smaller than lbm_state_bytes");
   const bool dev = on_device(buf);
   const cudaMemcpyKind k = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  TRY(sync_mineral(c));
   BlobHeader h{kMagic, c->steps, c->p.nx, c->p.ny, c->p.precision, c->p.dissolution, c->nparts, 0};
   CK(cudaMemcpyAsync(buf, &h, sizeof(h), dev ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost,
                      c->stream));

@@ -335,14 +335,36 @@ __global__ void __launch_bounds__(kBX * kBY)
 
 struct DissolveArgs {
   uint32_t* link;
-  double* mineral;
-  int* flip_list;
+  double* mineral;       // dense [rows][pitch] mineral (nodes not on the list)
+  int* slist;            // surface list: padded node index per entry
+  double* smin;          // surface list: mineral per entry
+  int* scount;           // surface list length
+  int* flip_list;        // padded indices of nodes found exhausted this pass
   int* flip_count;
   unsigned* done;
   long long* flips_total;
   int nx, ny, pitch, per_x, per_y;
   int check_all;  // also flip untouched solid nodes whose mineral is <= 0
 };
+
+__device__ __forceinline__ void node_xy(const DissolveArgs& d, int n, int& x, int& y) {
+  y = n / d.pitch - kYO;
+  x = n - (y + kYO) * d.pitch - kXO;
+}
+
+// Padded index of the in-lattice neighbour z = (x, y) + e_i, or -1.
+__device__ __forceinline__ int neighbour(const DissolveArgs& d, int x, int y, int i) {
+  int zx = x + cx_of(i), zy = y + cy_of(i);
+  if (zx < 0 || zx >= d.nx) {
+    if (!d.per_x) return -1;
+    zx = zx < 0 ? zx + d.nx : zx - d.nx;
+  }
+  if (zy < 0 || zy >= d.ny) {
+    if (!d.per_y) return -1;
+    zy = zy < 0 ? zy + d.ny : zy - d.ny;
+  }
+  return (zy + kYO) * d.pitch + (zx + kXO);
+}
 
 // Atomically clear bit `shift + i - 1` in the link word of every in-lattice
 // neighbour z = y + e_i of node (x, y), i.e. the bit that describes y as z's
@@ -351,99 +373,51 @@ __device__ __forceinline__ void clear_in_neighbours(const DissolveArgs& d, int x
                                                     int shift) {
 #pragma unroll
   for (int i = 1; i < 9; ++i) {
-    int zx = x + cx_of(i), zy = y + cy_of(i);
-    if (zx < 0 || zx >= d.nx) {
-      if (!d.per_x) continue;
-      zx = zx < 0 ? zx + d.nx : zx - d.nx;
-    }
-    if (zy < 0 || zy >= d.ny) {
-      if (!d.per_y) continue;
-      zy = zy < 0 ? zy + d.ny : zy - d.ny;
-    }
-    atomicAnd(d.link + (long long)(zy + kYO) * d.pitch + (zx + kXO), ~up_bit(shift, i));
+    const int z = neighbour(d, x, y, i);
+    if (z >= 0) atomicAnd(d.link + z, ~up_bit(shift, i));
   }
 }
 
-// Dissolution after a step: every solid node y gathers the mineral it loses,
-//   m(y) -= sum_j w_j r(s),  s = y - e_j a fluid neighbour,
-// where the step stored r(s) = k(s) u(s) / W_s(s) at every fluid node with a
-// solid neighbour (W_s = sum of the weights of s's links to solid nodes), so
-// the node's sink k u is shared among its solid links in proportion to w_j.
-// The order of the sum is fixed: the result is deterministic.  Nodes that
-// turned fluid before this step's collision (pending) become plain fluid and
-// stop being solid upstream for their neighbours; nodes whose mineral is
-// used up are collected and, by the last block to finish, marked pending:
-// solid for the next step's streaming, fluid (with zero populations) for its
-// collision, which their neighbours learn through their post-flip bits.
-// Link-word edits are atomic bit operations on disjoint bits of concurrently
-// read words, so no reader sees a bit it depends on change.
-constexpr int kDThreads = 256;
-
+// Mineral lost by solid node n this step (word w): sum over its fluid
+// (after this step's flips) in-lattice neighbours s = y - e_j of w_j r(s),
+// r(s) = k(s) u(s) / W_s(s) stored by the step.  Summed in the working
+// precision in a fixed order; FP64 throughput is scarce and the result only
+// enters the FP64 mineral.
 template <typename Real>
-__global__ void __launch_bounds__(kDThreads)
-    lbm_dissolve(const DissolveArgs d, const Real* __restrict__ rlink) {
-  const int tid = threadIdx.x;
-  bool flipped = false;
-  // persistent blocks walk 128 x 8 tiles; a thread takes four nodes of its
-  // row 32 apart and loads their link words before using any of them
-  const int ntx = (d.nx + 127) >> 7, ntiles = ntx * ((d.ny + 7) >> 3);
-  const int ty = tid >> 5, tx = tid & 31;
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int y = (t / ntx) * 8 + ty, xb = (t % ntx) * 128 + tx;
-    if (y >= d.ny) continue;
-    const long long row = (long long)(y + kYO) * d.pitch + kXO;
-    uint32_t w4[4];
+__device__ __forceinline__ Real mineral_take(const Real* __restrict__ rlink, long long n,
+                                             int pitch, uint32_t fluid) {
+  Real take = (Real)0;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) w4[j] = (xb + 32 * j < d.nx) ? d.link[row + xb + 32 * j] : 0u;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const uint32_t w = w4[j];
-      if (!(w & kOwnSolid)) continue;
-      const int x = xb + 32 * j;
-      const long long n = row + x;
-      const int id = y * d.nx + x;
-      if (w & kOwnPending) {
-        atomicAnd(d.link + n, ~(kOwnSolid | kOwnPending));
-        clear_in_neighbours(d, x, y, kUpSolidShift);
-        continue;
-      }
-      // fluid (after this step's flips) in-lattice neighbours s = y - e_j
-      const uint32_t fluid = ~((w >> kUpPostShift) | (w >> kUpOutShift)) & 0xFFu;
-      if (!fluid && !d.check_all) continue;
-      // the per-link amounts are summed in the working precision (FP64
-      // throughput is scarce); the mineral itself is kept in FP64
-      Real take = (Real)0;
-#pragma unroll
-      for (int jj = 1; jj < 9; ++jj)
-        if (fluid & (1u << (jj - 1)))
-          take += (Real)w_of(jj) * rlink[n - cx_of(jj) - (long long)cy_of(jj) * d.pitch];
-      const double m = d.mineral[n] - (double)take;
-      if (fluid) d.mineral[n] = m;
-      if (m <= 0.0) {
-        d.flip_list[atomicAdd(d.flip_count, 1)] = id;
-        flipped = true;
-      }
-    }
-  }
-  // The last block to finish applies the collected flips.  Only threads that
-  // appended to the list need their write ordered before the block's ticket.
-  __shared__ bool last;
-  if (flipped) __threadfence();
-  __syncthreads();
-  if (tid == 0) {
-    __threadfence();
-    const unsigned ticket = atomicAdd(d.done, 1u);
-    last = (ticket == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (!last) return;
+  for (int j = 1; j < 9; ++j)
+    if (fluid & (1u << (j - 1)))
+      take += (Real)w_of(j) * rlink[n - cx_of(j) - (long long)cy_of(j) * pitch];
+  return take;
+}
+
+// Mark every node of the flip list pending (solid for the next streaming,
+// fluid for its collision), tell its neighbours through their post-flip bits,
+// and put solid neighbours it exposes on the surface list.  Run by one block
+// after every node has been examined.
+__device__ void apply_flips(const DissolveArgs& d, int tid, int nthreads) {
   __threadfence();
   const int cnt = *((volatile int*)d.flip_count);
-  for (int k = tid; k < cnt; k += kDThreads) {
-    const int id = ((volatile int*)d.flip_list)[k];
-    const int x = id % d.nx, y = id / d.nx;
-    atomicOr(d.link + (long long)(y + kYO) * d.pitch + (x + kXO), kOwnPending);
-    clear_in_neighbours(d, x, y, kUpPostShift);
+  for (int k = tid; k < cnt; k += nthreads) {
+    const int n = ((volatile int*)d.flip_list)[k];
+    int x, y;
+    node_xy(d, n, x, y);
+    atomicOr(d.link + n, kOwnPending);
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+      const int z = neighbour(d, x, y, i);
+      if (z < 0) continue;
+      const uint32_t old = atomicAnd(d.link + z, ~up_bit(kUpPostShift, i));
+      if ((old & kOwnSolid) && !(old & kListed) &&
+          !(atomicOr(d.link + z, kListed) & kListed)) {
+        const int slot = atomicAdd(d.scount, 1);
+        d.slist[slot] = z;
+        d.smin[slot] = d.mineral[z];
+      }
+    }
   }
   __syncthreads();
   if (tid == 0) {
@@ -451,6 +425,118 @@ __global__ void __launch_bounds__(kDThreads)
     *d.flip_count = 0;
     *d.done = 0u;
   }
+}
+
+// Dissolution after a step, for the solid nodes on the surface list: each
+// gathers the mineral it loses (mineral_take); nodes that turned fluid
+// before this step's collision (pending) become plain fluid and stop being
+// solid upstream for their neighbours; nodes whose mineral is used up are
+// collected and, by the last block to finish, marked pending (apply_flips).
+// Link-word edits are atomic bit operations on bits no concurrent reader of
+// the same word depends on, so the result is independent of timing.
+constexpr int kDThreads = 256;
+
+template <typename Real>
+__global__ void __launch_bounds__(kDThreads)
+    lbm_dissolve_list(const DissolveArgs d, const Real* __restrict__ rlink) {
+  const int tid = threadIdx.x;
+  bool flipped = false;
+  const int count = *d.scount;
+  for (int e = blockIdx.x * kDThreads + tid; e < count; e += gridDim.x * kDThreads) {
+    const int n = d.slist[e];
+    const uint32_t w = d.link[n];
+    if (!(w & kOwnSolid)) continue;  // dissolved earlier
+    if (w & kOwnPending) {
+      int x, y;
+      node_xy(d, n, x, y);
+      atomicAnd(d.link + n, ~(kOwnSolid | kOwnPending | kListed));
+      clear_in_neighbours(d, x, y, kUpSolidShift);
+      continue;
+    }
+    const uint32_t fluid = ~((w >> kUpPostShift) | (w >> kUpOutShift)) & 0xFFu;
+    if (!fluid) continue;
+    const double m = d.smin[e] - (double)mineral_take(rlink, n, d.pitch, fluid);
+    d.smin[e] = m;
+    if (m <= 0.0) {
+      d.flip_list[atomicAdd(d.flip_count, 1)] = n;
+      flipped = true;
+    }
+  }
+  __shared__ bool last;
+  if (flipped) __threadfence();
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    last = (atomicAdd(d.done, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last) apply_flips(d, tid, kDThreads);
+}
+
+// Dissolution pass over every node (used once, after initialisation): the
+// same update as lbm_dissolve_list for surface nodes, and with check_all set
+// it also flips solid nodes given no mineral.  The mineral is the dense array.
+template <typename Real>
+__global__ void __launch_bounds__(kDThreads)
+    lbm_dissolve_dense(const DissolveArgs d, const Real* __restrict__ rlink) {
+  const int tid = threadIdx.x;
+  bool flipped = false;
+  const long long total = (long long)d.nx * d.ny;
+  for (long long id = blockIdx.x * (long long)kDThreads + tid; id < total;
+       id += (long long)gridDim.x * kDThreads) {
+    const int y = (int)(id / d.nx), x = (int)(id - (long long)y * d.nx);
+    const int n = (y + kYO) * d.pitch + (x + kXO);
+    const uint32_t w = d.link[n];
+    if (!(w & kOwnSolid)) continue;
+    if (w & kOwnPending) {
+      atomicAnd(d.link + n, ~(kOwnSolid | kOwnPending | kListed));
+      clear_in_neighbours(d, x, y, kUpSolidShift);
+      continue;
+    }
+    const uint32_t fluid = ~((w >> kUpPostShift) | (w >> kUpOutShift)) & 0xFFu;
+    if (!fluid && !d.check_all) continue;
+    const double m = d.mineral[n] - (double)mineral_take(rlink, n, d.pitch, fluid);
+    if (fluid) d.mineral[n] = m;
+    if (m <= 0.0) {
+      d.flip_list[atomicAdd(d.flip_count, 1)] = n;
+      flipped = true;
+    }
+  }
+  __shared__ bool last;
+  if (flipped) __threadfence();
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    last = (atomicAdd(d.done, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last) apply_flips(d, tid, kDThreads);
+}
+
+// Build the surface list: every solid node with a fluid in-lattice neighbour
+// (or pending) that is not listed yet; its mineral moves to the list.
+__global__ void __launch_bounds__(kDThreads) lbm_list_build(const DissolveArgs d) {
+  const long long total = (long long)d.nx * d.ny;
+  for (long long id = blockIdx.x * (long long)kDThreads + threadIdx.x; id < total;
+       id += (long long)gridDim.x * kDThreads) {
+    const int y = (int)(id / d.nx), x = (int)(id - (long long)y * d.nx);
+    const int n = (y + kYO) * d.pitch + (x + kXO);
+    const uint32_t w = d.link[n];
+    if (!(w & kOwnSolid) || (w & kListed)) continue;
+    const uint32_t fluid = ~((w >> kUpPostShift) | (w >> kUpOutShift)) & 0xFFu;
+    if (!fluid && !(w & kOwnPending)) continue;
+    d.link[n] = w | kListed;
+    const int slot = atomicAdd(d.scount, 1);
+    d.slist[slot] = n;
+    d.smin[slot] = d.mineral[n];
+  }
+}
+
+// Write the list's minerals back into the dense array (before read-out).
+__global__ void lbm_list_scatter(const DissolveArgs d) {
+  const int count = *d.scount;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x)
+    d.mineral[d.slist[e]] = d.smin[e];
 }
 
 }  // namespace lbm

@@ -27,11 +27,13 @@ __host__ __device__ constexpr double w_of(int i) {
 //   byte 1: is solid after this step's dissolution flips (reaction, W_s),
 //   byte 2: lies outside the lattice across a non-periodic side (unknown);
 // bit 24 marks the node itself solid while streaming, bit 25 marks a solid
-// node that turns fluid before this step collides (dissolution).  The words
+// node that turns fluid before this step collides (dissolution), bit 26 a
+// solid node on the dissolution surface list.  The words
 // change only when a node dissolves, so a step decodes its neighbourhood with
 // bit tests on one word.
 constexpr uint32_t kOwnSolid = 1u << 24;
 constexpr uint32_t kOwnPending = 1u << 25;
+constexpr uint32_t kListed = 1u << 26;  // solid node on the dissolution surface list
 constexpr int kUpSolidShift = 0;
 constexpr int kUpPostShift = 8;
 constexpr int kUpOutShift = 16;
