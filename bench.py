@@ -35,8 +35,10 @@ if ROOT not in sys.path:
 
 METRIC = "LBM-ADE GLUPS & % HBM roofline (FP32 vs FP64); adjoint/forward time ratio"
 # Algorithmic bytes of the fused step per node and launch: a fluid node reads
-# and writes 9 populations, reads 2 velocity components and its mask byte; a
-# solid node costs its mask byte.
+# and writes 9 populations, reads 2 velocity components and one byte of solid
+# flag; a solid node costs its flag byte.  (The library stores the flag in a
+# 4-byte word that also encodes the neighbourhood; the algorithmic count keeps
+# the information content.)
 BYTES_FLUID = {32: 9 * 4 * 2 + 2 * 4 + 1, 64: 9 * 8 * 2 + 2 * 8 + 1}
 BYTES_SOLID = 1
 
@@ -258,9 +260,10 @@ def main():
     try:
         from paper_1601_02708_gb300 import build as _b
         import hashlib
+        import glob
         h = hashlib.sha256()
-        for src in sorted(_b.sources()) + [os.path.join(_b.CSRC, "lbm_kernels.cuh"),
-                                           os.path.join(_b.CSRC, "lbm_lattice.cuh")]:
+        for src in sorted(glob.glob(os.path.join(_b.CSRC, "*.cu")) +
+                          glob.glob(os.path.join(_b.CSRC, "*.cuh"))):
             h.update(open(src, "rb").read())
         rec = json.load(open(tpath))
         if rec.get("source_sha256") == h.hexdigest():
