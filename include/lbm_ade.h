@@ -174,6 +174,30 @@ lbm_status lbm_set_kernel(lbm_ctx* c, int variant);
 lbm_status lbm_set_stream(lbm_ctx* c, void* stream);
 lbm_status lbm_synchronize(lbm_ctx* c);
 
+/* FP64 sum of a concentration field that allocates nothing -- the paper has
+ * no counterpart; this entry point exists for callers that cannot allocate
+ * device memory when they need the sum: code recording a CUDA graph (an
+ * allocation cannot be captured), code running inside a device-memory budget
+ * fixed at start-up, or a host framework that owns every allocation.
+ *   u          device pointer to n values (float if precision is 32, double
+ *              if 64), e.g. the [ny][nx] field of lbm_get_concentration
+ *   n          1 .. 67,108,864 (8192 x 8192 nodes); larger n -> LBM_ERR_ARG
+ *   mass_out   host or device pointer to one double; a host result is
+ *              complete when the call returns, a device result is ordered on
+ *              `stream`
+ *   stream     cudaStream_t of the work (NULL: legacy default stream)
+ * The partial sums live in a fixed 64 KB array in the library's device
+ * memory (every GPU that loads the library keeps it until the process exits);
+ * the sum is taken in a fixed order, so repeated calls give identical
+ * results.  The first call on a device looks up that array's device address
+ * (with that device current), so make one call before recording any stream
+ * capture.  All calls on a device share the array: calls that overlap on the
+ * GPU (different streams without ordering between them) race.  On error,
+ * lbm_mass_noalloc_error() describes it (per thread). */
+lbm_status lbm_mass_noalloc(const void* u, int precision, long long n, double* mass_out,
+                            void* stream);
+const char* lbm_mass_noalloc_error(void);
+
 /* Release the context's device memory (waits for its stream first). */
 void lbm_destroy(lbm_ctx* c);
 
