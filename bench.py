@@ -185,6 +185,8 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--batch-steps", type=int, default=2000)
+    ap.add_argument("--no-batch", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -320,6 +322,39 @@ def main():
                "h2d_bytes_per_step": bi / args.steps, "d2h_bytes_per_step": bo / args.steps,
                "seconds": t_e2e}
 
+    # ---- batched ragged instances (one persistent launch per step) -------------
+    batched = None
+    if not args.no_batch and args.batch_steps > 0:
+        from paper_1601_02708_gb300 import LBMBatch, inputs
+        cases = inputs.batch_cases()
+        bstream = torch.cuda.Stream()
+        members = [LBM(c["nx"], c["ny"], c["tau"], precision=32, stream=bstream.cuda_stream,
+                       **lattice_kwargs(c)) for c in cases]
+        batch = LBMBatch(members)
+        bud = [dev(c["u_dir"]) for c in cases]
+        bq = [dev(c["q_neu"]) for c in cases]
+        batch.substeps(1, 1, bud, bud, bq)  # loads the edge data into every member
+        tune = batch.autotune(trial_steps=20, repeats=2)
+        batch.substeps(args.warmup, 1, bud, bud, bq)
+        batch.time_steps(args.batch_steps)  # records the graph of the timed length
+        barrier()
+        bms = max_over_ranks(batch.time_steps(args.batch_steps))
+        bnodes = sum(c["nx"] * c["ny"] for c in cases)
+        bglups = world * bnodes * args.batch_steps / (bms / 1e3) / 1e9
+        batched = {"value": bglups, "unit": "GLUPS", "instances": len(cases),
+                   "nodes": bnodes, "steps": args.batch_steps,
+                   "ms_per_step": bms / args.batch_steps,
+                   "ratio_to_single_lattice": bglups / value,
+                   "tile_shape": LBMBatch.shapes()[batch.shape],
+                   "autotune_ms": {str(LBMBatch.shapes()[k]): v for k, v in tune.items()},
+                   "workload": "256 instances, side log-uniform 64-1024, porosity "
+                               "U[0.4,0.8], tau U[0.6,1.2], k 1e-3 with dissolution"}
+        batch.close()
+        for m in members:
+            m.close()
+        del members, batch
+        torch.cuda.empty_cache()
+
     # ---- CPU oracle on a bounded sample --------------------------------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.cpu_steps > 0:
@@ -350,7 +385,8 @@ def main():
                          "traffic": traffic, "algorithmic_bytes_per_launch": bytes_step,
                          "kernel_ms_per_launch": per_launch_ms,
                          "dissolve_ms_per_launch": diss_ms / max(diss_n, 1)},
-            "fp64": fp64, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "fp64": fp64, "batched": batched, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches,
             "clocks": clocks.summary(),
         }
         print(json.dumps(line), flush=True)

@@ -174,6 +174,47 @@ lbm_status lbm_set_kernel(lbm_ctx* c, int variant);
 lbm_status lbm_set_stream(lbm_ctx* c, void* stream);
 lbm_status lbm_synchronize(lbm_ctx* c);
 
+/* ---- batches: many lattices advanced together (Sec. 6.3, Algorithm 2 runs
+ * several pore-scale subdomains; each member steps as lbm_substeps does) -----
+ * A batch is built from contexts made by lbm_init that share precision,
+ * device, step parity and a created (non-default) stream; the contexts stay
+ * owned by the caller and usable on their own (read-out, diagnostics, save /
+ * restore), but while they are in a batch they should be stepped only
+ * through it, and they must outlive it.  One time step of the whole batch is
+ * two launches: a persistent step kernel over a tile list spanning every
+ * member and one dissolution pass over every member's surface list.  Each
+ * (n, eta, parity, shape) sequence is recorded once into a CUDA graph and
+ * replayed.  A member's results are bit-identical to stepping it alone.
+ * Errors: LBM_ERR_ARG for bad arguments (message in lbm_batch_last_error),
+ * LBM_ERR_CUDA / LBM_ERR_NOMEM from the runtime; a bounded wait that expired
+ * inside the pipelined kernel sets the status word of every member that CTA
+ * served, reported as LBM_ERR_TIMEOUT by that member's next read-out. */
+typedef struct lbm_batch lbm_batch;
+/* members: n context pointers (n >= 1, no repeats); the batch copies the
+ * pointer array and allocates its own device tables. */
+lbm_status lbm_batch_create(lbm_batch** out, int n, lbm_ctx* const* members);
+/* n steps of every member; edge-data arguments are arrays of one pointer per
+ * member, each laid out as in lbm_substeps (an array or entry may be NULL:
+ * zero data), host or device memory, read before the call returns. */
+lbm_status lbm_batch_substeps(lbm_batch* b, int n, int eta, const double* const* u_dir_t0,
+                              const double* const* u_dir_t1, const double* const* q_neu);
+/* Tile shape of the step kernel.  Shapes 0 .. 5: one thread per node, tiles
+ * of 32 x tile_h nodes, `threads` threads per block, each thread
+ * 32 * tile_h / threads rows apart.  Shape 6 (pipelined = 1): the TMA-fed pipeline of the
+ * single-lattice FP32 kernel over 128 x 8 tiles, one CTA per SM, available
+ * for FP32 members (LBM_ERR_ARG otherwise) and the default where available.
+ * Results do not depend on the shape; the speed does.  lbm_batch_time_steps
+ * times n steps (eta = 1, the current edge data) in milliseconds, advancing
+ * the members: an autotuner saves and restores them around it.
+ * lbm_batch_shape_info returns LBM_ERR_ARG past the last shape. */
+lbm_status lbm_batch_set_shape(lbm_batch* b, int shape);
+lbm_status lbm_batch_get_shape(const lbm_batch* b, int* shape);
+lbm_status lbm_batch_shape_info(int shape, int* tile_w, int* tile_h, int* threads,
+                                int* pipelined);
+lbm_status lbm_batch_time_steps(lbm_batch* b, int n, float* ms);
+void lbm_batch_destroy(lbm_batch* b);  /* does not destroy the members */
+const char* lbm_batch_last_error(void);
+
 /* FP64 sum of a concentration field that allocates nothing -- the paper has
  * no counterpart; this entry point exists for callers that cannot allocate
  * device memory when they need the sum: code recording a CUDA graph (an

@@ -6,8 +6,8 @@ The compute path is the CUDA library liblbmade.so (C ABI in
 include/lbm_ade.h); `LBM` wraps it.  Nothing here falls back to a CPU
 implementation: without the built library, constructing `LBM` raises.
 """
-from .lbm import (DIRICHLET, LBM, LBMError, NEUMANN, PERIODIC, REACT_BULK,
+from .lbm import (DIRICHLET, LBM, LBMBatch, LBMError, NEUMANN, PERIODIC, REACT_BULK,
                   REACT_NONE, REACT_SURFACE)
 
-__all__ = ["LBM", "LBMError", "PERIODIC", "DIRICHLET", "NEUMANN",
+__all__ = ["LBM", "LBMBatch", "LBMError", "PERIODIC", "DIRICHLET", "NEUMANN",
            "REACT_NONE", "REACT_SURFACE", "REACT_BULK"]

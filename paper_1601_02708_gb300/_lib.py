@@ -76,6 +76,22 @@ def load():
             fn = getattr(lib, name)
             fn.argtypes = args
             fn.restype = I
+        PP = ctypes.POINTER(P)
+        for name, args in {
+            "lbm_batch_create": [ctypes.POINTER(P), I, PP],
+            "lbm_batch_substeps": [P, I, I, PP, PP, PP],
+            "lbm_batch_set_shape": [P, I],
+            "lbm_batch_shape_info": [I] + [ctypes.POINTER(I)] * 4,
+            "lbm_batch_get_shape": [P, ctypes.POINTER(I)],
+            "lbm_batch_time_steps": [P, I, ctypes.POINTER(ctypes.c_float)],
+        }.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = I
+        lib.lbm_batch_destroy.argtypes = [P]
+        lib.lbm_batch_destroy.restype = None
+        lib.lbm_batch_last_error.argtypes = []
+        lib.lbm_batch_last_error.restype = ctypes.c_char_p
         lib.lbm_destroy.argtypes = [P]
         lib.lbm_destroy.restype = None
         lib.lbm_last_error.argtypes = []
@@ -89,4 +105,10 @@ def load():
 def check(status: int):
     if status != LBM_OK:
         msg = load().lbm_last_error().decode(errors="replace")
+        raise LBMError(status, msg)
+
+
+def check_batch(status: int):
+    if status != LBM_OK:
+        msg = load().lbm_batch_last_error().decode(errors="replace")
         raise LBMError(status, msg)

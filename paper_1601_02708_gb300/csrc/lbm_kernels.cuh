@@ -163,7 +163,7 @@ struct GlobalSrc {
 // the node is not on the outlet; the boundary code is then compiled out.
 template <typename Real, bool kFinal, bool kEdge, class Src>
 __device__ __forceinline__ double step_node(const StepArgs<Real>& a, const Src& src,
-                                            int x, int y, long long n) {
+                                            int x, int y, long long n, double frac) {
   const uint32_t w = src.word();
   const bool ghosts =
       kEdge && ((x == 0) | (x == a.nx - 1) | (y == 0) | (y == a.ny - 1)) &&
@@ -217,7 +217,7 @@ __device__ __forceinline__ double step_node(const StepArgs<Real>& a, const Src& 
       int slot;
       if (dside >= 0) {
         slot = edge_slot(dside, x, y, a.nx, a.ny);
-        const double up = (1.0 - a.frac) * a.ua[slot] + a.frac * a.ub[slot];
+        const double up = (1.0 - frac) * a.ua[slot] + frac * a.ub[slot];
         bad = maxent_dirichlet(f, unknown, up);
       } else {
         slot = edge_slot(nside, x, y, a.nx, a.ny);
@@ -257,10 +257,11 @@ __device__ __forceinline__ double step_node(const StepArgs<Real>& a, const Src& 
   return (double)u;
 }
 
-// True when every node of the box [x0, x0 + w) x [y0, y0 + h) is one node
-// or more away from each side of the lattice.
-__device__ __forceinline__ bool box_is_interior(int x0, int y0, int w, int h, int nx, int ny) {
-  return x0 >= 1 && y0 >= 1 && x0 + w <= nx - 1 && y0 + h <= ny - 1;
+// True when the warp's 32 consecutive nodes (xs .. xs + 31, row y) all lie
+// one node or more inside every side of the lattice: the boundary code can
+// be skipped for the whole warp (the test is warp-uniform).
+__device__ __forceinline__ bool group_is_interior(int xs, int y, int nx, int ny) {
+  return xs >= 1 && xs + 32 <= nx - 1 && y >= 1 && y <= ny - 2;
 }
 
 // Generic step: one thread per node, inputs from global memory.  Used in
@@ -275,10 +276,10 @@ __global__ void __launch_bounds__(kBX * kBY, sizeof(Real) == 4 ? 4 : 4)
   if (x < a.nx && y < a.ny) {
     const long long n = (long long)(y + kYO) * a.pitch + (x + kXO);
     GlobalSrc<Real> src{a, n};
-    if (box_is_interior(blockIdx.x * kBX, blockIdx.y * kBY, kBX, kBY, a.nx, a.ny))
-      my_u = step_node<Real, kFinal, false>(a, src, x, y, n);
+    if (group_is_interior(blockIdx.x * kBX, y, a.nx, a.ny))
+      my_u = step_node<Real, kFinal, false>(a, src, x, y, n, a.frac);
     else
-      my_u = step_node<Real, kFinal, true>(a, src, x, y, n);
+      my_u = step_node<Real, kFinal, true>(a, src, x, y, n, a.frac);
   }
   if (kFinal) {
     const double s = block_sum(my_u, red);
@@ -398,7 +399,7 @@ __device__ __forceinline__ Real mineral_take(const Real* __restrict__ rlink, lon
 // fluid for its collision), tell its neighbours through their post-flip bits,
 // and put solid neighbours it exposes on the surface list.  Run by one block
 // after every node has been examined.
-__device__ void apply_flips(const DissolveArgs& d, int tid, int nthreads) {
+__device__ inline void apply_flips(const DissolveArgs& d, int tid, int nthreads) {
   __threadfence();
   const int cnt = *((volatile int*)d.flip_count);
   for (int k = tid; k < cnt; k += nthreads) {
@@ -515,7 +516,7 @@ __global__ void __launch_bounds__(kDThreads)
 
 // Build the surface list: every solid node with a fluid in-lattice neighbour
 // (or pending) that is not listed yet; its mineral moves to the list.
-__global__ void __launch_bounds__(kDThreads) lbm_list_build(const DissolveArgs d) {
+static __global__ void __launch_bounds__(kDThreads) lbm_list_build(const DissolveArgs d) {
   const long long total = (long long)d.nx * d.ny;
   for (long long id = blockIdx.x * (long long)kDThreads + threadIdx.x; id < total;
        id += (long long)gridDim.x * kDThreads) {
@@ -533,7 +534,7 @@ __global__ void __launch_bounds__(kDThreads) lbm_list_build(const DissolveArgs d
 }
 
 // Write the list's minerals back into the dense array (before read-out).
-__global__ void lbm_list_scatter(const DissolveArgs d) {
+static __global__ void lbm_list_scatter(const DissolveArgs d) {
   const int count = *d.scount;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x)
     d.mineral[d.slist[e]] = d.smin[e];

@@ -191,26 +191,17 @@ __global__ void __launch_bounds__(kTmaThreads + 32, 1)
       const unsigned char* st = smem + s * kStageBytes;
       SmemSrc src{(const float*)st, (const float*)(st + kOffVel), (const float*)(st + kOffK),
                   (const uint32_t*)(st + kOffWord), r, 0};
-      const int x0 = (t % ntx) * kTW, y0 = (t / ntx) * kTH, y = y0 + r;
-      if (box_is_interior(x0, y0, kTW, kTH, a.nx, a.ny)) {
+      const int x0 = (t % ntx) * kTW, y = (t / ntx) * kTH + r;
 #pragma unroll 1
-        for (int j = 0; j < 2; ++j) {
-          const int xl = cbase + 32 * j;
-          src.c = xl + 4;
-          const long long n = (long long)(y + kYO) * a.pitch + (x0 + xl + kXO);
-          my_u += step_node<float, kFinal, false>(a, src, x0 + xl, y, n);
-        }
-      } else {
-#pragma unroll 1
-        for (int j = 0; j < 2; ++j) {
-          const int xl = cbase + 32 * j;
-          const int x = x0 + xl;
-          if (x < a.nx && y < a.ny) {
-            src.c = xl + 4;
-            const long long n = (long long)(y + kYO) * a.pitch + (x + kXO);
-            my_u += step_node<float, kFinal, true>(a, src, x, y, n);
-          }
-        }
+      for (int j = 0; j < 2; ++j) {
+        const int xl = cbase + 32 * j;
+        const int x = x0 + xl;
+        src.c = xl + 4;
+        const long long n = (long long)(y + kYO) * a.pitch + (x + kXO);
+        if (group_is_interior(x - lane, y, a.nx, a.ny))
+          my_u += step_node<float, kFinal, false>(a, src, x, y, n, a.frac);
+        else if (x < a.nx && y < a.ny)
+          my_u += step_node<float, kFinal, true>(a, src, x, y, n, a.frac);
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[s]);

@@ -157,3 +157,26 @@ def porous_case(nx: int, ny: int, seed: int, porosity: float = 0.6,
         u0=np.zeros((ny, nx)), react_mode=1, k=k, dissolution=True,
         mineral=np.ones((ny, nx)), u_dir=edge_array(nx, ny, W=c_in),
         q_neu=edge_array(nx, ny))
+
+
+def batch_cases(n_inst: int = 256, seed: int = 3, smin: int = 64, smax: int = 1024,
+                k: float = 1e-3, rmin: float = 8.0, rmax: float = 24.0) -> list:
+    """Independent reactive porous instances: square side log-uniform in
+    [smin, smax], porosity U[0.4, 0.8], tau U[0.6, 1.2], the disk and
+    stream-function generators of porous_case (instance i seeded 3000 + i),
+    surface rate k with dissolution, Dirichlet 1 west, zero-flux east,
+    periodic y."""
+    rng = SplitMix64(seed)
+    cases = []
+    for i in range(n_inst):
+        side = int(round(math.exp(math.log(smin) + (math.log(smax) - math.log(smin)) * rng.uniform())))
+        porosity = 0.4 + 0.4 * rng.uniform()
+        tau = 0.6 + 0.6 * rng.uniform()
+        solid = disk_packing(side, side, porosity, 3000 + i, rmin=rmin, rmax=rmax)
+        vel = streamfunction_velocity(side, side, 3000 + i + 1_000_003, solid=solid)
+        cases.append(dict(
+            nx=side, ny=side, tau=tau, edges=(1, 2, 0, 0), solid=solid, vel=vel,
+            u0=np.zeros((side, side)), react_mode=1, k=k, dissolution=True,
+            mineral=np.ones((side, side)), u_dir=edge_array(side, side, W=1.0),
+            q_neu=edge_array(side, side), porosity=porosity))
+    return cases

@@ -257,5 +257,98 @@ class LBM:
         check(self._lib.lbm_restore(self.handle, ptr, nb))
 
 
-__all__ = ["LBM", "LBMError", "PERIODIC", "DIRICHLET", "NEUMANN",
+class LBMBatch:
+    """Several lattices advanced together (Sec. 6.3, Algorithm 2 runs many
+    pore-scale subdomains): every time step of the whole batch is one
+    persistent step launch over all members' tiles plus one dissolution
+    launch, replayed from a recorded CUDA graph.  Members are LBM objects
+    sharing precision and a created stream (``LBM(..., stream=s)`` with
+    ``s = torch.cuda.Stream().cuda_stream``); they stay usable for read-out.
+    """
+
+    def __init__(self, members):
+        self._lib = _lib.load()
+        self.members = list(members)
+        arr = (ctypes.c_void_p * len(self.members))(*[m.handle.value for m in self.members])
+        h = ctypes.c_void_p()
+        _lib.check_batch(self._lib.lbm_batch_create(ctypes.byref(h), len(self.members), arr))
+        self._h = h
+        sh = ctypes.c_int()
+        _lib.check_batch(self._lib.lbm_batch_get_shape(self._h, ctypes.byref(sh)))
+        self.shape = sh.value
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._lib.lbm_batch_destroy(h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _ptr_array(self, arrays, keep):
+        if arrays is None:
+            return None
+        ptrs = []
+        for m, a in zip(self.members, arrays):
+            ptrs.append(_in_ptr(a, "f64", m.n_edge, keep) if a is not None else None)
+        return (ctypes.c_void_p * len(ptrs))(*ptrs)
+
+    def substeps(self, n, eta=1, u_dir_t0=None, u_dir_t1=None, q_neu=None):
+        """n steps of every member; each edge argument is a list with one
+        array (or None) per member."""
+        keep = []
+        a = self._ptr_array(u_dir_t0, keep)
+        b = self._ptr_array(u_dir_t1, keep)
+        q = self._ptr_array(q_neu, keep)
+        _lib.check_batch(self._lib.lbm_batch_substeps(self._h, int(n), int(eta), a, b, q))
+
+    @staticmethod
+    def shapes():
+        """Step-kernel shapes as (tile width, tile height, threads per
+        block, pipelined)."""
+        out = []
+        lib = _lib.load()
+        while True:
+            v = [ctypes.c_int() for _ in range(4)]
+            if lib.lbm_batch_shape_info(len(out), *[ctypes.byref(x) for x in v]) != 0:
+                return out
+            out.append((v[0].value, v[1].value, v[2].value, bool(v[3].value)))
+
+    def set_shape(self, shape):
+        _lib.check_batch(self._lib.lbm_batch_set_shape(self._h, int(shape)))
+        self.shape = int(shape)
+
+    def time_steps(self, n):
+        """Device milliseconds of n steps (advances the state)."""
+        ms = ctypes.c_float()
+        _lib.check_batch(self._lib.lbm_batch_time_steps(self._h, int(n), ctypes.byref(ms)))
+        return ms.value
+
+    def autotune(self, trial_steps=20, repeats=2):
+        """Pick the fastest tile shape by timing trial steps of the real
+        batch; every member's state is saved before and restored after, so
+        the batch ends where it started.  Returns {shape: ms}."""
+        blobs = [m.save() for m in self.members]
+        times = {}
+        for s in range(len(self.shapes())):
+            try:
+                self.set_shape(s)
+            except LBMError:  # the pipelined shape needs FP32 members
+                continue
+            self.time_steps(trial_steps)  # records the graph
+            best = min(self.time_steps(trial_steps) for _ in range(repeats))
+            times[s] = best
+            for m, bl in zip(self.members, blobs):
+                m.restore(bl)
+        self.set_shape(min(times, key=times.get))
+        for m, bl in zip(self.members, blobs):
+            m.restore(bl)
+        return times
+
+
+__all__ = ["LBM", "LBMBatch", "LBMError", "PERIODIC", "DIRICHLET", "NEUMANN",
            "REACT_NONE", "REACT_SURFACE", "REACT_BULK"]
