@@ -72,6 +72,8 @@ def _load():
         lib.or_trace_point.argtypes = [P, D, D]
         lib.or_maxent_dirichlet.restype = I
         lib.or_maxent_dirichlet.argtypes = [P, P, D]
+        lib.or_lbm_adjoint.restype = I
+        lib.or_lbm_adjoint.argtypes = [P, I, I, P, P, P, P, P, P, P, P]
         lib.or_maxent_neumann.restype = I
         lib.or_maxent_neumann.argtypes = [P, P, D, D, D, P, P]
         _lib = lib
@@ -144,6 +146,27 @@ class LBMOracle:
         b = _f64(u_dir_t1 if u_dir_t1 is not None else u_dir_t0, (self.n_edge,))
         q = _f64(q_neu, (self.n_edge,))
         self._lib.or_lbm_substeps(self._h, int(n), int(eta), _ptr(a), _ptr(b), _ptr(q))
+
+    def adjoint(self, n, eta=1, u_dir_t0=None, u_dir_t1=None, q_neu=None):
+        """Advance n substeps (as ``substeps``) and return the outlet
+        breakthrough J = sum of the east-edge fluid concentrations over the n
+        substeps with its gradients: dict(J, k [ny, nx] with respect to the
+        rate of every node, ua / ub with respect to the Dirichlet data at the
+        start / end of the coarse step, q with respect to the Neumann data;
+        the last three in the edge layout).  Fixed mask only."""
+        a = _f64(u_dir_t0, (self.n_edge,))
+        b = _f64(u_dir_t1 if u_dir_t1 is not None else u_dir_t0, (self.n_edge,))
+        q = _f64(q_neu, (self.n_edge,))
+        J = ctypes.c_double()
+        gk = np.zeros((self.ny, self.nx))
+        ga, gb, gq = (np.zeros(self.n_edge) for _ in range(3))
+        rc = self._lib.or_lbm_adjoint(self._h, int(n), int(eta), _ptr(a), _ptr(b), _ptr(q),
+                                      ctypes.byref(J), _ptr(gk), _ptr(ga), _ptr(gb), _ptr(gq))
+        if rc != 0:
+            raise ValueError({-1: "the adjoint needs a fixed mask (dissolution off)",
+                              -2: "two Neumann sides meet at a corner",
+                              -3: "out of memory"}.get(rc, f"error {rc}"))
+        return dict(J=J.value, k=gk, ua=ga, ub=gb, q=gq)
 
     def u(self):
         out = np.empty((self.ny, self.nx))

@@ -530,3 +530,211 @@ double or_trace_point(const or_lbm *o, double px, double py) {
   return u1 * (1 - gx) * (1 - gy) + u2 * gx * (1 - gy) + u3 * gx * gy +
          u4 * (1 - gx) * gy;
 }
+
+/* ---- discrete adjoint of or_lbm_substeps ----------------------------------
+ *
+ * The paper differentiates nothing; this is the reverse mode of the oracle's
+ * own substep, written out by hand, for a fixed solid mask (dissolution off:
+ * a flip is not differentiable).  With the mask fixed one substep maps the
+ * pre-collision state g^{n-1} to g^n by collision (with the sink), push
+ * streaming with bounce-back, the boundary conditions and the moments; it is
+ * affine in g and in the edge data, except that a Neumann node switches
+ * between the root of Sec. 4.1.1 (b) and the zero limit with the sign of R.
+ * The objective is the outlet breakthrough
+ *   J = sum_{n=1..N} sum_{east-edge fluid nodes} u^n,
+ * and the gradients are taken with respect to the rate k(x) of every node,
+ * the Dirichlet data a, b of Eq. "MTS" and the Neumann data q, holding the
+ * pre-collision state at the start of the call fixed.
+ *
+ * Forward: the substeps of or_lbm_substeps, keeping u^{n-1} (the input of
+ * each collision) and, at Neumann nodes, whether the root was taken (R < 0).
+ * Reverse, n = N .. 1, from gbar = dJ/dg^n (initially the direct term e(x),
+ * 1 at east-edge fluid nodes, 0 elsewhere):
+ *  - boundary conditions: the unknown entries were set from the known ones,
+ *    so their adjoint moves onto the known entries and the data --
+ *    Dirichlet f_i = w_i / W_U (u^p - sum_known f):
+ *      t = sum_U w_i gbar_i / W_U, pbar_known -= t, d/du^p += t;
+ *    Neumann on an axis side with the root, f_i = w_i / W_U (sum a_j f_j - q):
+ *      pbar_j += a_j t for the known j, d/dq -= t; with the zero limit the
+ *      unknowns depend on nothing;
+ *  - streaming: F_i(y) went to y + e_i if that node is fluid, back to y as
+ *    direction rev(i) if it is solid, nowhere if it lies outside:
+ *      Fbar_i(y) = pbar_i(y + e_i), pbar_rev(i)(y) or 0;
+ *  - collision, F_i = (1 - omega) g_i + w_i (omega P_i - k) u, u = sum_j g_j,
+ *    with feq_i = w_i P_i u (Eq. "LBM_feq") and the sink of k at reactive
+ *    nodes:
+ *      gbar_j = (1 - omega) Fbar_j + sum_i w_i (omega P_i - k) Fbar_i
+ *               (+ e(x) when n - 1 >= 1),
+ *      dJ/dk(x) += -u^{n-1}(x) sum_i w_i Fbar_i at reactive nodes.
+ * The state advances by N substeps, as with or_lbm_substeps.  Outputs may be
+ * NULL.  Returns 0; -1 if dissolution is on; -2 if two Neumann sides meet at
+ * a corner (that root is not affine in the data); -3 if memory ran out.
+ */
+int or_lbm_adjoint(or_lbm *o, int nsteps, int eta, const double *ua,
+                   const double *ub, const double *q, double *J_out,
+                   double *grad_k, double *grad_ua, double *grad_ub,
+                   double *grad_q) {
+  if (o->dissolution) return -1;
+  const int np_x = o->edge[SIDE_W] != EDGE_PERIODIC;
+  const int np_y = o->edge[SIDE_S] != EDGE_PERIODIC;
+  if (np_x && np_y) {
+    const int xs[2] = {SIDE_W, SIDE_E}, ys[2] = {SIDE_S, SIDE_N};
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b)
+        if (o->edge[xs[a]] == EDGE_NEUMANN && o->edge[ys[b]] == EDGE_NEUMANN) return -2;
+  }
+  const size_t N = nn(o);
+  const size_t ne = 2 * ((size_t)o->nx + (size_t)o->ny);
+  const int steps = nsteps > 0 ? nsteps : 0;
+  double *uh = (double *)malloc(((size_t)steps + 1) * N * sizeof(double));
+  uint8_t *root = (uint8_t *)calloc((size_t)steps * ne + 1, 1);
+  double *gbar = (double *)calloc(NQ * N, sizeof(double));
+  double *pbar = (double *)calloc(NQ * N, sizeof(double));
+  double *Fbar = (double *)calloc(NQ * N, sizeof(double));
+  if (!uh || !root || !gbar || !pbar || !Fbar) {
+    free(uh); free(root); free(gbar); free(pbar); free(Fbar);
+    return -3;
+  }
+  if (grad_k) memset(grad_k, 0, N * sizeof(double));
+  if (grad_ua) memset(grad_ua, 0, ne * sizeof(double));
+  if (grad_ub) memset(grad_ub, 0, ne * sizeof(double));
+  if (grad_q) memset(grad_q, 0, ne * sizeof(double));
+  const double omega = 1.0 / o->tau;
+  static const double SN[4][2] = {{-1, 0}, {1, 0}, {0, -1}, {0, 1}};
+
+  /* ---- forward, recording u^{n-1} and the Neumann branches ---- */
+  const double J0 = o->J;
+  for (int n = 1; n <= steps; ++n) {
+    memcpy(uh + (size_t)(n - 1) * N, o->u, N * sizeof(double));
+    o->reacted += collide(o, o->fpost);
+    stream(o);
+    for (int y = 0; y < o->ny; ++y)
+      for (int x = 0; x < o->nx; ++x) {
+        size_t m = at(o, x, y);
+        if (o->solid[m]) continue;
+        for (int s = 0; s < 4; ++s) {
+          int on = (s == SIDE_W && x == 0) || (s == SIDE_E && x == o->nx - 1) ||
+                   (s == SIDE_S && y == 0) || (s == SIDE_N && y == o->ny - 1);
+          if (!on || o->edge[s] != EDGE_NEUMANN) continue;
+          /* this node is Neumann unless a Dirichlet side also holds it */
+          int dir = 0;
+          for (int t = 0; t < 4; ++t) {
+            int on2 = (t == SIDE_W && x == 0) || (t == SIDE_E && x == o->nx - 1) ||
+                      (t == SIDE_S && y == 0) || (t == SIDE_N && y == o->ny - 1);
+            if (on2 && o->edge[t] == EDGE_DIRICHLET) dir = 1;
+          }
+          if (dir) break;
+          size_t e = edge_slot(o, s, x, y);
+          double R = q ? q[e] : 0.0;
+          for (int i = 0; i < NQ; ++i)
+            if (o->known[(size_t)i * N + m])
+              R -= (CX[i] * SN[s][0] + CY[i] * SN[s][1]) * o->fnew[(size_t)i * N + m];
+          root[(size_t)(n - 1) * ne + e] = R < 0.0;
+          break;
+        }
+      }
+    apply_bc(o, n, eta, ua, ub, q);
+    memcpy(o->f, o->fnew, NQ * N * sizeof(double));
+    moments(o);
+    for (int y = 0; y < o->ny; ++y)
+      if (!o->solid[at(o, o->nx - 1, y)]) o->J += o->u[at(o, o->nx - 1, y)];
+    o->steps += 1;
+  }
+  if (J_out) *J_out = o->J - J0;
+
+  /* ---- reverse sweep ---- */
+  for (int y = 0; y < o->ny; ++y) {
+    size_t m = at(o, o->nx - 1, y);
+    if (!o->solid[m])
+      for (int i = 0; i < NQ; ++i) gbar[(size_t)i * N + m] = 1.0;
+  }
+  for (int n = steps; n >= 1; --n) {
+    const double frac = (double)n / (double)eta;
+    /* boundary conditions */
+    memcpy(pbar, gbar, NQ * N * sizeof(double));
+    for (int y = 0; y < o->ny; ++y)
+      for (int x = 0; x < o->nx; ++x) {
+        size_t m = at(o, x, y);
+        if (o->solid[m]) continue;
+        int on[4] = {x == 0 && o->edge[SIDE_W] != EDGE_PERIODIC,
+                     x == o->nx - 1 && o->edge[SIDE_E] != EDGE_PERIODIC,
+                     y == 0 && o->edge[SIDE_S] != EDGE_PERIODIC,
+                     y == o->ny - 1 && o->edge[SIDE_N] != EDGE_PERIODIC};
+        int unk[NQ], nunk = 0;
+        for (int i = 0; i < NQ; ++i) {
+          int sx, sy;
+          unk[i] = !locate(o, x - CX[i], y - CY[i], &sx, &sy);
+          nunk += unk[i];
+        }
+        if (!nunk) continue;
+        int dside = -1, nside = -1;
+        for (int s = 0; s < 4; ++s) {
+          if (!on[s]) continue;
+          if (o->edge[s] == EDGE_DIRICHLET && dside < 0) dside = s;
+          if (o->edge[s] == EDGE_NEUMANN && nside < 0) nside = s;
+        }
+        double wu = 0.0, t = 0.0;
+        for (int i = 0; i < NQ; ++i)
+          if (unk[i]) wu += WT[i];
+        for (int i = 0; i < NQ; ++i)
+          if (unk[i]) t += WT[i] * gbar[(size_t)i * N + m] / wu;
+        if (dside >= 0) {
+          size_t e = edge_slot(o, dside, x, y);
+          for (int i = 0; i < NQ; ++i)
+            if (!unk[i]) pbar[(size_t)i * N + m] -= t;
+          if (grad_ua) grad_ua[e] += (1.0 - frac) * t;
+          if (grad_ub) grad_ub[e] += frac * t;
+        } else {
+          size_t e = edge_slot(o, nside, x, y);
+          if (root[(size_t)(n - 1) * ne + e]) {
+            for (int i = 0; i < NQ; ++i)
+              if (!unk[i])
+                pbar[(size_t)i * N + m] +=
+                    (CX[i] * SN[nside][0] + CY[i] * SN[nside][1]) * t;
+            if (grad_q) grad_q[e] -= t;
+          }
+        }
+        for (int i = 0; i < NQ; ++i)
+          if (unk[i]) pbar[(size_t)i * N + m] = 0.0;
+      }
+    /* streaming */
+    for (int y = 0; y < o->ny; ++y)
+      for (int x = 0; x < o->nx; ++x) {
+        size_t m = at(o, x, y);
+        for (int i = 0; i < NQ; ++i) {
+          double v = 0.0;
+          int tx, ty;
+          if (!o->solid[m] && locate(o, x + CX[i], y + CY[i], &tx, &ty)) {
+            size_t t = at(o, tx, ty);
+            v = o->solid[t] ? pbar[(size_t)reverse_of(i) * N + m] : pbar[(size_t)i * N + t];
+          }
+          Fbar[(size_t)i * N + m] = v;
+        }
+      }
+    /* collision */
+    const double *un = uh + (size_t)(n - 1) * N;
+    for (int y = 0; y < o->ny; ++y)
+      for (int x = 0; x < o->nx; ++x) {
+        size_t m = at(o, x, y);
+        if (o->solid[m]) {
+          for (int i = 0; i < NQ; ++i) gbar[(size_t)i * N + m] = 0.0;
+          continue;
+        }
+        const int rx = reactive(o, x, y);
+        double kr = rx ? o->k[m] : 0.0;
+        double s = 0.0, wf = 0.0;
+        for (int i = 0; i < NQ; ++i) {
+          double Fb = Fbar[(size_t)i * N + m];
+          double wP = feq(i, 1.0, o->vel[m], o->vel[N + m]); /* w_i P_i */
+          s += (omega * wP - WT[i] * kr) * Fb;
+          wf += WT[i] * Fb;
+        }
+        if (n - 1 >= 1 && x == o->nx - 1) s += 1.0;
+        for (int j = 0; j < NQ; ++j)
+          gbar[(size_t)j * N + m] = (1.0 - omega) * Fbar[(size_t)j * N + m] + s;
+        if (grad_k && rx) grad_k[m] -= un[m] * wf;
+      }
+  }
+  free(uh); free(root); free(gbar); free(pbar); free(Fbar);
+  return 0;
+}
