@@ -185,6 +185,8 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--kernel-steps", type=int, default=1000)
+    ap.add_argument("--adjoint-steps", type=int, default=5000)
     ap.add_argument("--batch-steps", type=int, default=2000)
     ap.add_argument("--no-batch", action="store_true")
     args = ap.parse_args()
@@ -232,7 +234,6 @@ def main():
     lat = LBM(n, n, case["tau"], precision=32, **kw)
     lat.substeps(args.warmup, 1, ud, ud, q)
     barrier()
-    lat.kernel_timing(True)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clocks:
@@ -243,6 +244,11 @@ def main():
         ev1.synchronize()
         barrier()
     ms = max_over_ranks(ev0.elapsed_time(ev1))
+    launches = 2 * args.steps  # one step and one dissolution launch per step
+    # per-kernel durations from CUDA events around every launch, on a
+    # separate stretch of steps (the events add small gaps between launches)
+    lat.kernel_timing(True)
+    lat.substeps(args.kernel_steps, 1, ud, ud, q)
     step_ms, step_n, diss_ms, diss_n = lat.kernel_times()
     lat.kernel_timing(False)
     diag = lat.diagnostics()
@@ -355,6 +361,47 @@ def main():
         del members, batch
         torch.cuda.empty_cache()
 
+    # ---- adjoint: gradient of the outlet breakthrough (512^2 workload) -------
+    adjoint = None
+    if args.adjoint_steps > 0:
+        from paper_1601_02708_gb300 import inputs
+        c4 = inputs.adjoint_case()
+        kw4 = {k: c4[k] for k in ("edges", "solid", "vel", "u0", "react_mode", "k_field")}
+        lat4 = LBM(c4["nx"], c4["ny"], c4["tau"], precision=32, **kw4)
+        ud4, q4 = dev(c4["u_dir"]), dev(c4["q_neu"])
+        start = lat4.save()
+        na = args.adjoint_steps
+        lat4.adjoint(na, 1, ud4, ud4, q4)  # warm-up; sizes the checkpoint buffers
+        lat4.restore(start)
+        lat4.substeps(na, 1, ud4, ud4, q4)
+        lat4.restore(start)
+        barrier()
+        ev0.record(stream)
+        lat4.substeps(na, 1, ud4, ud4, q4)
+        ev1.record(stream)
+        ev1.synchronize()
+        fwd_ms = max_over_ranks(ev0.elapsed_time(ev1))
+        lat4.restore(start)
+        barrier()
+        ev0.record(stream)
+        r4 = lat4.adjoint(na, 1, ud4, ud4, q4)
+        ev1.record(stream)
+        ev1.synchronize()
+        adj_ms = max_over_ranks(ev0.elapsed_time(ev1))
+        lat4.close()
+        del lat4
+        torch.cuda.empty_cache()
+        adjoint = {"ratio": adj_ms / fwd_ms, "forward_ms": fwd_ms, "adjoint_ms": adj_ms,
+                   "reverse_only_ratio": (adj_ms - fwd_ms) / fwd_ms, "steps": na,
+                   "stride": int(math.ceil(math.sqrt(na))), "J": r4["J"], "dtype": "f32",
+                   "workload": "512x512 porous (porosity 0.6, disks r 8-24, stream function "
+                               "|v|max 0.05 plus mean flow 0.15 along x), bulk rate field "
+                               "1e-3 (1 +- 0.2 U), tau 0.7, Dirichlet 1 west, zero-flux "
+                               "east, periodic y; J = outlet breakthrough; gradients "
+                               "w.r.t. every node's rate and the inlet value",
+                   "note": "adjoint_ms is one lbm_adjoint call: forward with checkpoints, "
+                           "recompute and reverse sweep, gradients copied to the host"}
+
     # ---- CPU oracle on a bounded sample --------------------------------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.cpu_steps > 0:
@@ -365,7 +412,6 @@ def main():
                          f"{dt:.1f} s"}
 
     if rank == 0:
-        launches = step_n + diss_n
         line = {
             "metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -379,13 +425,15 @@ def main():
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2 (2 x 604 MB populations), no flush"},
             "fluid_glups": world * n_fluid * args.steps / (ms / 1e3) / 1e9,
-            "roofline": {"bound": "hbm", "kernel": "lbm_step<float>",
+            "roofline": {"bound": "hbm", "kernel": "lbm_step_tma<false>",
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,
                          "traffic": traffic, "algorithmic_bytes_per_launch": bytes_step,
                          "kernel_ms_per_launch": per_launch_ms,
+                         "kernel_timing_steps": args.kernel_steps,
                          "dissolve_ms_per_launch": diss_ms / max(diss_n, 1)},
-            "fp64": fp64, "batched": batched, "cpu_baseline": cpu, "e2e": e2e,
+            "fp64": fp64, "batched": batched, "adjoint": adjoint, "cpu_baseline": cpu,
+            "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clocks.summary(),
         }

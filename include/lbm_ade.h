@@ -174,6 +174,47 @@ lbm_status lbm_set_kernel(lbm_ctx* c, int variant);
 lbm_status lbm_set_stream(lbm_ctx* c, void* stream);
 lbm_status lbm_synchronize(lbm_ctx* c);
 
+/* Replace the per-node rate field k(x) ([ny][nx], host or device, copied
+ * before return) of a context created with one (LBM_ERR_STATE otherwise);
+ * the next step uses it. */
+lbm_status lbm_set_rate_field(lbm_ctx* c, const double* k_field);
+
+/* ---- adjoint: gradients of the outlet breakthrough (reverse mode) ---------
+ * The paper computes no gradients; this is the discrete adjoint of the step
+ * of lbm_substeps -- pull streaming with bounce-back, the max-entropy
+ * boundary conditions of Sec. 4.1.1 (Eq. "LBM_Dir", "LBM_Neu", the time
+ * interpolation of Eq. "MTS"), the collision of Eq. "Collision" with the
+ * sink -- which for a fixed solid mask is affine in the populations and the
+ * edge data (a Neumann node's root / zero-limit branch is recorded in the
+ * forward run).  lbm_adjoint advances the context by n substeps exactly as
+ * lbm_substeps(c, n, eta, u_dir_t0, u_dir_t1, q_neu) would and returns the
+ * outlet breakthrough
+ *     J = sum_{j=1..n} sum_{fluid nodes with x = nx - 1} u^j
+ * with its gradients, holding the pre-collision state at the start of the
+ * call fixed:
+ *   grad_k  [ny][nx]: dJ/dk(x), the rate of every node (0 where no reaction
+ *           applies: solid nodes, and non-surface nodes in surface mode);
+ *   grad_ua, grad_ub [n_edge]: dJ/d(Dirichlet data at the start / the end of
+ *           the coarse step), edge layout as in lbm_substeps;
+ *   grad_q  [n_edge]: dJ/d(Neumann data).
+ * The gradient with respect to a uniform inlet value is the sum of grad_ua
+ * and grad_ub over that side's slots.  J and every gradient are FP64; any
+ * output may be NULL; outputs may be host or device memory and are complete
+ * when the call returns.
+ * Work and memory: the state is kept every `stride` steps (stride <= 0:
+ * ceil(sqrt(n))), each segment is recomputed once during the reverse sweep
+ * storing u and the Neumann branches of its steps, and one adjoint step runs
+ * per step: about three forward passes, with ceil(n / stride) + 3 population
+ * sets and `stride` concentration planes of device memory, kept in the
+ * context for the next call.
+ * Errors: LBM_ERR_STATE if dissolution is on (a flip is not differentiable);
+ * LBM_ERR_ARG for n < 1 or eta < 1, or two Neumann sides that meet at a
+ * corner (that root is not affine); LBM_ERR_NOMEM; LBM_ERR_TIMEOUT as for
+ * lbm_substeps. */
+lbm_status lbm_adjoint(lbm_ctx* c, int n, int eta, int stride, const double* u_dir_t0,
+                       const double* u_dir_t1, const double* q_neu, double* J, double* grad_k,
+                       double* grad_ua, double* grad_ub, double* grad_q);
+
 /* ---- batches: many lattices advanced together (Sec. 6.3, Algorithm 2 runs
  * several pore-scale subdomains; each member steps as lbm_substeps does) -----
  * A batch is built from contexts made by lbm_init that share precision,

@@ -69,6 +69,8 @@ def load():
             "lbm_synchronize": [P],
             "lbm_kernel_timing": [P, I],
             "lbm_set_kernel": [P, I],
+            "lbm_set_rate_field": [P, P],
+            "lbm_adjoint": [P, I, I, I, P, P, P, ctypes.POINTER(D), P, P, P, P],
             "lbm_kernel_times_read": [P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong),
                                       ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong)],
         }

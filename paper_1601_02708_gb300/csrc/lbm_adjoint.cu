@@ -1,0 +1,398 @@
+// lbm_adjoint.cu -- reverse mode of the fused step for a fixed solid mask
+// (lbm_adjoint, declared in include/lbm_ade.h).
+//
+// With the mask fixed, one step maps the stored post-collision populations
+// F^{n-1} to F^n through pull streaming with bounce-back, the boundary
+// conditions of Sec. 4.1.1 and the collision with the sink; the map is affine
+// in the populations and the edge data (a Neumann node switches between the
+// root and the zero limit, a branch that is recorded).  The objective is the
+// outlet breakthrough J = sum_n sum_{east-edge fluid nodes} u^n.
+//
+// The adjoint state kept between kernels is pbar, the sensitivity of J to
+// the populations a node pulled in (after the boundary conditions have moved
+// the sensitivity of the unknowns onto the known populations and the data).
+// One adjoint step n, per fluid node y:
+//   lambda_j(y) = pbar^{n+1}_j(y + e_j)        downstream fluid (pulled it)
+//               = pbar^{n+1}_rev(j)(y)         downstream solid (bounced back)
+//               = 0                            downstream outside
+//   gbar_j = (1 - omega) lambda_j + omega sum_i w_i P_i lambda_i
+//            - k sum_i w_i lambda_i + [y on the east edge]
+//   dJ/dk(y) -= u^n(y) sum_i w_i lambda_i       (reactive nodes)
+//   boundary nodes, t = sum_U w_i gbar_i / W_U over the unknowns U:
+//     Dirichlet: pbar_known = gbar_known - t, dJ/du^p += t (split over the
+//       start and end data by 1 - j/eta and j/eta, Eq. "MTS")
+//     Neumann with the root: pbar_k = gbar_k + (e_k.n) t, dJ/dq -= t
+//   pbar^n = gbar elsewhere, 0 on the unknowns.
+// A final pass gathers lambda^0 and adds the first collision's -u^0 sum
+// w_i lambda_i, so the state held fixed is the pre-collision one at the start
+// of the call.
+//
+// sqrt(N) checkpointing: the forward run keeps F every L steps; the reverse
+// sweep restores each segment's checkpoint, recomputes its L steps storing
+// u^n and the Neumann branches, then runs its L adjoint steps backwards.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <vector>
+
+#include "lbm_ade.h"
+#include "lbm_ctx.h"
+#include "lbm_kernels.cuh"
+
+namespace {
+
+#define ACK(call)                                                                \
+  do {                                                                           \
+    cudaError_t e_ = (call);                                                     \
+    if (e_ != cudaSuccess)                                                       \
+      return ctx_fail(e_ == cudaErrorMemoryAllocation ? LBM_ERR_NOMEM : LBM_ERR_CUDA, \
+                      "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),    \
+                      __FILE__, __LINE__);                                       \
+  } while (0)
+
+#define ATRY(...)                   \
+  do {                              \
+    lbm_status s_ = (__VA_ARGS__);  \
+    if (s_ != LBM_OK) return s_;    \
+  } while (0)
+
+template <typename Real>
+struct AdjArgs {
+  const Real* __restrict__ mu_in;   // pbar of step n + 1, [9][rows][pitch]
+  Real* __restrict__ mu_out;        // pbar of step n
+  const uint32_t* __restrict__ link;
+  const Real* __restrict__ vel;     // [2][rows][pitch]
+  const Real* __restrict__ kf;      // [rows][pitch] or null
+  const Real* __restrict__ u_n;     // u^n, the input of step n's collision
+  const unsigned char* __restrict__ root;  // Neumann root taken at step n, per edge slot
+  double* __restrict__ gk;          // [rows][pitch] dJ/dk
+  double* __restrict__ g_ua;        // [nedge] dJ/d(start data)
+  double* __restrict__ g_ub;        // [nedge] dJ/d(end data)
+  double* __restrict__ g_q;         // [nedge] dJ/dq
+  long long plane;
+  int nx, ny, pitch, per_x, per_y;
+  int edge[4];
+  int react_mode;
+  Real omega, k_scalar;
+  double frac;  // j / eta of step n
+};
+
+template <typename Real, bool kInit, bool kEdge>
+__device__ __forceinline__ void adjoint_node(const AdjArgs<Real>& a, int x, int y, long long n) {
+  using namespace lbm;
+  const uint32_t w = a.link[n];
+  if (w & kOwnSolid) return;
+  Real lam[9];
+  lam[0] = a.mu_in[n];
+#pragma unroll
+  for (int j = 1; j < 9; ++j) {
+    const int jb = opp_of(j);
+    if (kEdge && (w & up_bit(kUpOutShift, jb))) {
+      lam[j] = (Real)0;
+    } else if (w & up_bit(kUpSolidShift, jb)) {
+      lam[j] = a.mu_in[jb * a.plane + n];
+    } else {
+      lam[j] = a.mu_in[j * a.plane + n + cx_of(j) + (long long)cy_of(j) * a.pitch];
+    }
+  }
+  const uint32_t post = (w >> kUpPostShift) & 0xFFu;
+  const bool reactive =
+      a.react_mode == kReactBulk || (a.react_mode == kReactSurface && post != 0u);
+  Real wl = (Real)w_of(0) * lam[0];
+#pragma unroll
+  for (int i = 1; i < 9; ++i) wl += (Real)w_of(i) * lam[i];
+  if (reactive && a.gk) a.gk[n] -= (double)a.u_n[n] * (double)wl;
+  if (kInit) return;
+  const Real kr = reactive ? (a.kf ? a.kf[n] : a.k_scalar) : (Real)0;
+  const Real vx = a.vel[n], vy = a.vel[a.plane + n];
+  const Real base = (Real)1 - (Real)1.5 * (vx * vx + vy * vy);
+  // sum_i w_i P_i lambda_i, by opposite pairs (P differs in the sign of 3 e.v)
+  Real wp = (Real)w_of(0) * base * lam[0];
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    const int i = p < 2 ? p + 1 : p + 3;
+    const int o = opp_of(i);
+    const Real ev = (Real)cx_of(i) * vx + (Real)cy_of(i) * vy;
+    const Real sym = base + (Real)4.5 * ev * ev;
+    const Real anti = (Real)3 * ev;
+    wp += (Real)w_of(i) * ((sym + anti) * lam[i] + (sym - anti) * lam[o]);
+  }
+  Real s = a.omega * wp - kr * wl;
+  if (kEdge && x == a.nx - 1) s += (Real)1;  // u^n counts in J
+  const Real om1 = (Real)1 - a.omega;
+  Real nu[9];
+#pragma unroll
+  for (int j = 0; j < 9; ++j) nu[j] = om1 * lam[j] + s;
+  bool ghosts = false;
+  if (kEdge) {
+    ghosts = ((x == 0) | (x == a.nx - 1) | (y == 0) | (y == a.ny - 1)) && (a.per_x | a.per_y);
+    const unsigned unknown = ((w >> kUpOutShift) & 0xFFu) << 1;
+    if (unknown) {
+      int dside, nside, sx, sy;
+      edge_kind(a.edge, x, y, a.nx, a.ny, &dside, &nside, &sx, &sy);
+      double wu = 0.0, t = 0.0;
+#pragma unroll
+      for (int i = 0; i < 9; ++i)
+        if (unknown & (1u << i)) {
+          wu += w_of(i);
+          t += w_of(i) * (double)nu[i];
+        }
+      t /= wu;
+      if (dside >= 0) {
+        const int slot = edge_slot(dside, x, y, a.nx, a.ny);
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+          if (!(unknown & (1u << i))) nu[i] = (Real)((double)nu[i] - t);
+        a.g_ua[slot] += (1.0 - a.frac) * t;
+        a.g_ub[slot] += a.frac * t;
+      } else {
+        const int slot = edge_slot(nside, x, y, a.nx, a.ny);
+        if (a.root[slot]) {
+#pragma unroll
+          for (int i = 0; i < 9; ++i) {
+            const int d = cx_of(i) * sx + cy_of(i) * sy;
+            if (!(unknown & (1u << i)) && d != 0) nu[i] = (Real)((double)nu[i] + d * t);
+          }
+          a.g_q[slot] -= t;
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 9; ++i)
+        if (unknown & (1u << i)) nu[i] = (Real)0;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 9; ++i)
+    store_node(a.mu_out + i * a.plane, n, nu[i], ghosts, x, y, a.nx, a.ny, a.pitch, a.per_x,
+               a.per_y);
+}
+
+// One adjoint step (kInit: the gather of lambda^0 and the first collision's
+// rate term only).  One thread per node, 32 x 8 blocks.
+template <typename Real, bool kInit>
+__global__ void __launch_bounds__(lbm::kBX * lbm::kBY) lbm_adjoint_step(const AdjArgs<Real> a) {
+  const int x = blockIdx.x * lbm::kBX + threadIdx.x;
+  const int y = blockIdx.y * lbm::kBY + threadIdx.y;
+  if (x >= a.nx || y >= a.ny) return;
+  const long long n = (long long)(y + lbm::kYO) * a.pitch + (x + lbm::kXO);
+  if (lbm::group_is_interior(blockIdx.x * lbm::kBX, y, a.nx, a.ny))
+    adjoint_node<Real, kInit, false>(a, x, y, n);
+  else
+    adjoint_node<Real, kInit, true>(a, x, y, n);
+}
+
+}  // namespace
+
+// Buffers of the reverse sweep, kept in the context between calls.
+struct AdjWork {
+  size_t plane_b = 0;  // bytes of one plane in the working precision
+  int cap_k = 0, cap_l = 0;
+  char* ck = nullptr;        // checkpoints, cap_k x 9 planes
+  char* fin = nullptr;       // final state, 9 planes
+  char* mu[2] = {nullptr, nullptr};  // adjoint state, 9 planes each
+  char* uh = nullptr;        // u history of one segment, cap_l planes
+  char* u0 = nullptr;        // u at the start of the call
+  unsigned char* roots = nullptr;  // Neumann branches of one segment, cap_l x nedge
+  double* gk = nullptr;      // [rows][pitch]
+  double* ge = nullptr;      // [3][nedge]: start, end, Neumann gradients
+  double* jn0 = nullptr;     // east-edge sums before the call, [ny]
+  double* part = nullptr;    // recompute scratch: mass partials
+  double* jn = nullptr;      //   east-edge sums
+  long long* inf = nullptr;  //   infeasible counters
+};
+
+void ctx_adjoint_free(lbm_ctx* c) {
+  AdjWork* w = c->adj;
+  if (!w) return;
+  void* ptrs[] = {w->ck, w->fin, w->mu[0], w->mu[1], w->uh, w->u0, w->roots,
+                  w->gk, w->ge,  w->jn0,   w->part,  w->jn, w->inf};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete w;
+  c->adj = nullptr;
+}
+
+namespace {
+
+lbm_status ensure_work(lbm_ctx* c, int K, int L) {
+  AdjWork* w = c->adj;
+  if (w && w->cap_k >= K && w->cap_l >= L) return LBM_OK;
+  ctx_adjoint_free(c);
+  w = new AdjWork();
+  c->adj = w;
+  w->plane_b = (size_t)c->plane * c->esize;
+  w->cap_k = K;
+  w->cap_l = L;
+  const size_t fb = 9 * w->plane_b;
+  const size_t ne = (size_t)c->nedge;
+  ACK(cudaMalloc((void**)&w->ck, (size_t)K * fb));
+  ACK(cudaMalloc((void**)&w->fin, fb));
+  ACK(cudaMalloc((void**)&w->mu[0], fb));
+  ACK(cudaMalloc((void**)&w->mu[1], fb));
+  ACK(cudaMalloc((void**)&w->uh, (size_t)L * w->plane_b));
+  ACK(cudaMalloc((void**)&w->u0, w->plane_b));
+  ACK(cudaMalloc((void**)&w->roots, (size_t)L * ne + 1));
+  ACK(cudaMalloc((void**)&w->gk, (size_t)c->plane * sizeof(double)));
+  ACK(cudaMalloc((void**)&w->ge, 3 * ne * sizeof(double)));
+  ACK(cudaMalloc((void**)&w->jn0, (size_t)c->p.ny * sizeof(double)));
+  const size_t parts = (size_t)c->grid.x * c->grid.y;
+  ACK(cudaMalloc((void**)&w->part, parts * sizeof(double)));
+  ACK(cudaMalloc((void**)&w->jn, (size_t)c->p.ny * sizeof(double)));
+  ACK(cudaMalloc((void**)&w->inf, ne * sizeof(long long)));
+  return LBM_OK;
+}
+
+template <typename Real>
+AdjArgs<Real> adj_args(lbm_ctx* c, AdjWork* w, int mc, const Real* u_n,
+                       const unsigned char* root, double frac) {
+  AdjArgs<Real> a;
+  a.mu_in = (const Real*)w->mu[mc];
+  a.mu_out = (Real*)w->mu[mc ^ 1];
+  a.link = c->link;
+  a.vel = (const Real*)c->vel;
+  a.kf = (const Real*)c->kf;
+  a.u_n = u_n;
+  a.root = root;
+  a.gk = w->gk;
+  a.g_ua = w->ge;
+  a.g_ub = w->ge + c->nedge;
+  a.g_q = w->ge + 2 * c->nedge;
+  a.plane = c->plane;
+  a.nx = c->p.nx;
+  a.ny = c->p.ny;
+  a.pitch = c->pitch;
+  a.per_x = c->p.edge[0] == LBM_EDGE_PERIODIC;
+  a.per_y = c->p.edge[2] == LBM_EDGE_PERIODIC;
+  for (int s = 0; s < 4; ++s) a.edge[s] = c->p.edge[s];
+  a.react_mode = c->p.react_mode;
+  a.omega = (Real)(1.0 / c->p.tau);
+  a.k_scalar = (Real)c->p.k_scalar;
+  a.frac = frac;
+  return a;
+}
+
+template <typename Real>
+lbm_status adjoint_impl(lbm_ctx* c, int n, int eta, int L) {
+  const int K = (n + L - 1) / L;
+  ATRY(ensure_work(c, K, L));
+  AdjWork* w = c->adj;
+  const size_t pb = w->plane_b, fb = 9 * pb;
+  const size_t ne = (size_t)c->nedge;
+  cudaStream_t st = c->stream;
+  const dim3 grid = c->grid, block = c->block;
+
+  // forward, keeping a checkpoint every L steps
+  ACK(cudaMemcpyAsync(w->u0, c->u, pb, cudaMemcpyDeviceToDevice, st));
+  ACK(cudaMemcpyAsync(w->jn0, c->jnode, (size_t)c->p.ny * sizeof(double),
+                      cudaMemcpyDeviceToDevice, st));
+  for (int j = 1; j <= n; ++j) {
+    if ((j - 1) % L == 0)
+      ACK(cudaMemcpyAsync(w->ck + (size_t)((j - 1) / L) * fb, c->f[c->cur], fb,
+                          cudaMemcpyDeviceToDevice, st));
+    ATRY(ctx_launch_step<Real>(c, step_args<Real>(c, (double)j / eta), j == n));
+    c->cur ^= 1;
+    c->steps += 1;
+  }
+  const int cur_final = c->cur;
+  const int nparts_final = c->nparts;
+  ACK(cudaMemcpyAsync(w->fin, c->f[cur_final], fb, cudaMemcpyDeviceToDevice, st));
+
+  // reverse sweep
+  ACK(cudaMemsetAsync(w->mu[0], 0, fb, st));
+  ACK(cudaMemsetAsync(w->mu[1], 0, fb, st));
+  ACK(cudaMemsetAsync(w->gk, 0, (size_t)c->plane * sizeof(double), st));
+  ACK(cudaMemsetAsync(w->ge, 0, 3 * ne * sizeof(double), st));
+  ACK(cudaMemsetAsync(w->roots, 0, (size_t)L * ne, st));
+  int mc = 0;
+  for (int s = K - 1; s >= 0; --s) {
+    const int n0 = s * L, n1 = n0 + L < n ? n0 + L : n;
+    ACK(cudaMemcpyAsync(c->f[0], w->ck + (size_t)s * fb, fb, cudaMemcpyDeviceToDevice, st));
+    c->cur = 0;
+    for (int j = n0 + 1; j <= n1; ++j) {
+      lbm::StepArgs<Real> a = step_args<Real>(c, (double)j / eta);
+      a.u_out = (Real*)(w->uh + (size_t)(j - n0 - 1) * pb);
+      a.bc_root = w->roots + (size_t)(j - n0 - 1) * ne;
+      a.partial = w->part;
+      a.jnode = w->jn;
+      a.infeasible = w->inf;
+      ATRY(ctx_launch_step<Real>(c, a, true));
+      c->cur ^= 1;
+    }
+    for (int j = n1; j > n0; --j) {
+      const auto a = adj_args<Real>(c, w, mc, (const Real*)(w->uh + (size_t)(j - n0 - 1) * pb),
+                                    w->roots + (size_t)(j - n0 - 1) * ne, (double)j / eta);
+      lbm_adjoint_step<Real, false><<<grid, block, 0, st>>>(a);
+      ACK(cudaGetLastError());
+      mc ^= 1;
+    }
+  }
+  const auto a0 = adj_args<Real>(c, w, mc, (const Real*)w->u0, w->roots, 0.0);
+  lbm_adjoint_step<Real, true><<<grid, block, 0, st>>>(a0);
+  ACK(cudaGetLastError());
+
+  // the context ends where the forward run left it
+  ACK(cudaMemcpyAsync(c->f[cur_final], w->fin, fb, cudaMemcpyDeviceToDevice, st));
+  c->cur = cur_final;
+  c->nparts = nparts_final;
+  return LBM_OK;
+}
+
+// A context the adjoint can differentiate: fixed mask, and no corner where
+// two Neumann sides meet (that root is not affine in the data).
+lbm_status check_adjoint(const lbm_ctx* c) {
+  if (c->p.dissolution)
+    return ctx_fail(LBM_ERR_STATE,
+                    "lbm_adjoint: needs a fixed mask (the context dissolves; a flip is not "
+                    "differentiable)");
+  const int* e = c->p.edge;
+  if (e[0] != LBM_EDGE_PERIODIC && e[2] != LBM_EDGE_PERIODIC)
+    for (int xs = 0; xs < 2; ++xs)
+      for (int ys = 2; ys < 4; ++ys)
+        if (e[xs] == LBM_EDGE_NEUMANN && e[ys] == LBM_EDGE_NEUMANN)
+          return ctx_fail(LBM_ERR_ARG,
+                          "lbm_adjoint: two Neumann sides meet at a corner (the corner root "
+                          "is not affine in the data)");
+  return LBM_OK;
+}
+
+lbm_status copy_out(lbm_ctx* c, double* dst, const double* src, size_t count) {
+  if (!dst) return LBM_OK;
+  ACK(cudaMemcpyAsync(dst, src, count * sizeof(double), cudaMemcpyDefault, c->stream));
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_adjoint(lbm_ctx* c, int n, int eta, int stride, const double* u_dir_t0,
+                       const double* u_dir_t1, const double* q_neu, double* J, double* grad_k,
+                       double* grad_ua, double* grad_ub, double* grad_q) {
+  ATRY(ctx_check(c));
+  if (n < 1 || eta < 1) return ctx_fail(LBM_ERR_ARG, "lbm_adjoint: need n >= 1 and eta >= 1");
+  ATRY(check_adjoint(c));
+  int L = stride > 0 ? stride : (int)std::ceil(std::sqrt((double)n));
+  if (L > n) L = n;
+  ATRY(ctx_stage_edges(c, u_dir_t0, u_dir_t1, q_neu));
+  ATRY(c->esize == 8 ? adjoint_impl<double>(c, n, eta, L) : adjoint_impl<float>(c, n, eta, L));
+  AdjWork* w = c->adj;
+  if (grad_k) ATRY(ctx_field_out_f64(c, w->gk, grad_k));
+  const size_t ne = (size_t)c->nedge;
+  ATRY(copy_out(c, grad_ua, w->ge, ne));
+  ATRY(copy_out(c, grad_ub, w->ge + ne, ne));
+  ATRY(copy_out(c, grad_q, w->ge + 2 * ne, ne));
+  if (J) {
+    std::vector<double> after(c->p.ny), before(c->p.ny);
+    ACK(cudaMemcpyAsync(after.data(), c->jnode, c->p.ny * sizeof(double),
+                        cudaMemcpyDeviceToHost, c->stream));
+    ACK(cudaMemcpyAsync(before.data(), w->jn0, c->p.ny * sizeof(double),
+                        cudaMemcpyDeviceToHost, c->stream));
+    ACK(cudaStreamSynchronize(c->stream));
+    double s = 0.0;
+    for (int y = 0; y < c->p.ny; ++y) s += after[y] - before[y];
+    *J = s;
+  }
+  return ctx_status(c);
+}
+
+}  // extern "C"

@@ -295,11 +295,11 @@ lbm_status sync_mineral(lbm_ctx* c) {
 }
 
 template <typename Real>
-lbm_status launch_step(lbm_ctx* c, double frac, bool final_step);
+lbm_status launch_step_impl(lbm_ctx* c, const lbm::StepArgs<Real>& a, bool final_step);
 
 template <>
-lbm_status launch_step<double>(lbm_ctx* c, double frac, bool final_step) {
-  auto a = step_args<double>(c, frac);
+lbm_status launch_step_impl<double>(lbm_ctx* c, const lbm::StepArgs<double>& a,
+                                    bool final_step) {
   if (final_step)
     lbm::lbm_step<double, true><<<c->grid, c->block, 0, c->stream>>>(a);
   else
@@ -310,8 +310,8 @@ lbm_status launch_step<double>(lbm_ctx* c, double frac, bool final_step) {
 }
 
 template <>
-lbm_status launch_step<float>(lbm_ctx* c, double frac, bool final_step) {
-  auto a = step_args<float>(c, frac);
+lbm_status launch_step_impl<float>(lbm_ctx* c, const lbm::StepArgs<float>& a,
+                                   bool final_step) {
   if (c->use_tma) {
     const lbm::TmaMaps& m = c->maps[c->cur];
     if (final_step)
@@ -336,7 +336,7 @@ template <typename Real>
 lbm_status run_steps(lbm_ctx* c, int n, int eta) {
   for (int j = 1; j <= n; ++j) {
     TRY(time_begin(c, 0));
-    TRY(launch_step<Real>(c, (double)j / (double)eta, j == n));
+    TRY(launch_step_impl<Real>(c, step_args<Real>(c, (double)j / (double)eta), j == n));
     TRY(time_end(c, 0));
     c->cur ^= 1;
     if (c->p.dissolution) TRY(launch_dissolve<Real>(c));
@@ -385,6 +385,7 @@ void free_ctx(lbm_ctx* c) {
                   c->status, c->diag,     c->scratch,   c->slist,      c->smin};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  ctx_adjoint_free(c);
   delete c;
 }
 
@@ -632,6 +633,47 @@ lbm_status field_out(lbm_ctx* c, const T* src, O* dst, int planes) {
 
 }  // namespace
 
+// ---- services for the other translation units (lbm_ctx.h) ----------------
+
+lbm_status ctx_fail(lbm_status s, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+lbm_status ctx_check(const lbm_ctx* c) { return check_ctx(c); }
+lbm_status ctx_status(lbm_ctx* c) { return check_status(c); }
+bool ctx_on_device(const void* p) { return on_device(p); }
+
+lbm_status ctx_stage_edges(lbm_ctx* c, const double* ua, const double* ub, const double* q) {
+  const size_t eb = (size_t)c->nedge * sizeof(double);
+  double* e = c->edge;
+  if (ua) CK(cudaMemcpyAsync(e, ua, eb, kind_from(ua), c->stream));
+  else CK(cudaMemsetAsync(e, 0, eb, c->stream));
+  const double* b = ub ? ub : ua;
+  if (b) CK(cudaMemcpyAsync(e + c->nedge, b, eb, kind_from(b), c->stream));
+  else CK(cudaMemsetAsync(e + c->nedge, 0, eb, c->stream));
+  if (q) CK(cudaMemcpyAsync(e + 2 * c->nedge, q, eb, kind_from(q), c->stream));
+  else CK(cudaMemsetAsync(e + 2 * c->nedge, 0, eb, c->stream));
+  // host-sourced edge data must not be reused before the copies complete
+  if ((ua && !on_device(ua)) || (b && !on_device(b)) || (q && !on_device(q)))
+    CK(cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+template <typename Real>
+lbm_status ctx_launch_step(lbm_ctx* c, const lbm::StepArgs<Real>& a, bool final_step) {
+  return launch_step_impl<Real>(c, a, final_step);
+}
+template lbm_status ctx_launch_step<float>(lbm_ctx*, const lbm::StepArgs<float>&, bool);
+template lbm_status ctx_launch_step<double>(lbm_ctx*, const lbm::StepArgs<double>&, bool);
+
+lbm_status ctx_field_out_f64(lbm_ctx* c, const double* padded, double* out) {
+  return field_out<double, double>(c, padded, out, 1);
+}
+
 extern "C" {
 
 int lbm_abi_version(void) { return LBM_ADE_ABI_VERSION; }
@@ -678,20 +720,32 @@ lbm_status lbm_substeps(lbm_ctx* c, int n, int eta, const double* u_dir_t0,
   TRY(check_ctx(c));
   if (n < 0 || eta < 1) return fail(LBM_ERR_ARG, "lbm_substeps: need n >= 0, eta >= 1");
   if (n == 0) return LBM_OK;
-  const size_t eb = (size_t)c->nedge * sizeof(double);
-  double* e = c->edge;
-  if (u_dir_t0) CK(cudaMemcpyAsync(e, u_dir_t0, eb, kind_from(u_dir_t0), c->stream));
-  else CK(cudaMemsetAsync(e, 0, eb, c->stream));
-  const double* b = u_dir_t1 ? u_dir_t1 : u_dir_t0;
-  if (b) CK(cudaMemcpyAsync(e + c->nedge, b, eb, kind_from(b), c->stream));
-  else CK(cudaMemsetAsync(e + c->nedge, 0, eb, c->stream));
-  if (q_neu) CK(cudaMemcpyAsync(e + 2 * c->nedge, q_neu, eb, kind_from(q_neu), c->stream));
-  else CK(cudaMemsetAsync(e + 2 * c->nedge, 0, eb, c->stream));
-  // host-sourced edge data must not be reused before the copies complete
-  if ((u_dir_t0 && !on_device(u_dir_t0)) || (b && !on_device(b)) ||
-      (q_neu && !on_device(q_neu)))
-    CK(cudaStreamSynchronize(c->stream));
+  TRY(ctx_stage_edges(c, u_dir_t0, u_dir_t1, q_neu));
   return c->esize == 8 ? run_steps<double>(c, n, eta) : run_steps<float>(c, n, eta);
+}
+
+lbm_status lbm_set_rate_field(lbm_ctx* c, const double* k_field) {
+  TRY(check_ctx(c));
+  if (!k_field) return fail(LBM_ERR_ARG, "lbm_set_rate_field: null field");
+  if (!c->kf)
+    return fail(LBM_ERR_STATE,
+                "lbm_set_rate_field: the context was created without a rate field");
+  const size_t nxy = (size_t)c->p.nx * c->p.ny;
+  double* dk = nullptr;
+  bool owned = false;
+  TRY(stage_doubles(c, k_field, nxy, &dk, &owned));
+  const int g = grid1d((long long)nxy);
+  if (c->esize == 8)
+    k_pitch_in<double><<<g, 256, 0, c->stream>>>(dk, (double*)c->kf, c->p.nx, c->p.ny, c->pitch, 1, 0.0);
+  else
+    k_pitch_in<float><<<g, 256, 0, c->stream>>>(dk, (float*)c->kf, c->p.nx, c->p.ny, c->pitch, 1, 0.0);
+  const cudaError_t e = cudaGetLastError();
+  if (owned) {
+    cudaStreamSynchronize(c->stream);
+    cudaFree(dk);
+  }
+  if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "lbm_set_rate_field: %s", cudaGetErrorString(e));
+  return LBM_OK;
 }
 
 lbm_status lbm_interface_trace(lbm_ctx* c, int npts, const double* xy, double* u_out) {

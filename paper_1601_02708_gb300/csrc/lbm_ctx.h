@@ -57,7 +57,23 @@ struct lbm_ctx {
   int ev_used[2] = {0, 0};
   double ms_sum[2] = {0.0, 0.0};
   long long launches[2] = {0, 0};
+  struct AdjWork* adj = nullptr;  // adjoint buffers (lbm_adjoint.cu), kept between calls
 };
+
+// Services of lbm_api.cu for the other translation units of the library.
+lbm_status ctx_fail(lbm_status s, const char* fmt, ...);  // message of lbm_last_error
+lbm_status ctx_check(const lbm_ctx* c);                    // null context
+lbm_status ctx_status(lbm_ctx* c);   // waits for the stream, reads the device error word
+bool ctx_on_device(const void* p);
+// Copies the edge data of one call (NULL = zeros) into c->edge.
+lbm_status ctx_stage_edges(lbm_ctx* c, const double* ua, const double* ub, const double* q);
+// One step launch with explicit arguments (fin = c->f[c->cur] for the tile
+// pipeline's tensor maps).
+template <typename Real>
+lbm_status ctx_launch_step(lbm_ctx* c, const lbm::StepArgs<Real>& a, bool final_step);
+// Padded [rows][pitch] FP64 field -> caller's [ny][nx] array (host or device).
+lbm_status ctx_field_out_f64(lbm_ctx* c, const double* padded, double* out);
+void ctx_adjoint_free(lbm_ctx* c);  // lbm_adjoint.cu
 
 
 // Kernel arguments of a context's next step (fin = the current buffer) and
@@ -79,6 +95,7 @@ inline lbm::StepArgs<Real> step_args(lbm_ctx* c, double frac) {
   a.jnode = c->jnode;
   a.partial = c->partial;
   a.status = c->status;
+  a.bc_root = nullptr;
   a.plane = c->plane;
   a.nx = c->p.nx;
   a.ny = c->p.ny;

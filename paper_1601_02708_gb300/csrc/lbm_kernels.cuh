@@ -40,6 +40,8 @@ struct StepArgs {
   double* __restrict__ jnode;          // per east-edge row: sum_t u
   double* __restrict__ partial;        // per block: sum u (final substep)
   int* __restrict__ status;            // device error word (0 = fine)
+  unsigned char* __restrict__ bc_root;  // per edge slot: 1 where the Neumann root
+                                        // set the unknowns this step (or null)
   long long plane;  // pitch * rows
   int nx, ny, pitch;
   int per_x, per_y;
@@ -198,21 +200,8 @@ __device__ __forceinline__ double step_node(const StepArgs<Real>& a, const Src& 
     const unsigned unknown = ((w >> kUpOutShift) & 0xFFu) << 1;  // bit i: direction i
     if (unknown) {
       // Boundary node: Dirichlet wins at corners, else Neumann.
-      const bool on[4] = {x == 0 && a.edge[0] != kPeriodic,
-                          x == a.nx - 1 && a.edge[1] != kPeriodic,
-                          y == 0 && a.edge[2] != kPeriodic,
-                          y == a.ny - 1 && a.edge[3] != kPeriodic};
-      int dside = -1, nside = -1, sx = 0, sy = 0;
-#pragma unroll
-      for (int s = 0; s < 4; ++s) {
-        if (!on[s]) continue;
-        if (a.edge[s] == kDirichlet && dside < 0) dside = s;
-        if (a.edge[s] == kNeumann) {
-          if (nside < 0) nside = s;
-          sx += (s == 0) ? -1 : (s == 1) ? 1 : 0;
-          sy += (s == 2) ? -1 : (s == 3) ? 1 : 0;
-        }
-      }
+      int dside, nside, sx, sy;
+      edge_kind(a.edge, x, y, a.nx, a.ny, &dside, &nside, &sx, &sy);
       bool bad;
       int slot;
       if (dside >= 0) {
@@ -225,7 +214,9 @@ __device__ __forceinline__ double step_node(const StepArgs<Real>& a, const Src& 
 #pragma unroll
         for (int i = 0; i < 9; ++i)
           fbb[i] = (unknown & (1u << opp_of(i))) ? src.own(i) : (Real)0;
-        bad = maxent_neumann(f, unknown, sx, sy, a.q[slot], fbb);
+        const int how = maxent_neumann(f, unknown, sx, sy, a.q[slot], fbb);
+        bad = how == kNeuInfeasible;
+        if (a.bc_root) a.bc_root[slot] = how == kNeuRoot;
       }
       if (bad) a.infeasible[slot] += 1;
     }

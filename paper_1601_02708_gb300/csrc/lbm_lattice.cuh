@@ -110,10 +110,13 @@ __device__ bool maxent_dirichlet(Real (&f)[9], unsigned unknown, double up) {
 // unknown has e.n = -1 and the root gives f proportional to w; at a corner
 // (n = (sx, sy)/sqrt 2) the unknowns have e.n = -1/sqrt 2 or -sqrt 2 and the
 // root condition is a quadratic in t = exp(gamma / sqrt 2), solved in closed
-// form.  Returns true if the data admit no root (R > 0; unknowns set to 0).
+// form.  Returns kNeuRoot when the root set the unknowns, else the unknowns
+// are 0 (the gamma -> -inf limit) and the return is kNeuInfeasible if the
+// data admit no root (R > 0) or kNeuZero if R = 0.
+enum { kNeuRoot = 0, kNeuInfeasible = 1, kNeuZero = 2 };
 template <typename Real>
-__device__ bool maxent_neumann(Real (&f)[9], unsigned unknown, int sx, int sy,
-                               double q, const Real (&fbb)[9]) {
+__device__ int maxent_neumann(Real (&f)[9], unsigned unknown, int sx, int sy,
+                              double q, const Real (&fbb)[9]) {
   const bool corner = (sx != 0) && (sy != 0);
   const double inv_len = corner ? 0.70710678118654752440 : 1.0;
   double R = q;
@@ -141,14 +144,14 @@ __device__ bool maxent_neumann(Real (&f)[9], unsigned unknown, int sx, int sy,
 #pragma unroll
     for (int i = 1; i < 9; ++i)
       if ((m1 | m2) & (1u << i)) f[i] = (Real)0;
-    return S < 0.0;
+    return S < 0.0 ? kNeuInfeasible : kNeuZero;
   }
   if (!corner) {
     const double scale = S / w1;
 #pragma unroll
     for (int i = 1; i < 9; ++i)
       if (m1 & (1u << i)) f[i] = (Real)(w_of(i) * scale);
-    return false;
+    return kNeuRoot;
   }
   // (w1 / (sqrt2 e)) t + (sqrt2 w2 / e) t^2 = S
   const double inv_e = 0.36787944117144233;  // exp(-1)
@@ -160,7 +163,31 @@ __device__ bool maxent_neumann(Real (&f)[9], unsigned unknown, int sx, int sy,
     if (m1 & (1u << i)) f[i] = (Real)(w_of(i) * t * inv_e);
     if (m2 & (1u << i)) f[i] = (Real)(w_of(i) * t * t * inv_e);
   }
-  return false;
+  return kNeuRoot;
+}
+
+// Boundary kind of an edge node (x, y) whose unknown set is not empty:
+// Dirichlet wins at corners (*dside >= 0, the first Dirichlet side), else
+// Neumann (*nside, the first Neumann side, with the outward normal (sx, sy)
+// summed over the node's Neumann sides).
+__device__ __forceinline__ void edge_kind(const int (&edge)[4], int x, int y, int nx, int ny,
+                                          int* dside, int* nside, int* sx, int* sy) {
+  const bool on[4] = {x == 0 && edge[0] != kPeriodic, x == nx - 1 && edge[1] != kPeriodic,
+                      y == 0 && edge[2] != kPeriodic, y == ny - 1 && edge[3] != kPeriodic};
+  *dside = -1;
+  *nside = -1;
+  *sx = 0;
+  *sy = 0;
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    if (!on[s]) continue;
+    if (edge[s] == kDirichlet && *dside < 0) *dside = s;
+    if (edge[s] == kNeumann) {
+      if (*nside < 0) *nside = s;
+      *sx += (s == 0) ? -1 : (s == 1) ? 1 : 0;
+      *sy += (s == 2) ? -1 : (s == 3) ? 1 : 0;
+    }
+  }
 }
 
 }  // namespace lbm

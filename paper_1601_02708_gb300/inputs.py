@@ -159,6 +159,26 @@ def porous_case(nx: int, ny: int, seed: int, porosity: float = 0.6,
         q_neu=edge_array(nx, ny))
 
 
+def adjoint_case(nx: int = 512, ny: int = 512, seed: int = 4, porosity: float = 0.6,
+                 tau: float = 0.7, k: float = 1e-3, k_noise: float = 0.2,
+                 umax: float = 0.05, mean_u: float = 0.15, c_in: float = 1.0) -> dict:
+    """Reactive porous lattice for the gradient workload: the disks and the
+    stream-function stirring of porous_case plus a uniform mean flow mean_u
+    along x (zeroed in solids, so the inlet signal crosses the lattice within
+    a few thousand steps), a per-node rate k (1 + k_noise U[-1, 1]) at every
+    fluid node (bulk mode, fixed mask), Dirichlet c_in west, zero-flux east,
+    periodic y, c0 = 0."""
+    solid = disk_packing(nx, ny, porosity, seed)
+    vel = streamfunction_velocity(nx, ny, seed + 1_000_003, umax=umax)
+    vel[0] += mean_u
+    vel[:, solid != 0] = 0.0
+    kf = k * (1.0 + k_noise * (2.0 * uniform_array(seed + 2_000_003, nx * ny) - 1.0))
+    return dict(
+        nx=nx, ny=ny, tau=tau, edges=(1, 2, 0, 0), solid=solid, vel=vel,
+        u0=np.zeros((ny, nx)), react_mode=2, k_field=kf.reshape(ny, nx),
+        u_dir=edge_array(nx, ny, W=c_in), q_neu=edge_array(nx, ny))
+
+
 def batch_cases(n_inst: int = 256, seed: int = 3, smin: int = 64, smax: int = 1024,
                 k: float = 1e-3, rmin: float = 8.0, rmax: float = 24.0) -> list:
     """Independent reactive porous instances: square side log-uniform in

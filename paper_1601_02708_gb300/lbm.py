@@ -161,6 +161,34 @@ class LBM:
         check(self._lib.lbm_substeps(self.handle, int(n), int(eta), a, b, q))
         self._keep = keep  # device inputs stay referenced until the next call
 
+    def set_rate_field(self, k_field):
+        """Replace the per-node rate k(x) [ny, nx] (the context must have
+        been created with a ``k_field``)."""
+        keep = []
+        check(self._lib.lbm_set_rate_field(
+            self.handle, _in_ptr(k_field, "f64", self.nx * self.ny, keep)))
+        self.synchronize()
+
+    def adjoint(self, n, eta=1, u_dir_t0=None, u_dir_t1=None, q_neu=None, stride=0):
+        """Advance n substeps as ``substeps`` does and return the outlet
+        breakthrough J (sum over the substeps of the fluid concentrations on
+        the east edge) with its gradients, computed by the library's reverse
+        sweep with sqrt(n) checkpoints: dict(J, k [ny, nx] = dJ/dk(x),
+        ua / ub [n_edge] = dJ/d(Dirichlet data at the start / end),
+        q [n_edge] = dJ/d(Neumann data)).  Fixed mask only."""
+        keep = []
+        m = self.n_edge
+        a = _in_ptr(u_dir_t0, "f64", m, keep)
+        b = _in_ptr(u_dir_t1, "f64", m, keep)
+        q = _in_ptr(q_neu, "f64", m, keep)
+        J = ctypes.c_double()
+        gk = np.empty((self.ny, self.nx))
+        ga, gb, gq = (np.empty(m) for _ in range(3))
+        check(self._lib.lbm_adjoint(self.handle, int(n), int(eta), int(stride), a, b, q,
+                                    ctypes.byref(J), gk.ctypes.data, ga.ctypes.data,
+                                    gb.ctypes.data, gq.ctypes.data))
+        return dict(J=J.value, k=gk, ua=ga, ub=gb, q=gq)
+
     KERNELS = {"auto": 0, "generic": 1, "tma": 2}
 
     def set_kernel(self, variant="auto"):
@@ -257,6 +285,62 @@ class LBM:
         check(self._lib.lbm_restore(self.handle, ptr, nb))
 
 
+def outlet_breakthrough(lbm, k_field, c_in, n, start_state, stride=0):
+    """J(k, c_in): the outlet breakthrough of ``lbm`` over n substeps from
+    ``start_state`` (a blob of ``lbm.save()``), with the rate field
+    ``k_field`` [ny, nx] and a uniform inlet value ``c_in`` on the west side
+    (zero-flux Neumann data elsewhere), as a differentiable torch function:
+    its backward returns dJ/dk and dJ/dc_in from the library's adjoint.  The
+    reverse sweep runs with the forward (one call computes both), so the
+    backward only scales the stored gradients.  ``lbm`` is left after the n
+    substeps."""
+    return _Breakthrough.apply(k_field, c_in, lbm, int(n), start_state, int(stride))
+
+
+def _breakthrough_class():
+    torch = _torch()
+
+    class Breakthrough(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, k_field, c_in, lbm, n, start_state, stride):
+            lbm.restore(start_state)
+            lbm.set_rate_field(k_field.detach().to(torch.float64).reshape(lbm.ny, lbm.nx))
+            cin = float(c_in.detach().reshape(()).item()) if torch.is_tensor(c_in) else float(c_in)
+            ud = np.zeros(lbm.n_edge)
+            if lbm.edges[0] == DIRICHLET:
+                ud[:lbm.ny] = cin
+            r = lbm.adjoint(n, 1, ud, ud, None, stride)
+            dev = k_field.device if torch.is_tensor(k_field) else "cpu"
+            gk = torch.as_tensor(r["k"], device=dev).to(k_field.dtype).reshape(k_field.shape)
+            gc = float(r["ua"][:lbm.ny].sum() + r["ub"][:lbm.ny].sum())
+            ctx.save_for_backward(gk)
+            ctx.gc = gc
+            ctx.cin_like = c_in if torch.is_tensor(c_in) else None
+            return torch.tensor(r["J"], dtype=torch.float64, device=dev)
+
+        @staticmethod
+        def backward(ctx, gJ):
+            (gk,) = ctx.saved_tensors
+            gc = None
+            if ctx.cin_like is not None:
+                gc = (gJ * ctx.gc).to(ctx.cin_like.dtype).reshape(ctx.cin_like.shape)
+            return (gJ * gk).to(gk.dtype), gc, None, None, None, None
+
+    return Breakthrough
+
+
+class _LazyFunction:
+    _cls = None
+
+    def apply(self, *args):
+        if _LazyFunction._cls is None:
+            _LazyFunction._cls = _breakthrough_class()
+        return _LazyFunction._cls.apply(*args)
+
+
+_Breakthrough = _LazyFunction()
+
+
 class LBMBatch:
     """Several lattices advanced together (Sec. 6.3, Algorithm 2 runs many
     pore-scale subdomains): every time step of the whole batch is one
@@ -350,5 +434,5 @@ class LBMBatch:
         return times
 
 
-__all__ = ["LBM", "LBMBatch", "LBMError", "PERIODIC", "DIRICHLET", "NEUMANN",
+__all__ = ["LBM", "LBMBatch", "LBMError", "outlet_breakthrough", "PERIODIC", "DIRICHLET", "NEUMANN",
            "REACT_NONE", "REACT_SURFACE", "REACT_BULK"]

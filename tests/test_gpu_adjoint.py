@@ -1,0 +1,273 @@
+"""The library's adjoint (reverse sweep with sqrt(N) checkpoints) against
+the oracle's adjoint on the same seeded inputs, in FP64 and FP32 mode, on
+lattices spanning several tiles with ragged edges; its independence of the
+checkpoint stride; the state it leaves behind; the torch autograd face; and
+the error cases."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+# FP64 mode: the same affine maps in another order of rounding; FP32 mode:
+# gradient error bound of the target (1e-4 relative to the largest entry)
+TOL = {64: 1e-10, 32: 1e-4}
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1601_02708_gb300 import build
+    build.build()
+    import paper_1601_02708_gb300 as p
+    return p
+
+
+def _case(seed, nx, ny, edges=(1, 2, 0, 0), react_mode=2, mean_u=0.08, u0_amp=0.5):
+    from paper_1601_02708_gb300 import inputs
+    rng = np.random.default_rng(seed)
+    solid = inputs.disk_packing(nx, ny, 0.75, seed, rmin=2, rmax=5)
+    vel = inputs.streamfunction_velocity(nx, ny, seed + 7, umax=0.04, solid=solid)
+    vel[0] += mean_u
+    vel[:, solid != 0] = 0
+    kf = 2e-2 * (1 + 0.2 * rng.uniform(-1, 1, (ny, nx)))
+    u0 = u0_amp * rng.uniform(0, 1, (ny, nx))
+    u0[solid != 0] = 0
+    ne = 2 * (nx + ny)
+    ua = rng.uniform(0.5, 1.5, ne)
+    ub = rng.uniform(0.5, 1.5, ne)
+    q = 0.01 * rng.uniform(-1, 1, ne)
+    return dict(nx=nx, ny=ny, tau=0.8, edges=edges, solid=solid, vel=vel,
+                react_mode=react_mode, k_field=kf, u0=u0), ua, ub, q
+
+
+def _compare(r, ref, prec):
+    assert r["J"] == pytest.approx(ref["J"], rel=TOL[prec])
+    for key in ("k", "ua", "ub", "q"):
+        scale = np.abs(ref[key]).max()
+        if scale == 0.0:  # e.g. inlet data farther from the outlet than n nodes
+            assert np.all(r[key] == 0.0), key
+        else:
+            assert np.abs(r[key] - ref[key]).max() <= TOL[prec] * scale, key
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("shape,stride", [((150, 37), 11), ((40, 150), 0), ((64, 24), 13)])
+def test_adjoint_matches_oracle(pkg, oracle_mod, prec, shape, stride):
+    case, ua, ub, q = _case(1, *shape)
+    n, eta = 120, 7
+    m = pkg.LBM(precision=prec, **case)
+    r = m.adjoint(n, eta, ua, ub, q, stride=stride)
+    o = oracle_mod.LBMOracle(**case)
+    ref = o.adjoint(n, eta, ua, ub, q)
+    _compare(r, ref, prec)
+    # the context advanced like the oracle's state
+    u = m.concentration()
+    assert np.abs(u - o.u()).max() <= (1e-12 if prec == 64 else 1e-5) * np.abs(o.u()).max()
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_adjoint_dirichlet_corners_surface_reaction(pkg, oracle_mod, prec):
+    case, ua, ub, q = _case(2, 70, 45, edges=(1, 2, 1, 1), react_mode=1)
+    m = pkg.LBM(precision=prec, **case)
+    r = m.adjoint(90, 5, ua, ub, q)
+    ref = oracle_mod.LBMOracle(**case).adjoint(90, 5, ua, ub, q)
+    _compare(r, ref, prec)
+
+
+def test_adjoint_neumann_zero_limit(pkg, oracle_mod):
+    # large positive q on part of the outlet: the zero limit there
+    case, ua, ub, q = _case(3, 48, 20)
+    q[20:30] = 5.0
+    m = pkg.LBM(precision=64, **case)
+    r = m.adjoint(60, 1, ua, ub, q)
+    ref = oracle_mod.LBMOracle(**case).adjoint(60, 1, ua, ub, q)
+    _compare(r, ref, 64)
+    assert np.all(r["q"][20:30] == 0.0)
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_stride_independence_and_final_state(pkg, prec):
+    """Every checkpoint stride recomputes the same steps, so the gradients
+    are bitwise equal; the context ends as after lbm_substeps."""
+    case, ua, ub, q = _case(4, 100, 30)
+    n, eta = 77, 3
+    results = []
+    for stride in (1, 8, 0, 77, 500):
+        m = pkg.LBM(precision=prec, **case)
+        results.append(m.adjoint(n, eta, ua, ub, q, stride=stride))
+    for r in results[1:]:
+        assert r["J"] == results[0]["J"]
+        for key in ("k", "ua", "ub", "q"):
+            assert np.array_equal(r[key], results[0][key])
+    a = pkg.LBM(precision=prec, **case)
+    b = pkg.LBM(precision=prec, **case)
+    ra = a.adjoint(n, eta, ua, ub, q)
+    b.substeps(n, eta, ua, ub, q)
+    assert np.array_equal(a.concentration(), b.concentration())
+    assert np.array_equal(a.populations(), b.populations())
+    da, db = a.diagnostics(), b.diagnostics()
+    assert da == db
+    # a second call reuses the buffers and continues from the new state
+    r2 = a.adjoint(10, 1, ua, ua, q)
+    b2 = pkg.LBM(precision=prec, **case)
+    b2.substeps(n, eta, ua, ub, q)
+    assert r2["J"] == pytest.approx(b2.adjoint(10, 1, ua, ua, q)["J"], rel=0)
+    assert ra["J"] > 0
+
+
+def test_inlet_homogeneity(pkg):
+    """c0 = 0 and zero-flux outlet: J is homogeneous of degree one in the
+    inlet value, so c_in dJ/dc_in = J."""
+    case, _, _, _ = _case(5, 80, 32, u0_amp=0.0)
+    m = pkg.LBM(precision=64, **case)
+    ud = np.zeros(2 * (80 + 32))
+    ud[:32] = 1.3
+    r = m.adjoint(150, 1, ud, ud, None)
+    dj = r["ua"][:32].sum() + r["ub"][:32].sum()
+    assert r["J"] > 0
+    assert 1.3 * dj == pytest.approx(r["J"], rel=1e-12)
+
+
+def test_autograd_function(pkg):
+    import torch
+    case, _, _, _ = _case(6, 64, 32, u0_amp=0.0)
+    m = pkg.LBM(precision=64, **case)
+    start = m.save()
+    k = torch.tensor(case["k_field"], dtype=torch.float64, device="cuda", requires_grad=True)
+    c_in = torch.tensor(0.9, dtype=torch.float64, requires_grad=True)
+    J = pkg.outlet_breakthrough(m, k, c_in, 100, start)
+    (2.0 * J).backward()
+    ud = np.zeros(2 * (64 + 32))
+    ud[:32] = 0.9
+    m.restore(start)
+    ref = m.adjoint(100, 1, ud, ud, None)
+    assert J.item() == pytest.approx(ref["J"], rel=1e-14)
+    assert np.allclose(k.grad.cpu().numpy(), 2.0 * ref["k"], rtol=1e-14, atol=0)
+    assert c_in.grad.item() == pytest.approx(
+        2.0 * (ref["ua"][:32].sum() + ref["ub"][:32].sum()), rel=1e-14)
+
+
+def test_adjoint_errors(pkg):
+    m = pkg.LBM(16, 16, 0.8, edges=(2, 2, 2, 2), precision=32)
+    with pytest.raises(pkg.LBMError):
+        m.adjoint(5)  # Neumann corners
+    d = pkg.LBM(16, 16, 0.8, edges=(1, 2, 0, 0), precision=32, react_mode=1, k=1e-3,
+                dissolution=True, solid=np.eye(16, dtype=np.uint8))
+    with pytest.raises(pkg.LBMError):
+        d.adjoint(5)  # dissolution
+    p = pkg.LBM(16, 16, 0.8, edges=(1, 2, 0, 0), precision=32)
+    with pytest.raises(pkg.LBMError):
+        p.adjoint(0)
+    with pytest.raises(pkg.LBMError):
+        p.set_rate_field(np.zeros((16, 16)))  # created without a rate field
+
+
+# ---- the gradient workload at full size: 512 x 512, 5000 steps ------------
+
+@pytest.fixture(scope="module")
+def c4():
+    from paper_1601_02708_gb300 import inputs
+    c = inputs.adjoint_case()
+    case = {k: c[k] for k in ("nx", "ny", "tau", "edges", "solid", "vel", "react_mode",
+                              "k_field", "u0")}
+    return case, c["u_dir"], c["q_neu"]
+
+
+@pytest.fixture(scope="module")
+def c4_fp64(pkg, c4):
+    case, ud, q = c4
+    m = pkg.LBM(precision=64, **case)
+    start = m.save()
+    r = m.adjoint(5000, 1, ud, ud, q)
+    return m, start, r
+
+
+def test_config4_central_differences_on_32_nodes(pkg, c4, c4_fp64):
+    """FP64 mode, delta = 1e-3 k(x), 32 fluid nodes drawn with seed 44."""
+    case, ud, q = c4
+    m, start, r = c4_fp64
+    assert r["J"] > 100.0  # the inlet signal has broken through
+    fluid = np.flatnonzero(case["solid"].reshape(-1) == 0)
+    pick = np.random.default_rng(44).choice(fluid, 32, replace=False)
+    k0 = case["k_field"].reshape(-1)
+    worst, checked = 0.0, 0
+    for idx in pick:
+        d = 1e-3 * k0[idx]
+        js = []
+        for sgn in (1.0, -1.0):
+            kk = k0.copy()
+            kk[idx] += sgn * d
+            m.restore(start)
+            m.set_rate_field(kk)
+            m.substeps(5000, 1, ud, ud, q)
+            js.append(m.diagnostics()["outlet_J"])
+        fd = (js[0] - js[1]) / (2 * d)
+        g = r["k"].reshape(-1)[idx]
+        # rounding of J itself limits what a difference quotient resolves
+        noise = 8 * np.finfo(float).eps * abs(r["J"]) / (2 * d)
+        if abs(fd) < 1e3 * noise:  # (nearly) unreached pocket: below resolution
+            assert abs(g - fd) <= 10 * noise
+            continue
+        # 1e-4 relative, beyond the difference quotient's own rounding
+        worst = max(worst, (abs(g - fd) - 4 * noise) / abs(fd))
+        checked += 1
+    print("FD nodes checked", checked, "worst relative error", worst)
+    assert worst <= 1e-4 and checked >= 16
+    # the inlet value: central difference and homogeneity (c0 = 0)
+    js = []
+    for c_in in (1.0 + 1e-3, 1.0 - 1e-3):
+        m.restore(start)
+        m.set_rate_field(k0)
+        u = ud * c_in
+        m.substeps(5000, 1, u, u, q)
+        js.append(m.diagnostics()["outlet_J"])
+    ny = case["ny"]
+    dcin = r["ua"][:ny].sum() + r["ub"][:ny].sum()
+    assert dcin == pytest.approx((js[0] - js[1]) / 2e-3, rel=1e-6)
+    assert dcin == pytest.approx(r["J"], rel=1e-12)
+
+
+def test_config4_fp32_against_fp64(pkg, c4, c4_fp64):
+    case, ud, q = c4
+    _, _, r64 = c4_fp64
+    m = pkg.LBM(precision=32, **case)
+    r32 = m.adjoint(5000, 1, ud, ud, q)
+    assert r32["J"] == pytest.approx(r64["J"], rel=1e-4)
+    assert np.abs(r32["k"] - r64["k"]).max() <= 1e-4 * np.abs(r64["k"]).max()
+    ny = case["ny"]
+    assert (r32["ua"][:ny].sum() + r32["ub"][:ny].sum()) == pytest.approx(
+        r64["ua"][:ny].sum() + r64["ub"][:ny].sum(), rel=1e-4)
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_config4_lattice_matches_oracle_adjoint(pkg, oracle_mod, c4, prec):
+    """The full 512 x 512 lattice against the oracle's adjoint over 300 steps
+    (the oracle keeps every step's concentration, so the run is short), from
+    a seeded nonzero start so that the outlet sees concentration at once."""
+    case, ud, q = c4
+    case = dict(case)
+    rng = np.random.default_rng(9)
+    u0 = rng.uniform(0, 1, (case["ny"], case["nx"]))
+    u0[case["solid"] != 0] = 0
+    case["u0"] = u0
+    r = pkg.LBM(precision=prec, **case).adjoint(300, 1, ud, ud, q)
+    ref = oracle_mod.LBMOracle(**case).adjoint(300, 1, ud, ud, q)
+    if prec == 32:
+        # An outlet node whose west neighbours are solid gets its outgoing
+        # populations by bounce-back only; its Neumann sum S decays towards 0
+        # and changes sign under over-relaxation, and the unknowns follow
+        # max(S, 0) (root or zero limit).  Where S is within FP32 rounding of
+        # 0 the branch taken differs from FP64, and dJ/dq -- a sum of O(J)
+        # sensitivities over the steps with the root -- differs with it.
+        # dJ/dq is compared at outlet nodes fed by fluid neighbours.
+        ny, nx = case["ny"], case["nx"]
+        sol = case["solid"]
+        fed = np.array([not (sol[(y - 1) % ny, nx - 2] or sol[y, nx - 2] or sol[(y + 1) % ny, nx - 2])
+                        for y in range(ny)])
+        keep = np.ones(r["q"].size, bool)
+        keep[ny:2 * ny] = fed
+        r = dict(r, q=np.where(keep, r["q"], 0.0))
+        ref = dict(ref, q=np.where(keep, ref["q"], 0.0))
+    _compare(r, ref, prec)
