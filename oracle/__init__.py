@@ -72,6 +72,9 @@ def _load():
         lib.or_trace_point.argtypes = [P, D, D]
         lib.or_maxent_dirichlet.restype = I
         lib.or_maxent_dirichlet.argtypes = [P, P, D]
+        lib.or_lbm_clone.restype = P
+        lib.or_lbm_clone.argtypes = [P]
+        lib.or_lbm_assign.argtypes = [P, P]
         lib.or_lbm_adjoint.restype = I
         lib.or_lbm_adjoint.argtypes = [P, I, I, P, P, P, P, P, P, P, P]
         lib.or_maxent_neumann.restype = I
@@ -146,6 +149,19 @@ class LBMOracle:
         b = _f64(u_dir_t1 if u_dir_t1 is not None else u_dir_t0, (self.n_edge,))
         q = _f64(q_neu, (self.n_edge,))
         self._lib.or_lbm_substeps(self._h, int(n), int(eta), _ptr(a), _ptr(b), _ptr(q))
+
+    def snapshot(self):
+        """Deep copy of the evolving state (for the Schwarz rollback)."""
+        snap = LBMOracle.__new__(LBMOracle)
+        snap.__dict__.update(self.__dict__)
+        snap._h = self._lib.or_lbm_clone(self._h)
+        if not snap._h:
+            raise MemoryError("oracle allocation failed")
+        return snap
+
+    def rollback(self, snap):
+        """Restore the state saved by ``snapshot``."""
+        self._lib.or_lbm_assign(self._h, snap._h)
 
     def adjoint(self, n, eta=1, u_dir_t0=None, u_dir_t1=None, q_neu=None):
         """Advance n substeps (as ``substeps``) and return the outlet

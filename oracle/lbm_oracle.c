@@ -738,3 +738,34 @@ int or_lbm_adjoint(or_lbm *o, int nsteps, int eta, const double *ua,
   free(uh); free(root); free(gbar); free(pbar); free(Fbar);
   return 0;
 }
+
+/* ---- snapshots for the Schwarz rollback ------------------------------------
+ * Every Schwarz iteration of a coarse step restarts the fine solver from its
+ * state at t_n (Algorithm 1 repeats the substeps of one coarse step).  A
+ * snapshot is a deep copy of the evolving state: populations, concentration,
+ * mask, mineral and the counters. */
+or_lbm *or_lbm_clone(const or_lbm *o) {
+  or_lbm *c = or_lbm_new(o->nx, o->ny, o->edge, o->tau, o->react_mode, o->k_scalar,
+                         o->k, o->dissolution, o->solid, o->vel, o->mineral, NULL);
+  if (!c) return NULL;
+  size_t N = nn(o);
+  memcpy(c->f, o->f, NQ * N * sizeof(double));
+  memcpy(c->u, o->u, N * sizeof(double));
+  c->steps = o->steps; c->bc_infeasible = o->bc_infeasible; c->flips = o->flips;
+  c->newton_iters = o->newton_iters; c->newton_fail = o->newton_fail;
+  c->J = o->J; c->reacted = o->reacted;
+  return c;
+}
+
+/* Overwrite the evolving state of dst (same lattice) with that of src. */
+void or_lbm_assign(or_lbm *dst, const or_lbm *src) {
+  size_t N = nn(src);
+  memcpy(dst->f, src->f, NQ * N * sizeof(double));
+  memcpy(dst->u, src->u, N * sizeof(double));
+  memcpy(dst->solid, src->solid, N);
+  memcpy(dst->mineral, src->mineral, N * sizeof(double));
+  memcpy(dst->k, src->k, N * sizeof(double));
+  dst->steps = src->steps; dst->bc_infeasible = src->bc_infeasible; dst->flips = src->flips;
+  dst->newton_iters = src->newton_iters; dst->newton_fail = src->newton_fail;
+  dst->J = src->J; dst->reacted = src->reacted;
+}
