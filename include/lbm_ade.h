@@ -256,6 +256,49 @@ lbm_status lbm_batch_time_steps(lbm_batch* b, int n, float* ms);
 void lbm_batch_destroy(lbm_batch* b);  /* does not destroy the members */
 const char* lbm_batch_last_error(void);
 
+/* ---- the continuum solver of the hybrid method: Q1 finite elements --------
+ * Sec. 3 (Galerkin, Sec. 3.1.1; SUPG, Sec. 3.1.2 Eq. "SUPG", "SUPG_tau") and
+ * Sec. 6.1.1 (generalized trapezoidal rule, Eq. "FEM_discrete"): the
+ * advection-diffusion equation dc/dt + v.grad c - D lap c = 0 with uniform D
+ * and v on a structured mesh of nex x ney bilinear elements covering
+ * [x0, x0 + nex hx] x [y0, y0 + ney hy], elements optionally switched off
+ * (a hole where a lattice lives).  Each step solves
+ *     (M + theta dt K) d^{n+1} = (M - (1 - theta) dt K) d^n
+ * with the listed Dirichlet nodes at their prescribed values; every other
+ * boundary (the mesh edge, the edge of switched-off elements) is zero-flux.
+ * Nodes are numbered j (nex + 1) + i; nodal vectors are FP64.
+ * The linear system is solved on the GPU (Jacobi-preconditioned BiCGSTAB,
+ * FP64, to the relative residual tol).  Pointers may be host or device
+ * memory; everything runs on `stream`.  Errors: LBM_ERR_ARG (bad parameters or
+ * node ids), LBM_ERR_STATE (no convergence / breakdown of the linear solve),
+ * LBM_ERR_NOMEM, LBM_ERR_CUDA; the message is in lbm_last_error(). */
+typedef struct lbm_fem lbm_fem;
+typedef struct {
+  int nex, ney;            /* elements along x and y */
+  double x0, y0, hx, hy;   /* origin and element size */
+  double D, vx, vy;        /* diffusivity, velocity */
+  double theta, dt;        /* trapezoidal weight in [0, 1], time step */
+  int supg;                /* 1: SUPG test functions, 0: Galerkin */
+  double tol;              /* relative residual of the solve (<= 0: 1e-12) */
+  int max_iter;            /* solver iterations per step (<= 0: 1000) */
+} lbm_fem_params;
+/* elem_active [ney][nex] (NULL: all on); dir_nodes [n_dir] node ids of the
+ * Dirichlet nodes, in the order of the values lbm_fem_step takes; d0 the
+ * initial nodal values (NULL: zero). */
+lbm_status lbm_fem_init(lbm_fem** out, const lbm_fem_params* p, const uint8_t* elem_active,
+                        int n_dir, const int* dir_nodes, const double* d0, void* stream);
+/* One time step; dir_values [n_dir] are the Dirichlet values at t^{n+1}. */
+lbm_status lbm_fem_step(lbm_fem* f, const double* dir_values);
+/* Finite-element (bilinear) interpolant of the current d at npts points
+ * xy [npts][2] (physical coordinates; points outside are clamped to the
+ * nearest element): the coarse-to-fine transfer of Sec. 5.1 / 6.2 (iii). */
+lbm_status lbm_fem_interpolate(lbm_fem* f, int npts, const double* xy, double* out);
+lbm_status lbm_fem_get(lbm_fem* f, double* d);        /* [(ney+1)(nex+1)] */
+lbm_status lbm_fem_set(lbm_fem* f, const double* d);  /* e.g. the Schwarz rollback */
+/* Iterations and relative residual of the last solve. */
+lbm_status lbm_fem_solver_info(lbm_fem* f, int* iters, double* rel_resid);
+void lbm_fem_destroy(lbm_fem* f);
+
 /* FP64 sum of a concentration field that allocates nothing -- the paper has
  * no counterpart; this entry point exists for callers that cannot allocate
  * device memory when they need the sum: code recording a CUDA graph (an

@@ -29,6 +29,15 @@ class Params(ctypes.Structure):
                 ("k_scalar", ctypes.c_double), ("dissolution", ctypes.c_int)]
 
 
+class FemParams(ctypes.Structure):
+    _fields_ = [("nex", ctypes.c_int), ("ney", ctypes.c_int),
+                ("x0", ctypes.c_double), ("y0", ctypes.c_double),
+                ("hx", ctypes.c_double), ("hy", ctypes.c_double),
+                ("D", ctypes.c_double), ("vx", ctypes.c_double), ("vy", ctypes.c_double),
+                ("theta", ctypes.c_double), ("dt", ctypes.c_double),
+                ("supg", ctypes.c_int), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int)]
+
+
 class Diag(ctypes.Structure):
     _fields_ = [("mass", ctypes.c_double), ("outlet_J", ctypes.c_double),
                 ("steps", ctypes.c_longlong), ("bc_infeasible", ctypes.c_longlong),
@@ -70,6 +79,12 @@ def load():
             "lbm_kernel_timing": [P, I],
             "lbm_set_kernel": [P, I],
             "lbm_set_rate_field": [P, P],
+            "lbm_fem_init": [ctypes.POINTER(P), ctypes.POINTER(FemParams), P, I, P, P, P],
+            "lbm_fem_step": [P, P],
+            "lbm_fem_interpolate": [P, I, P, P],
+            "lbm_fem_get": [P, P],
+            "lbm_fem_set": [P, P],
+            "lbm_fem_solver_info": [P, ctypes.POINTER(I), ctypes.POINTER(D)],
             "lbm_adjoint": [P, I, I, I, P, P, P, ctypes.POINTER(D), P, P, P, P],
             "lbm_kernel_times_read": [P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong),
                                       ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong)],
@@ -94,6 +109,8 @@ def load():
         lib.lbm_batch_destroy.restype = None
         lib.lbm_batch_last_error.argtypes = []
         lib.lbm_batch_last_error.restype = ctypes.c_char_p
+        lib.lbm_fem_destroy.argtypes = [P]
+        lib.lbm_fem_destroy.restype = None
         lib.lbm_destroy.argtypes = [P]
         lib.lbm_destroy.restype = None
         lib.lbm_last_error.argtypes = []

@@ -1,0 +1,586 @@
+// lbm_fem.cu -- the continuum solver of the hybrid method: Q1 finite
+// elements for the advection-diffusion equation on a structured rectangular
+// mesh, stepped on the GPU (lbm_fem_*, declared in include/lbm_ade.h).
+//
+// Sec. 3: Galerkin weak form (Sec. 3.1.1) and SUPG (Sec. 3.1.2, Eq. "SUPG",
+// "SUPG_tau"); Sec. 6.1.1: semi-discrete M d' + K d = 0 advanced by the
+// generalized trapezoidal rule (Eq. "FEM_discrete"),
+//     (M + theta dt K) d^{n+1} = (M - (1 - theta) dt K) d^n,
+// Dirichlet nodes taking their prescribed values at t^{n+1}; every other
+// boundary (the mesh edge and the edge of switched-off elements) is
+// zero-flux.
+//
+// The element matrices of a bilinear element with uniform D and v are
+// tensor products of the 1-D linear-element matrices
+//     m(h) = h/6 [[2,1],[1,2]], k(h) = 1/h [[1,-1],[-1,1]],
+//     c = 1/2 [[-1,1],[-1,1]]  (int phi_a phi_b'),
+// assembled once on the host into 9-diagonal (one per neighbour offset)
+// arrays of A = M + theta dt K and B = M - (1 - theta) dt K.  The rows of
+// Dirichlet and inactive nodes are the identity in A and zero in B.  Each step
+// solves A x = B d^n (+ prescribed values) by Jacobi-preconditioned
+// BiCGSTAB in FP64: five vector kernels and three one-block scalar kernels
+// per iteration, dot products folded in a fixed order (deterministic), the
+// scalars kept on the device, the residual read back every few iterations.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "lbm_ade.h"
+#include "lbm_ctx.h"
+
+namespace {
+
+#define FCK(call)                                                                \
+  do {                                                                           \
+    cudaError_t e_ = (call);                                                     \
+    if (e_ != cudaSuccess)                                                       \
+      return ctx_fail(e_ == cudaErrorMemoryAllocation ? LBM_ERR_NOMEM : LBM_ERR_CUDA, \
+                      "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),    \
+                      __FILE__, __LINE__);                                       \
+  } while (0)
+
+#define FTRY(...)                   \
+  do {                              \
+    lbm_status s_ = (__VA_ARGS__);  \
+    if (s_ != LBM_OK) return s_;    \
+  } while (0)
+
+constexpr int kThreads = 256;
+constexpr int kCheckEvery = 8;  // iterations between residual read-backs
+
+// Device scalars of the solver.
+struct Scal {
+  double rho, alpha, omega, beta;
+  double bnorm2, rnorm2;
+  int done;      // converged (or broken down): every kernel returns at once
+  int breakdown;
+};
+
+struct Vec {
+  double *x, *r, *rhat, *p, *phat, *v, *s, *shat, *t;
+};
+
+// Row (i, j) of A x for the 9-diagonal matrix: A[k][row] multiplies the
+// neighbour at offset di = k % 3 - 1, dj = k / 3 - 1.
+__device__ __forceinline__ double spmv_row(const double* __restrict__ A, const double* __restrict__ x,
+                                           int i, int j, int nxn, int nyn, long long n) {
+  const long long row = (long long)j * nxn + i;
+  double acc = 0.0;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const int di = k % 3 - 1, dj = k / 3 - 1;
+    const int ii = i + di, jj = j + dj;
+    if (ii < 0 || ii >= nxn || jj < 0 || jj >= nyn) continue;
+    acc += A[k * n + row] * x[(long long)jj * nxn + ii];
+  }
+  return acc;
+}
+
+__device__ __forceinline__ void block_dot(double v0, double v1, double* part0, double* part1) {
+  __shared__ double s0[kThreads / 32], s1[kThreads / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v0 += __shfl_down_sync(0xffffffffu, v0, o);
+    v1 += __shfl_down_sync(0xffffffffu, v1, o);
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) {
+    s0[w] = v0;
+    s1[w] = v1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int k = 0; k < kThreads / 32; ++k) {
+      a += s0[k];
+      b += s1[k];
+    }
+    if (part0) part0[blockIdx.x] = a;
+    if (part1) part1[blockIdx.x] = b;
+  }
+}
+
+__device__ __forceinline__ double fold(const double* part, int nb) {
+  double s = 0.0;
+  for (int k = 0; k < nb; ++k) s += part[k];
+  return s;
+}
+
+// rhs b = B d (rows of fixed nodes: their values), x0 = d with the fixed
+// values, r = b - A x0 computed by the next kernel.
+__global__ void __launch_bounds__(kThreads)
+    k_rhs(const double* __restrict__ B, const double* __restrict__ d, const int* __restrict__ fixed_id,
+          const double* __restrict__ fixed_val, double* __restrict__ b, double* __restrict__ x,
+          int nxn, int nyn, double* part_bb) {
+  const long long n = (long long)nxn * nyn;
+  const long long p = blockIdx.x * (long long)kThreads + threadIdx.x;
+  double bb = 0.0;
+  if (p < n) {
+    const int i = (int)(p % nxn), j = (int)(p / nxn);
+    const int f = fixed_id[p];
+    double bv, xv;
+    if (f >= 0) {
+      bv = fixed_val[f];
+      xv = bv;
+    } else if (f == -2) {  // inactive
+      bv = 0.0;
+      xv = 0.0;
+    } else {
+      bv = spmv_row(B, d, i, j, nxn, nyn, n);
+      xv = d[p];
+    }
+    b[p] = bv;
+    x[p] = xv;
+    // the residual is measured against the free rows' right-hand side (the
+    // prescribed rows are met exactly from the start and stay so)
+    bb = f == -1 ? bv * bv : 0.0;
+  }
+  block_dot(bb, 0.0, part_bb, nullptr);
+}
+
+// r = b - A x, rhat = r, p = 0, v = 0, partials of (r, r).
+__global__ void __launch_bounds__(kThreads)
+    k_init_res(const double* __restrict__ A, const double* __restrict__ b, Vec w, int nxn, int nyn,
+               double* part_rr) {
+  const long long n = (long long)nxn * nyn;
+  const long long p = blockIdx.x * (long long)kThreads + threadIdx.x;
+  double rr = 0.0;
+  if (p < n) {
+    const int i = (int)(p % nxn), j = (int)(p / nxn);
+    const double r = b[p] - spmv_row(A, w.x, i, j, nxn, nyn, n);
+    w.r[p] = r;
+    w.rhat[p] = r;
+    w.p[p] = 0.0;
+    w.v[p] = 0.0;
+    rr = r * r;
+  }
+  block_dot(rr, 0.0, part_rr, nullptr);
+}
+
+__global__ void k_scal_init(Scal* sc, const double* part_bb, const double* part_rr, int nb,
+                            double tol) {
+  if (threadIdx.x != 0) return;
+  sc->bnorm2 = fold(part_bb, nb);
+  sc->rnorm2 = fold(part_rr, nb);
+  sc->rho = sc->rnorm2;  // rhat = r0
+  sc->alpha = 1.0;
+  sc->omega = 1.0;
+  sc->beta = 0.0;
+  sc->breakdown = 0;
+  sc->done = (sc->rnorm2 <= tol * tol * sc->bnorm2) ? 1 : 0;
+}
+
+// p = r + beta (p - omega v); phat = p / diag(A)
+__global__ void __launch_bounds__(kThreads)
+    k_update_p(const double* __restrict__ A, Vec w, const Scal* sc, long long n) {
+  if (sc->done) return;
+  const long long p = blockIdx.x * (long long)kThreads + threadIdx.x;
+  if (p >= n) return;
+  const double pv = w.r[p] + sc->beta * (w.p[p] - sc->omega * w.v[p]);
+  w.p[p] = pv;
+  w.phat[p] = pv / A[4 * n + p];
+}
+
+// y = A xin and the partial dots (rhat, y) [mode 0] or (y, s), (y, y) [mode 1]
+template <int kMode>
+__global__ void __launch_bounds__(kThreads)
+    k_spmv_dot(const double* __restrict__ A, const double* __restrict__ xin, double* __restrict__ y,
+               const double* __restrict__ other, const Scal* sc, int nxn, int nyn,
+               double* part0, double* part1) {
+  if (sc->done) return;
+  const long long n = (long long)nxn * nyn;
+  const long long p = blockIdx.x * (long long)kThreads + threadIdx.x;
+  double d0 = 0.0, d1 = 0.0;
+  if (p < n) {
+    const int i = (int)(p % nxn), j = (int)(p / nxn);
+    const double yv = spmv_row(A, xin, i, j, nxn, nyn, n);
+    y[p] = yv;
+    d0 = yv * other[p];
+    d1 = yv * yv;
+  }
+  block_dot(d0, kMode ? d1 : 0.0, part0, kMode ? part1 : nullptr);
+}
+
+// alpha = rho / (rhat, v)
+__global__ void k_scal_alpha(Scal* sc, const double* part, int nb) {
+  if (threadIdx.x != 0 || sc->done) return;
+  const double rv = fold(part, nb);
+  if (rv == 0.0 || !isfinite(rv)) {
+    sc->breakdown = 1;
+    sc->done = 1;
+    return;
+  }
+  sc->alpha = sc->rho / rv;
+}
+
+// s = r - alpha v; shat = s / diag(A)
+__global__ void __launch_bounds__(kThreads)
+    k_update_s(const double* __restrict__ A, Vec w, const Scal* sc, long long n) {
+  if (sc->done) return;
+  const long long p = blockIdx.x * (long long)kThreads + threadIdx.x;
+  if (p >= n) return;
+  const double s = w.r[p] - sc->alpha * w.v[p];
+  w.s[p] = s;
+  w.shat[p] = s / A[4 * n + p];
+}
+
+// omega = (t, s) / (t, t)
+__global__ void k_scal_omega(Scal* sc, const double* part_ts, const double* part_tt, int nb) {
+  if (threadIdx.x != 0 || sc->done) return;
+  const double ts = fold(part_ts, nb), tt = fold(part_tt, nb);
+  sc->omega = tt > 0.0 ? ts / tt : 0.0;
+}
+
+// x += alpha phat + omega shat; r = s - omega t; partials (rhat, r), (r, r)
+__global__ void __launch_bounds__(kThreads)
+    k_update_x(Vec w, const Scal* sc, long long n, double* part_rr_hat, double* part_rr) {
+  if (sc->done) return;
+  const long long p = blockIdx.x * (long long)kThreads + threadIdx.x;
+  double a = 0.0, b = 0.0;
+  if (p < n) {
+    w.x[p] += sc->alpha * w.phat[p] + sc->omega * w.shat[p];
+    const double r = w.s[p] - sc->omega * w.t[p];
+    w.r[p] = r;
+    a = w.rhat[p] * r;
+    b = r * r;
+  }
+  block_dot(a, b, part_rr_hat, part_rr);
+}
+
+// rho_new, beta, convergence
+__global__ void k_scal_rho(Scal* sc, const double* part_a, const double* part_b, int nb,
+                           double tol, int* iters) {
+  if (threadIdx.x != 0 || sc->done) return;
+  const double rho_new = fold(part_a, nb);
+  sc->rnorm2 = fold(part_b, nb);
+  *iters += 1;
+  if (sc->rnorm2 <= tol * tol * sc->bnorm2) {
+    sc->done = 1;
+    return;
+  }
+  if (rho_new == 0.0 || sc->omega == 0.0 || !isfinite(rho_new)) {
+    sc->breakdown = 1;
+    sc->done = 1;
+    return;
+  }
+  sc->beta = (rho_new / sc->rho) * (sc->alpha / sc->omega);
+  sc->rho = rho_new;
+}
+
+// FE interpolation (bilinear on the containing element) of d at points
+__global__ void k_interp(const double* __restrict__ d, int nex, int ney, double x0, double y0,
+                         double hx, double hy, const double* __restrict__ xy, int npts,
+                         double* __restrict__ out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= npts) return;
+  const double px = (xy[2 * k] - x0) / hx, py = (xy[2 * k + 1] - y0) / hy;
+  int i = (int)floor(px), j = (int)floor(py);
+  i = i < 0 ? 0 : (i > nex - 1 ? nex - 1 : i);
+  j = j < 0 ? 0 : (j > ney - 1 ? ney - 1 : j);
+  const double gx = px - i, gy = py - j;
+  const int nxn = nex + 1;
+  const double* r0 = d + (long long)j * nxn + i;
+  const double* r1 = r0 + nxn;
+  out[k] = r0[0] * (1 - gx) * (1 - gy) + r0[1] * gx * (1 - gy) + r1[1] * gx * gy +
+           r1[0] * (1 - gx) * gy;
+}
+
+}  // namespace
+
+struct lbm_fem {
+  lbm_fem_params p;
+  int nxn = 0, nyn = 0;
+  long long n = 0;
+  int nb = 0;  // blocks of the vector kernels
+  int n_dir = 0;
+  cudaStream_t stream = nullptr;
+  double* A = nullptr;  // [9][n]
+  double* B = nullptr;  // [9][n]
+  double* d = nullptr;  // state
+  double* b = nullptr;  // right-hand side
+  Vec w{};
+  double* vecs = nullptr;   // storage of w
+  int* fixed_id = nullptr;  // per node: index into the prescribed values, -1 free, -2 inactive
+  double* fixed_val = nullptr;
+  double* part = nullptr;   // 4 x nb partials
+  Scal* sc = nullptr;
+  int* iters = nullptr;
+  double* scratch = nullptr;  // staging of host points / results of lbm_fem_interpolate
+  size_t scratch_n = 0;
+  int last_iters = 0;
+  double last_resid = 0.0;
+};
+
+namespace {
+
+void fem_free(lbm_fem* f) {
+  void* ptrs[] = {f->A, f->B, f->d, f->b, f->vecs, f->fixed_id, f->fixed_val, f->part,
+                  f->sc, f->iters, f->scratch};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete f;
+}
+
+// Element matrices (Galerkin + SUPG) of one hx x hy element in the local
+// node order (0,0), (1,0), (1,1), (0,1).
+void element(const lbm_fem_params& p, double tau, double Me[4][4], double Ke[4][4]) {
+  const double mx[2][2] = {{p.hx / 3, p.hx / 6}, {p.hx / 6, p.hx / 3}};
+  const double my[2][2] = {{p.hy / 3, p.hy / 6}, {p.hy / 6, p.hy / 3}};
+  const double kx[2][2] = {{1 / p.hx, -1 / p.hx}, {-1 / p.hx, 1 / p.hx}};
+  const double ky[2][2] = {{1 / p.hy, -1 / p.hy}, {-1 / p.hy, 1 / p.hy}};
+  const double c[2][2] = {{-0.5, 0.5}, {-0.5, 0.5}};  // int phi_a phi_b'
+  const int loc[4][2] = {{0, 0}, {1, 0}, {1, 1}, {0, 1}};
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) {
+      const int ia = loc[a][0], ja = loc[a][1], ib = loc[b][0], jb = loc[b][1];
+      const double mass = mx[ia][ib] * my[ja][jb];
+      const double adv = p.vx * c[ia][ib] * my[ja][jb] + p.vy * mx[ia][ib] * c[ja][jb];
+      const double dif = p.D * (kx[ia][ib] * my[ja][jb] + mx[ia][ib] * ky[ja][jb]);
+      // SUPG: the test function gains tau v.grad N_a
+      const double adv_t = p.vx * c[ib][ia] * my[ja][jb] + p.vy * mx[ia][ib] * c[jb][ja];
+      const double vv = p.vx * p.vx * kx[ia][ib] * my[ja][jb] +
+                        p.vy * p.vy * mx[ia][ib] * ky[ja][jb] +
+                        p.vx * p.vy * (c[ib][ia] * c[ja][jb] + c[ia][ib] * c[jb][ja]);
+      Me[a][b] = mass + tau * adv_t;
+      Ke[a][b] = adv + dif + tau * vv;
+    }
+}
+
+// tau_e = h / (2|v|) (coth Pe - 1/Pe), Pe = |v| h / (2D), h the element
+// length along the flow, min(hx / |v^_x|, hy / |v^_y|).
+double supg_tau(const lbm_fem_params& p) {
+  const double speed = std::hypot(p.vx, p.vy);
+  if (!p.supg || speed == 0.0) return 0.0;
+  const double ux = std::fabs(p.vx) / speed, uy = std::fabs(p.vy) / speed;
+  double h = INFINITY;
+  if (ux > 0) h = std::fmin(h, p.hx / ux);
+  if (uy > 0) h = std::fmin(h, p.hy / uy);
+  if (!(p.D > 0.0)) return h / (2.0 * speed);
+  const double pe = speed * h / (2.0 * p.D);
+  const double xi = pe > 30.0 ? 1.0 - 1.0 / pe : (std::cosh(pe) / std::sinh(pe) - 1.0 / pe);
+  return h / (2.0 * speed) * xi;
+}
+
+lbm_status fem_setup(lbm_fem* f, const uint8_t* elem_active, const int* dir_nodes,
+                     const double* d0) {
+  const lbm_fem_params& p = f->p;
+  const int nxn = f->nxn;
+  const long long n = f->n;
+  std::vector<double> A(9 * n, 0.0), B(9 * n, 0.0);
+  std::vector<char> touched(n, 0);
+  double Me[4][4], Ke[4][4];
+  element(p, supg_tau(p), Me, Ke);
+  const int loc[4][2] = {{0, 0}, {1, 0}, {1, 1}, {0, 1}};
+  const double ca = p.theta * p.dt, cb = -(1.0 - p.theta) * p.dt;
+  for (int j = 0; j < p.ney; ++j)
+    for (int i = 0; i < p.nex; ++i) {
+      if (elem_active && !elem_active[(long long)j * p.nex + i]) continue;
+      for (int a = 0; a < 4; ++a) {
+        const int ra = (j + loc[a][1]) * nxn + (i + loc[a][0]);
+        touched[ra] = 1;
+        for (int b = 0; b < 4; ++b) {
+          const int di = loc[b][0] - loc[a][0], dj = loc[b][1] - loc[a][1];
+          const int k = (dj + 1) * 3 + (di + 1);
+          A[k * n + ra] += Me[a][b] + ca * Ke[a][b];
+          B[k * n + ra] += Me[a][b] + cb * Ke[a][b];
+        }
+      }
+    }
+  std::vector<int> fid(n, -1);
+  for (long long q = 0; q < n; ++q)
+    if (!touched[q]) fid[q] = -2;
+  for (int k = 0; k < f->n_dir; ++k) {
+    const int q = dir_nodes[k];
+    if (q < 0 || q >= n) return ctx_fail(LBM_ERR_ARG, "lbm_fem_init: Dirichlet node %d out of range", q);
+    if (fid[q] >= 0) return ctx_fail(LBM_ERR_ARG, "lbm_fem_init: Dirichlet node %d repeated", q);
+    fid[q] = k;
+  }
+  for (long long q = 0; q < n; ++q)
+    if (fid[q] != -1) {  // identity row in A, zero row in B
+      for (int k = 0; k < 9; ++k) {
+        A[k * n + q] = k == 4 ? 1.0 : 0.0;
+        B[k * n + q] = 0.0;
+      }
+    }
+  FCK(cudaMemcpyAsync(f->A, A.data(), 9 * n * sizeof(double), cudaMemcpyHostToDevice, f->stream));
+  FCK(cudaMemcpyAsync(f->B, B.data(), 9 * n * sizeof(double), cudaMemcpyHostToDevice, f->stream));
+  FCK(cudaMemcpyAsync(f->fixed_id, fid.data(), n * sizeof(int), cudaMemcpyHostToDevice, f->stream));
+  std::vector<double> d(n, 0.0);
+  if (d0) {
+    const bool dev = ctx_on_device(d0);
+    if (dev) FCK(cudaMemcpy(d.data(), d0, n * sizeof(double), cudaMemcpyDeviceToHost));
+    else std::memcpy(d.data(), d0, n * sizeof(double));
+  }
+  for (long long q = 0; q < n; ++q)
+    if (fid[q] == -2) d[q] = 0.0;
+  FCK(cudaMemcpyAsync(f->d, d.data(), n * sizeof(double), cudaMemcpyHostToDevice, f->stream));
+  FCK(cudaStreamSynchronize(f->stream));
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_fem_init(lbm_fem** out, const lbm_fem_params* p, const uint8_t* elem_active,
+                        int n_dir, const int* dir_nodes, const double* d0, void* stream) {
+  if (!out || !p) return ctx_fail(LBM_ERR_ARG, "lbm_fem_init: null argument");
+  *out = nullptr;
+  if (p->nex < 1 || p->ney < 1 || !(p->hx > 0) || !(p->hy > 0) || !(p->dt > 0) ||
+      !(p->theta >= 0.0 && p->theta <= 1.0) || !(p->D >= 0.0) || n_dir < 0 ||
+      (n_dir > 0 && !dir_nodes))
+    return ctx_fail(LBM_ERR_ARG, "lbm_fem_init: bad parameters");
+  if ((long long)(p->nex + 1) * (p->ney + 1) > (1ll << 30))
+    return ctx_fail(LBM_ERR_ARG, "lbm_fem_init: mesh too large");
+  lbm_fem* f = new lbm_fem();
+  f->p = *p;
+  if (!(f->p.tol > 0)) f->p.tol = 1e-12;
+  if (f->p.max_iter <= 0) f->p.max_iter = 1000;
+  f->nxn = p->nex + 1;
+  f->nyn = p->ney + 1;
+  f->n = (long long)f->nxn * f->nyn;
+  f->nb = (int)((f->n + kThreads - 1) / kThreads);
+  f->n_dir = n_dir;
+  f->stream = (cudaStream_t)stream;
+  const long long n = f->n;
+  cudaError_t e = cudaSuccess;
+  auto al = [&](void** ptr, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(ptr, bytes);
+  };
+  al((void**)&f->A, 9 * n * sizeof(double));
+  al((void**)&f->B, 9 * n * sizeof(double));
+  al((void**)&f->d, n * sizeof(double));
+  al((void**)&f->b, n * sizeof(double));
+  al((void**)&f->vecs, 9 * n * sizeof(double));
+  al((void**)&f->fixed_id, n * sizeof(int));
+  al((void**)&f->fixed_val, (n_dir > 0 ? n_dir : 1) * sizeof(double));
+  al((void**)&f->part, 4 * (size_t)f->nb * sizeof(double));
+  al((void**)&f->sc, sizeof(Scal));
+  al((void**)&f->iters, sizeof(int));
+  if (e != cudaSuccess) {
+    fem_free(f);
+    return ctx_fail(LBM_ERR_NOMEM, "lbm_fem_init: %s", cudaGetErrorString(e));
+  }
+  double* v = f->vecs;
+  f->w = Vec{v, v + n, v + 2 * n, v + 3 * n, v + 4 * n, v + 5 * n, v + 6 * n, v + 7 * n, v + 8 * n};
+  const lbm_status st = fem_setup(f, elem_active, dir_nodes, d0);
+  if (st != LBM_OK) {
+    fem_free(f);
+    return st;
+  }
+  *out = f;
+  return LBM_OK;
+}
+
+lbm_status lbm_fem_step(lbm_fem* f, const double* dir_values) {
+  if (!f) return ctx_fail(LBM_ERR_ARG, "lbm_fem_step: null solver");
+  if (f->n_dir > 0 && !dir_values) return ctx_fail(LBM_ERR_ARG, "lbm_fem_step: null values");
+  cudaStream_t s = f->stream;
+  const long long n = f->n;
+  const int nb = f->nb, nxn = f->nxn, nyn = f->nyn;
+  double* P0 = f->part;
+  double* P1 = f->part + nb;
+  double* P2 = f->part + 2 * nb;
+  double* P3 = f->part + 3 * nb;
+  if (f->n_dir > 0)
+    FCK(cudaMemcpyAsync(f->fixed_val, dir_values, f->n_dir * sizeof(double), cudaMemcpyDefault, s));
+  FCK(cudaMemsetAsync(f->iters, 0, sizeof(int), s));
+  k_rhs<<<nb, kThreads, 0, s>>>(f->B, f->d, f->fixed_id, f->fixed_val, f->b, f->w.x, nxn, nyn, P0);
+  k_init_res<<<nb, kThreads, 0, s>>>(f->A, f->b, f->w, nxn, nyn, P1);
+  k_scal_init<<<1, 32, 0, s>>>(f->sc, P0, P1, nb, f->p.tol);
+  FCK(cudaGetLastError());
+  int done = 0, it = 0;
+  while (!done && it < f->p.max_iter) {
+    for (int k = 0; k < kCheckEvery; ++k, ++it) {
+      k_update_p<<<nb, kThreads, 0, s>>>(f->A, f->w, f->sc, n);
+      k_spmv_dot<0><<<nb, kThreads, 0, s>>>(f->A, f->w.phat, f->w.v, f->w.rhat, f->sc, nxn, nyn, P0, nullptr);
+      k_scal_alpha<<<1, 32, 0, s>>>(f->sc, P0, nb);
+      k_update_s<<<nb, kThreads, 0, s>>>(f->A, f->w, f->sc, n);
+      k_spmv_dot<1><<<nb, kThreads, 0, s>>>(f->A, f->w.shat, f->w.t, f->w.s, f->sc, nxn, nyn, P0, P1);
+      k_scal_omega<<<1, 32, 0, s>>>(f->sc, P0, P1, nb);
+      k_update_x<<<nb, kThreads, 0, s>>>(f->w, f->sc, n, P2, P3);
+      k_scal_rho<<<1, 32, 0, s>>>(f->sc, P2, P3, nb, f->p.tol, f->iters);
+    }
+    FCK(cudaGetLastError());
+    Scal h;
+    FCK(cudaMemcpyAsync(&h, f->sc, sizeof(Scal), cudaMemcpyDeviceToHost, s));
+    FCK(cudaStreamSynchronize(s));
+    done = h.done;
+    f->last_resid = h.bnorm2 > 0 ? std::sqrt(h.rnorm2 / h.bnorm2) : std::sqrt(h.rnorm2);
+    if (h.breakdown && !(h.rnorm2 <= f->p.tol * f->p.tol * h.bnorm2))
+      return ctx_fail(LBM_ERR_STATE, "lbm_fem_step: BiCGSTAB broke down (relative residual %.3e)",
+                      f->last_resid);
+  }
+  FCK(cudaMemcpyAsync(&f->last_iters, f->iters, sizeof(int), cudaMemcpyDeviceToHost, s));
+  FCK(cudaStreamSynchronize(s));
+  if (!done)
+    return ctx_fail(LBM_ERR_STATE, "lbm_fem_step: no convergence in %d iterations (residual %.3e)",
+                    f->p.max_iter, f->last_resid);
+  FCK(cudaMemcpyAsync(f->d, f->w.x, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  return LBM_OK;
+}
+
+lbm_status lbm_fem_interpolate(lbm_fem* f, int npts, const double* xy, double* out) {
+  if (!f || npts < 0 || (npts > 0 && (!xy || !out)))
+    return ctx_fail(LBM_ERR_ARG, "lbm_fem_interpolate: bad arguments");
+  if (npts == 0) return LBM_OK;
+  cudaStream_t s = f->stream;
+  const bool xy_dev = ctx_on_device(xy), out_dev = ctx_on_device(out);
+  const double* dxy = xy;
+  double* dout = out;
+  double* tmp = nullptr;
+  if (!xy_dev || !out_dev) {
+    if (f->scratch_n < 3 * (size_t)npts) {
+      FCK(cudaStreamSynchronize(s));
+      if (f->scratch) cudaFree(f->scratch);
+      f->scratch = nullptr;
+      f->scratch_n = 0;
+      FCK(cudaMalloc((void**)&f->scratch, 3 * (size_t)npts * sizeof(double)));
+      f->scratch_n = 3 * (size_t)npts;
+    }
+    tmp = f->scratch;
+    if (!xy_dev) {
+      FCK(cudaMemcpyAsync(tmp, xy, 2 * (size_t)npts * sizeof(double), cudaMemcpyHostToDevice, s));
+      dxy = tmp;
+    }
+    if (!out_dev) dout = tmp + 2 * (size_t)npts;
+  }
+  const lbm_fem_params& p = f->p;
+  k_interp<<<(npts + 127) / 128, 128, 0, s>>>(f->d, p.nex, p.ney, p.x0, p.y0, p.hx, p.hy, dxy,
+                                               npts, dout);
+  FCK(cudaGetLastError());
+  if (!out_dev) FCK(cudaMemcpyAsync(out, dout, (size_t)npts * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (tmp) FCK(cudaStreamSynchronize(s));
+  return LBM_OK;
+}
+
+lbm_status lbm_fem_get(lbm_fem* f, double* d) {
+  if (!f || !d) return ctx_fail(LBM_ERR_ARG, "lbm_fem_get: null argument");
+  FCK(cudaMemcpyAsync(d, f->d, f->n * sizeof(double), cudaMemcpyDefault, f->stream));
+  FCK(cudaStreamSynchronize(f->stream));
+  return LBM_OK;
+}
+
+lbm_status lbm_fem_set(lbm_fem* f, const double* d) {
+  if (!f || !d) return ctx_fail(LBM_ERR_ARG, "lbm_fem_set: null argument");
+  FCK(cudaMemcpyAsync(f->d, d, f->n * sizeof(double), cudaMemcpyDefault, f->stream));
+  if (!ctx_on_device(d)) FCK(cudaStreamSynchronize(f->stream));
+  return LBM_OK;
+}
+
+lbm_status lbm_fem_solver_info(lbm_fem* f, int* iters, double* rel_resid) {
+  if (!f) return ctx_fail(LBM_ERR_ARG, "lbm_fem_solver_info: null solver");
+  if (iters) *iters = f->last_iters;
+  if (rel_resid) *rel_resid = f->last_resid;
+  return LBM_OK;
+}
+
+void lbm_fem_destroy(lbm_fem* f) {
+  if (!f) return;
+  cudaStreamSynchronize(f->stream);
+  fem_free(f);
+}
+
+}  // extern "C"

@@ -200,3 +200,95 @@ def batch_cases(n_inst: int = 256, seed: int = 3, smin: int = 64, smax: int = 10
             mineral=np.ones((side, side)), u_dir=edge_array(side, side, W=1.0),
             q_neu=edge_array(side, side), porosity=porosity))
     return cases
+
+
+# ---- layouts of the two-subdomain hybrid runs --------------------------------
+# A layout holds the inputs of one hybrid run: the lattice's arguments, the
+# continuum mesh and its Dirichlet node list (fixed nodes first, then the
+# nodes of Gamma_f->c that take the lattice's trace), the lattice coordinates
+# of those trace points, the physical coordinates of the lattice's Gamma_c->f
+# edge nodes and their (contiguous) slot range in the lattice edge layout,
+# and the step counts.  Time unit: one lattice step; lattice spacing h.
+
+def hybrid_plain_layout(n_coarse: int = 100) -> dict:
+    """Plain hybrid (no solids, no reaction): continuum [0, 0.6] x [0, 0.25]
+    on 40 x 10 Q1 elements, lattice 256 x 64 on x in [0.5, 1.0] (h = 0.5/255,
+    periodic in y with period 64 h), overlap [0.5, 0.6]; uniform velocity
+    0.05 (lattice units) along x, tau 0.8 (D = 0.1 h^2), Gaussian pulse
+    c0 = exp(-(x - 0.3)^2 / 0.002), c = 0 at the continuum inlet, zero flux
+    at the lattice outlet and the continuum's y sides; 10 substeps per
+    coarse step, 3 Schwarz iterations."""
+    nfx, nfy = 256, 64
+    h = 0.5 / (nfx - 1)
+    tau = 0.8
+    D = (tau - 0.5) / 3.0 * h * h
+    nex, ney = 40, 10
+    hx, hy = 0.6 / nex, 0.25 / ney
+    nxn = nex + 1
+    xs = 0.5 + np.arange(nfx) * h
+    u0 = np.tile(np.exp(-(xs - 0.3) ** 2 / 0.002), (nfy, 1))
+    vel = np.zeros((2, nfy, nfx))
+    vel[0] = 0.05
+    node_x = (np.arange((nex + 1) * (ney + 1)) % nxn) * hx
+    inlet = [j * nxn for j in range(ney + 1)]
+    gamma = [j * nxn + nex for j in range(ney + 1)]
+    gamma_xy = np.array([[(0.6 - 0.5) / h, ((j * hy) / h) % nfy] for j in range(ney + 1)])
+    pts = np.array([[0.5, j * h] for j in range(nfy)])
+    return dict(
+        lbm=dict(nx=nfx, ny=nfy, tau=tau, edges=(1, 2, 0, 0), vel=vel, u0=u0),
+        fem=dict(nex=nex, ney=ney, x0=0.0, y0=0.0, hx=hx, hy=hy, D=D, v=(0.05 * h, 0.0),
+                 theta=0.5, dt=10.0, supg=True, elem_active=None,
+                 dirichlet=inlet + gamma, d0=np.exp(-(node_x - 0.3) ** 2 / 0.002)),
+        fixed_values=np.zeros(len(inlet)), gamma_lattice_xy=gamma_xy,
+        lbm_points=pts, lbm_slots=(0, nfy), q_neu=None,
+        eta=10, max_iter=3, n_coarse=n_coarse, h=h)
+
+
+def hybrid_block_layout(nex: int = 400, ney: int = 100, hole=(170, 230, 20, 80),
+                        n_f: int = 2048, seed: int = 5, porosity: float = 0.55,
+                        k: float = 5e-4, tau: float = 0.7, eta: int = 50,
+                        max_iter: int = 5, n_coarse: int = 200, rmin: float = 8.0,
+                        rmax: float = 24.0) -> dict:
+    """Continuum [0, 4] x [0, 1] on nex x ney Q1 elements with an element-
+    aligned hole (element ranges i0..i1, j0..j1); the pore block covers the
+    hole plus two continuum elements on every side and holds an n_f x n_f
+    lattice (wet nodes on the block's edges) of the disk / stream-function
+    generator with surface reaction k and dissolution.  The continuum has
+    v = 0 and the lattice's diffusivity D = (tau - 1/2)/3 h^2; c = 1 at the
+    continuum inlet x = 0 and c0 = 1 everywhere; the lattice's four sides
+    take the continuum's values (Gamma_c->f), the hole's edge takes the
+    lattice's trace (Gamma_f->c)."""
+    hc = 4.0 / nex
+    assert abs(1.0 / ney - hc) < 1e-12
+    i0, i1, j0, j1 = hole
+    bx0, bx1 = (i0 - 2) * hc, (i1 + 2) * hc
+    by0, by1 = (j0 - 2) * hc, (j1 + 2) * hc
+    h = (bx1 - bx0) / (n_f - 1)
+    D = (tau - 0.5) / 3.0 * h * h
+    act = np.ones((ney, nex), np.uint8)
+    act[j0:j1, i0:i1] = 0
+    nxn = nex + 1
+    inlet = [j * nxn for j in range(ney + 1)]
+    ring = [j * nxn + i for j in range(j0, j1 + 1) for i in range(i0, i1 + 1)
+            if i in (i0, i1) or j in (j0, j1)]
+    gamma_xy = np.array([[((r % nxn) * hc - bx0) / h, ((r // nxn) * hc - by0) / h]
+                         for r in ring])
+    side = bx0 + np.arange(n_f) * h
+    sidey = by0 + np.arange(n_f) * h
+    pts = np.concatenate([
+        np.stack([np.full(n_f, bx0), sidey], 1),    # W
+        np.stack([np.full(n_f, bx1), sidey], 1),    # E
+        np.stack([side, np.full(n_f, by0)], 1),     # S
+        np.stack([side, np.full(n_f, by1)], 1)])    # N
+    solid = disk_packing(n_f, n_f, porosity, seed, rmin=rmin, rmax=rmax)
+    vel = streamfunction_velocity(n_f, n_f, seed + 1_000_003, solid=solid)
+    u0 = np.where(solid != 0, 0.0, 1.0)
+    return dict(
+        lbm=dict(nx=n_f, ny=n_f, tau=tau, edges=(1, 1, 1, 1), solid=solid, vel=vel, u0=u0,
+                 react_mode=1, k=k, dissolution=True, mineral=np.ones((n_f, n_f))),
+        fem=dict(nex=nex, ney=ney, x0=0.0, y0=0.0, hx=hc, hy=hc, D=D, v=(0.0, 0.0),
+                 theta=0.5, dt=float(eta), supg=False, elem_active=act,
+                 dirichlet=inlet + ring, d0=np.ones((ney + 1) * nxn)),
+        fixed_values=np.ones(len(inlet)), gamma_lattice_xy=gamma_xy,
+        lbm_points=pts, lbm_slots=(0, 4 * n_f), q_neu=None,
+        eta=eta, max_iter=max_iter, n_coarse=n_coarse, h=h)

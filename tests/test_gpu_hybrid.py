@@ -1,0 +1,129 @@
+"""The library's Q1 continuum solver and the hybrid driver (Algorithm 1)
+against the oracle's: the continuum alone (Galerkin and SUPG, a hole,
+Dirichlet data that change every step, the element interpolant), the plain
+hybrid at full size (40 x 10 elements coupled to a 256 x 64 lattice, 100
+coarse steps of 3 Schwarz iterations and 10 substeps), the pore-block hybrid
+on a small mesh, and one coarse step of the pore-block hybrid at full size
+(400 x 100 elements around a 2048 x 2048 lattice)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1601_02708_gb300 import build
+    build.build()
+    import paper_1601_02708_gb300 as p
+    return p
+
+
+def _oracle_run(layout, n_coarse):
+    from oracle import LBMOracle
+    from oracle.fem import Q1FEM, schwarz_step
+    lbm = LBMOracle(**layout["lbm"])
+    fem = Q1FEM(**layout["fem"])
+    s0, s1 = layout["lbm_slots"]
+    for _ in range(n_coarse):
+        schwarz_step(fem, lbm, layout["eta"], layout["max_iter"], layout["fixed_values"],
+                     layout["gamma_lattice_xy"], layout["lbm_points"], np.arange(s0, s1),
+                     layout["q_neu"])
+    return fem, lbm
+
+
+@pytest.mark.parametrize("supg,hole", [(True, False), (False, True)])
+def test_fem_matches_oracle(pkg, oracle_mod, supg, hole):
+    from oracle.fem import Q1FEM
+    from paper_1601_02708_gb300.fem import FEM
+    nex, ney = 37, 11
+    rng = np.random.default_rng(7)
+    act = None
+    if hole:
+        act = np.ones((ney, nex), np.uint8)
+        act[3:8, 10:20] = 0
+    nxn = nex + 1
+    dirichlet = [j * nxn for j in range(ney + 1)] + [3 * nxn + 25, 9 * nxn + 30]
+    kw = dict(nex=nex, ney=ney, x0=-0.3, y0=0.2, hx=0.02, hy=0.03, D=1e-3,
+              v=(0.4, -0.15) if supg else (0.0, 0.0), theta=0.5, dt=0.01, supg=supg,
+              elem_active=act, dirichlet=dirichlet, d0=rng.uniform(0, 1, nxn * (ney + 1)))
+    g = FEM(**kw)
+    o = Q1FEM(**kw)
+    for step in range(15):
+        vals = rng.uniform(0, 2, len(dirichlet))
+        g.step(vals)
+        o.step(vals)
+    d = g.get()
+    assert np.abs(d - o.d).max() <= 1e-10 * np.abs(o.d).max()
+    it, res = g.solver_info()
+    assert 0 < it < 1000 and res <= 1e-12
+    pts = np.stack([rng.uniform(-0.3, 0.44, 40), rng.uniform(0.2, 0.53, 40)], 1)
+    assert np.abs(g.interpolate(pts) - o.interpolate(pts)).max() <= 1e-10
+
+
+def test_fem_rejects_bad_input(pkg):
+    from paper_1601_02708_gb300.fem import FEM
+    with pytest.raises(pkg.LBMError):
+        FEM(4, 4, 0, 0, 0.1, 0.1, D=1.0, dirichlet=[0, 0])   # repeated node
+    with pytest.raises(pkg.LBMError):
+        FEM(4, 4, 0, 0, 0.1, 0.1, D=1.0, dirichlet=[25])      # out of range
+    with pytest.raises(pkg.LBMError):
+        FEM(4, 4, 0, 0, -0.1, 0.1, D=1.0)                     # bad spacing
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_plain_hybrid_full_size(pkg, oracle_mod, prec):
+    from paper_1601_02708_gb300 import inputs
+    from paper_1601_02708_gb300.hybrid import Hybrid
+    layout = inputs.hybrid_plain_layout()
+    run = Hybrid(layout, precision=prec)
+    run.run()
+    fem, lbm = _oracle_run(layout, layout["n_coarse"])
+    tol = 1e-9 if prec == 64 else 1e-5
+    d = run.continuum()
+    assert np.abs(d - fem.d).max() <= tol * np.abs(fem.d).max()
+    u = run.lbm.concentration()
+    assert np.abs(u - lbm.u()).max() <= tol * np.abs(fem.d).max()
+    assert run.lbm.diagnostics()["steps"] == 100 * 3 * 10 - 100 * 2 * 10  # rollbacks
+    assert lbm.u().max() > 1e-6  # the pulse has entered the lattice
+
+
+@pytest.mark.parametrize("prec,k", [(64, 5e-3), (32, 5e-4)])
+def test_block_hybrid_small(pkg, oracle_mod, prec, k):
+    """FP64 with a rate that dissolves dozens of nodes (exact masks); FP32
+    with the configuration's rate, under which no node flips in these steps
+    (an FP32 flip can land one step from the FP64 one)."""
+    from paper_1601_02708_gb300 import inputs
+    from paper_1601_02708_gb300.hybrid import Hybrid
+    layout = inputs.hybrid_block_layout(nex=40, ney=10, hole=(17, 23, 2, 8), n_f=96,
+                                        k=k, eta=20, max_iter=3, n_coarse=4,
+                                        rmin=3, rmax=8)
+    run = Hybrid(layout, precision=prec)
+    run.run()
+    fem, lbm = _oracle_run(layout, 4)
+    tol = 1e-9 if prec == 64 else 1e-5
+    assert np.abs(run.continuum() - fem.d).max() <= tol
+    u = run.lbm.concentration()
+    assert np.abs(u - lbm.u()).max() <= tol
+    assert np.array_equal(run.lbm.solid(), lbm.solid())
+    fluid = lbm.solid() == 0
+    assert u[fluid].min() < 0.99  # the surface reaction has drawn the block down
+    if prec == 64:
+        assert lbm.diag()["flips"] > 0
+
+
+def test_block_hybrid_full_size_one_coarse_step(pkg, oracle_mod):
+    """400 x 100 elements around a 2048 x 2048 lattice: one coarse step
+    (5 Schwarz iterations of 50 substeps) against the oracle, FP32 lattice."""
+    from paper_1601_02708_gb300 import inputs
+    from paper_1601_02708_gb300.hybrid import Hybrid
+    layout = inputs.hybrid_block_layout(n_coarse=1)
+    run = Hybrid(layout, precision=32)
+    run.run()
+    fem, lbm = _oracle_run(layout, 1)
+    assert np.abs(run.continuum() - fem.d).max() <= 1e-5
+    u = run.lbm.concentration()
+    assert np.abs(u - lbm.u()).max() <= 1e-5
