@@ -187,8 +187,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--kernel-steps", type=int, default=1000)
     ap.add_argument("--adjoint-steps", type=int, default=5000)
+    ap.add_argument("--hybrid-coarse", type=int, default=200)
     ap.add_argument("--batch-steps", type=int, default=2000)
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-instances", type=int, default=256)
+    ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -268,12 +271,10 @@ def main():
     try:
         from paper_1601_02708_gb300 import build as _b
         import hashlib
-        import glob
-        h = hashlib.sha256()
-        for src in sorted(glob.glob(os.path.join(_b.CSRC, "*.cu")) +
-                          glob.glob(os.path.join(_b.CSRC, "*.cuh"))):
-            h.update(open(src, "rb").read())
         rec = json.load(open(tpath))
+        h = hashlib.sha256()
+        for name in rec["source_files"]:  # the files that define the step kernel
+            h.update(open(os.path.join(_b.CSRC, name), "rb").read())
         if rec.get("source_sha256") == h.hexdigest():
             traffic = rec["dram_bytes_per_launch_full_size"]
     except (OSError, ValueError, KeyError):
@@ -332,7 +333,7 @@ def main():
     batched = None
     if not args.no_batch and args.batch_steps > 0:
         from paper_1601_02708_gb300 import LBMBatch, inputs
-        cases = inputs.batch_cases()
+        cases = inputs.batch_cases(n_inst=args.batch_instances)
         bstream = torch.cuda.Stream()
         members = [LBM(c["nx"], c["ny"], c["tau"], precision=32, stream=bstream.cuda_stream,
                        **lattice_kwargs(c)) for c in cases]
@@ -340,7 +341,7 @@ def main():
         bud = [dev(c["u_dir"]) for c in cases]
         bq = [dev(c["q_neu"]) for c in cases]
         batch.substeps(1, 1, bud, bud, bq)  # loads the edge data into every member
-        tune = batch.autotune(trial_steps=20, repeats=2)
+        tune = {} if args.no_autotune else batch.autotune(trial_steps=20, repeats=2)
         batch.substeps(args.warmup, 1, bud, bud, bq)
         batch.time_steps(args.batch_steps)  # records the graph of the timed length
         barrier()
@@ -353,7 +354,7 @@ def main():
                    "ratio_to_single_lattice": bglups / value,
                    "tile_shape": LBMBatch.shapes()[batch.shape],
                    "autotune_ms": {str(LBMBatch.shapes()[k]): v for k, v in tune.items()},
-                   "workload": "256 instances, side log-uniform 64-1024, porosity "
+                   "workload": f"{len(cases)} instances, side log-uniform 64-1024, porosity "
                                "U[0.4,0.8], tau U[0.6,1.2], k 1e-3 with dissolution"}
         batch.close()
         for m in members:
@@ -402,6 +403,40 @@ def main():
                    "note": "adjoint_ms is one lbm_adjoint call: forward with checkpoints, "
                            "recompute and reverse sweep, gradients copied to the host"}
 
+    # ---- hybrid runs (Algorithm 1): Q1 continuum + lattice, Schwarz ---------
+    hybrid = None
+    if args.hybrid_coarse > 0:
+        from paper_1601_02708_gb300 import inputs
+        from paper_1601_02708_gb300.hybrid import Hybrid
+        hybrid = {}
+        for name, layout, ncoarse in (
+                ("plain", inputs.hybrid_plain_layout(), 100),
+                ("pore_block", inputs.hybrid_block_layout(), args.hybrid_coarse)):
+            run = Hybrid(layout, precision=32)
+            run.run(1)  # warm-up: allocations, first solves
+            barrier()
+            ev0.record(stream)
+            t0 = time.perf_counter()
+            run.run(ncoarse)
+            ev1.record(stream)
+            ev1.synchronize()
+            wall = time.perf_counter() - t0
+            hms = max_over_ranks(ev0.elapsed_time(ev1))
+            lat = layout["lbm"]
+            node_steps = lat["nx"] * lat["ny"] * layout["eta"] * layout["max_iter"] * ncoarse
+            its = run.solver_iters[-ncoarse * layout["max_iter"]:]
+            hybrid[name] = {
+                "coarse_steps": ncoarse, "ms_per_coarse_step": hms / ncoarse,
+                "lattice": [lat["nx"], lat["ny"]],
+                "fem_elements": [layout["fem"]["nex"], layout["fem"]["ney"]],
+                "substeps": layout["eta"], "schwarz_iterations": layout["max_iter"],
+                "lattice_glups": world * node_steps / (hms / 1e3) / 1e9,
+                "fem_solver_iterations_mean": float(np.mean(its)),
+                "wall_s": wall}
+            run.close()
+            del run
+            torch.cuda.empty_cache()
+
     # ---- CPU oracle on a bounded sample --------------------------------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.cpu_steps > 0:
@@ -432,7 +467,8 @@ def main():
                          "kernel_ms_per_launch": per_launch_ms,
                          "kernel_timing_steps": args.kernel_steps,
                          "dissolve_ms_per_launch": diss_ms / max(diss_n, 1)},
-            "fp64": fp64, "batched": batched, "adjoint": adjoint, "cpu_baseline": cpu,
+            "fp64": fp64, "batched": batched, "adjoint": adjoint, "hybrid": hybrid,
+            "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clocks.summary(),
