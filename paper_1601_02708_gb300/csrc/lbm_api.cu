@@ -205,6 +205,11 @@ __global__ void k_trace(const Real* __restrict__ u, int nx, int ny, int pitch, i
            U(bx, by) * gx * gy + U(ax, by) * (1 - gx) * gy;
 }
 
+__global__ void k_to_f32(const double* __restrict__ src, float* __restrict__ dst, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = (float)src[i];
+}
+
 int grid1d(long long n) {
   long long b = (n + 255) / 256;
   if (b < 1) b = 1;
@@ -382,7 +387,8 @@ void free_ctx(lbm_ctx* c) {
   void* ptrs[] = {c->f[0],   c->f[1],     c->link,      c->vel,        c->kf,
                   c->u,      c->ureact,   c->mineral,   c->edge,       c->infeasible,
                   c->jnode,  c->partial,  c->flip_list, c->flip_count, c->counters,
-                  c->status, c->diag,     c->scratch,   c->slist,      c->smin};
+                  c->status, c->diag,     c->scratch,   c->slist,      c->smin,
+                  c->edge32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   ctx_adjoint_free(c);
@@ -496,6 +502,10 @@ lbm_status init_impl(lbm_ctx* c, const uint8_t* solid, const double* vel,
   CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
   CK(cudaMalloc((void**)&c->edge, 3 * (size_t)c->nedge * sizeof(double)));
   CK(cudaMemsetAsync(c->edge, 0, 3 * (size_t)c->nedge * sizeof(double), c->stream));
+  if (c->esize == 4) {
+    CK(cudaMalloc((void**)&c->edge32, 3 * (size_t)c->nedge * sizeof(float)));
+    CK(cudaMemsetAsync(c->edge32, 0, 3 * (size_t)c->nedge * sizeof(float), c->stream));
+  }
   CK(cudaMalloc((void**)&c->infeasible, (size_t)c->nedge * sizeof(long long)));
   CK(cudaMemsetAsync(c->infeasible, 0, (size_t)c->nedge * sizeof(long long), c->stream));
   CK(cudaMalloc((void**)&c->jnode, (size_t)p.ny * sizeof(double)));
@@ -657,9 +667,18 @@ lbm_status ctx_stage_edges(lbm_ctx* c, const double* ua, const double* ub, const
   else CK(cudaMemsetAsync(e + c->nedge, 0, eb, c->stream));
   if (q) CK(cudaMemcpyAsync(e + 2 * c->nedge, q, eb, kind_from(q), c->stream));
   else CK(cudaMemsetAsync(e + 2 * c->nedge, 0, eb, c->stream));
+  TRY(ctx_edges_changed(c));
   // host-sourced edge data must not be reused before the copies complete
   if ((ua && !on_device(ua)) || (b && !on_device(b)) || (q && !on_device(q)))
     CK(cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+lbm_status ctx_edges_changed(lbm_ctx* c) {
+  if (!c->edge32) return LBM_OK;
+  const int n = 3 * c->nedge;
+  k_to_f32<<<(n + 255) / 256, 256, 0, c->stream>>>(c->edge, c->edge32, n);
+  CK(cudaGetLastError());
   return LBM_OK;
 }
 

@@ -216,8 +216,8 @@ __global__ void __launch_bounds__(lbm::kTmaThreads + 32, 1)
   } else {
     // ---- consumers ------------------------------------------------------
     const int cw = warp - 1;
-    const int r = cw >> 1;
-    const int cbase = (cw & 1) * 64 + lane;
+    const int r = cw / kWarpsPerRow;
+    const int cbase = (cw % kWarpsPerRow) * (32 * kNodesPerLane) + lane;
     int k = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
       const int s = k % kStages;
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(lbm::kTmaThreads + 32, 1)
       const int x0 = td.y, y = td.z + r;
       double tile_u = 0.0;
 #pragma unroll 1
-      for (int j = 0; j < 2; ++j) {
+      for (int j = 0; j < kNodesPerLane; ++j) {
         const int xl = cbase + 32 * j;
         const int x = x0 + xl;
         src.c = xl + 4;
@@ -586,6 +586,8 @@ lbm_status lbm_batch_substeps(lbm_batch* b, int n, int eta, const double* const*
       if (src[k]) BCK(cudaMemcpyAsync(c->edge + k * c->nedge, src[k], eb, cudaMemcpyDefault, b->stream));
       else BCK(cudaMemsetAsync(c->edge + k * c->nedge, 0, eb, b->stream));
     }
+    const lbm_status st = ctx_edges_changed(c);
+    if (st != LBM_OK) return st;
   }
   BCK(cudaStreamSynchronize(b->stream));  // host edge data may be reused after return
   return run_batch(b, n, eta);

@@ -28,6 +28,7 @@ struct lbm_ctx {
   void* ureact = nullptr;  // Real [rows][pitch] (dissolution)
   double* mineral = nullptr;
   double* edge = nullptr;  // [3][nedge]: u_dir_t0, u_dir_t1, q
+  float* edge32 = nullptr;  // FP32 copy of edge (FP32 lattices)
   long long* infeasible = nullptr;  // [nedge]
   double* jnode = nullptr;          // [ny]
   double* partial = nullptr;        // [max(blocks)]
@@ -67,6 +68,8 @@ lbm_status ctx_status(lbm_ctx* c);   // waits for the stream, reads the device e
 bool ctx_on_device(const void* p);
 // Copies the edge data of one call (NULL = zeros) into c->edge.
 lbm_status ctx_stage_edges(lbm_ctx* c, const double* ua, const double* ub, const double* q);
+// Refreshes the FP32 copy of the edge data after c->edge changed.
+lbm_status ctx_edges_changed(lbm_ctx* c);
 // One step launch with explicit arguments (fin = c->f[c->cur] for the tile
 // pipeline's tensor maps).
 template <typename Real>
@@ -91,6 +94,9 @@ inline lbm::StepArgs<Real> step_args(lbm_ctx* c, double frac) {
   a.ua = c->edge;
   a.ub = c->edge + c->nedge;
   a.q = c->edge + 2 * c->nedge;
+  a.ua32 = c->edge32;
+  a.ub32 = c->edge32 ? c->edge32 + c->nedge : nullptr;
+  a.q32 = c->edge32 ? c->edge32 + 2 * c->nedge : nullptr;
   a.infeasible = c->infeasible;
   a.jnode = c->jnode;
   a.partial = c->partial;

@@ -36,6 +36,9 @@ struct StepArgs {
   const double* __restrict__ ua;  // edge data, start of the coarse step
   const double* __restrict__ ub;  // edge data, end of the coarse step
   const double* __restrict__ q;   // Neumann data
+  const float* __restrict__ ua32;  // FP32 copies of the edge data (FP32 lattice)
+  const float* __restrict__ ub32;
+  const float* __restrict__ q32;
   long long* __restrict__ infeasible;  // per edge slot
   double* __restrict__ jnode;          // per east-edge row: sum_t u
   double* __restrict__ partial;        // per block: sum u (final substep)
@@ -206,19 +209,30 @@ __device__ __forceinline__ double step_node(const StepArgs<Real>& a, const Src& 
       int slot;
       if (dside >= 0) {
         slot = edge_slot(dside, x, y, a.nx, a.ny);
-        const double up = (1.0 - frac) * a.ua[slot] + frac * a.ub[slot];
-        bad = maxent_dirichlet(f, unknown, up);
+        if constexpr (sizeof(Real) == 4) {
+          const float fr = (float)frac;
+          bad = maxent_dirichlet_f32(f, unknown, (1.f - fr) * a.ua32[slot] + fr * a.ub32[slot]);
+        } else {
+          const double up = (1.0 - frac) * a.ua[slot] + frac * a.ub[slot];
+          bad = maxent_dirichlet(f, unknown, up);
+        }
       } else {
         slot = edge_slot(nside, x, y, a.nx, a.ny);
-        Real fbb[9];
+        int how = -1;
+        if constexpr (sizeof(Real) == 4) {
+          if (sx == 0 || sy == 0) how = maxent_neumann_side_f32(f, unknown, sx, sy, a.q32[slot]);
+        }
+        if (how < 0) {  // FP64 lattice, or the corner of two Neumann sides
+          Real fbb[9];
 #pragma unroll
-        for (int i = 0; i < 9; ++i)
-          fbb[i] = (unknown & (1u << opp_of(i))) ? src.own(i) : (Real)0;
-        const int how = maxent_neumann(f, unknown, sx, sy, a.q[slot], fbb);
+          for (int i = 0; i < 9; ++i)
+            fbb[i] = (unknown & (1u << opp_of(i))) ? src.own(i) : (Real)0;
+          how = maxent_neumann(f, unknown, sx, sy, a.q[slot], fbb);
+        }
         bad = how == kNeuInfeasible;
         if (a.bc_root) a.bc_root[slot] = how == kNeuRoot;
       }
-      if (bad) a.infeasible[slot] += 1;
+      if (bad) atomicAdd(reinterpret_cast<unsigned long long*>(a.infeasible + slot), 1ull);
     }
   }
   Real u = f[0];
@@ -243,7 +257,8 @@ __device__ __forceinline__ double step_node(const StepArgs<Real>& a, const Src& 
     store_node(a.ureact, n, share(kr * u, wsolid), ghosts, x, y, a.nx, a.ny, a.pitch,
                a.per_x, a.per_y);
   }
-  if (kEdge && x == a.nx - 1) a.jnode[y] += (double)u;
+  // one node per row adds to its row's sum: a reduction without a read-back
+  if (kEdge && x == a.nx - 1) atomicAdd(a.jnode + y, (double)u);
   if (kFinal) a.u_out[n] = u;
   return (double)u;
 }

@@ -166,6 +166,52 @@ __device__ int maxent_neumann(Real (&f)[9], unsigned unknown, int sx, int sy,
   return kNeuRoot;
 }
 
+// 1 / W_U for an unknown set of na axis and nd diagonal directions:
+// W_U = na / 9 + nd / 36 = (4 na + nd) / 36, so 1 / W_U = 36 / (4 na + nd).
+static __constant__ float kInvWeight36[21] = {
+    0.f,        36.f,        18.f,        12.f,        9.f,         36.f / 5.f,  6.f,
+    36.f / 7.f, 36.f / 8.f,  4.f,         36.f / 10.f, 36.f / 11.f, 3.f,         36.f / 13.f,
+    36.f / 14.f, 36.f / 15.f, 36.f / 16.f, 36.f / 17.f, 2.f,         36.f / 19.f, 36.f / 20.f};
+__device__ __forceinline__ float inv_weight_sum(unsigned unknown) {
+  return kInvWeight36[4 * __popc(unknown & 0x1Eu) + __popc(unknown & 0x1E0u)];
+}
+
+// FP32 forms of the two side solutions, for the FP32 lattice: the same closed
+// forms (f proportional to w over the unknowns, Sec. 4.1.1 (a) and, on a
+// straight side, (b)) evaluated in the lattice's own precision.
+__device__ __forceinline__ bool maxent_dirichlet_f32(float (&f)[9], unsigned unknown, float up) {
+  float known = 0.f;
+#pragma unroll
+  for (int i = 0; i < 9; ++i)
+    if (!(unknown & (1u << i))) known += f[i];
+  const float rest = up - known;
+  const float scale = rest * inv_weight_sum(unknown);
+#pragma unroll
+  for (int i = 0; i < 9; ++i)
+    if (unknown & (1u << i)) f[i] = (float)w_of(i) * scale;
+  return rest < 0.f;
+}
+// Straight side with outward normal (sx, sy), one of them zero: every unknown
+// has e.n = -1 and S = sum_{e.n = 1} f - q.
+__device__ __forceinline__ int maxent_neumann_side_f32(float (&f)[9], unsigned unknown, int sx,
+                                                       int sy, float q) {
+  float S = -q;
+#pragma unroll
+  for (int i = 1; i < 9; ++i)
+    if (!(unknown & (1u << i)) && cx_of(i) * sx + cy_of(i) * sy == 1) S += f[i];
+  if (!(S > 0.f)) {
+#pragma unroll
+    for (int i = 1; i < 9; ++i)
+      if (unknown & (1u << i)) f[i] = 0.f;
+    return S < 0.f ? kNeuInfeasible : kNeuZero;
+  }
+  const float scale = S * inv_weight_sum(unknown);
+#pragma unroll
+  for (int i = 1; i < 9; ++i)
+    if (unknown & (1u << i)) f[i] = (float)w_of(i) * scale;
+  return kNeuRoot;
+}
+
 // Boundary kind of an edge node (x, y) whose unknown set is not empty:
 // Dirichlet wins at corners (*dside >= 0, the first Dirichlet side), else
 // Neumann (*nside, the first Neumann side, with the outward normal (sx, sy)

@@ -22,8 +22,10 @@ constexpr int kTH = 8;             // tile height (rows)
 constexpr int kBoxW = kTW + 8;     // halo box width: 4 columns each side (16 B aligned)
 constexpr int kBoxH = kTH + 2;     // halo box height: one row each side
 constexpr int kStages = 3;
-constexpr int kTmaThreads = 512;   // consumer threads: 16 warps, two per tile row,
-                                   // two nodes per lane (plus one producer warp)
+constexpr int kTmaThreads = 512;   // consumer threads: 16 warps (plus one producer warp)
+constexpr int kWarpsPerRow = 16 / kTH;                    // consumer warps sharing a tile row
+constexpr int kNodesPerLane = kTW / (32 * kWarpsPerRow);  // nodes of a row per lane
+static_assert(16 % kTH == 0 && kNodesPerLane * 32 * kWarpsPerRow == kTW, "tile mapping");
 constexpr long long kSpinLimit = 1ll << 24;
 
 constexpr int round128(int b) { return (b + 127) / 128 * 128; }
@@ -178,8 +180,8 @@ __global__ void __launch_bounds__(kTmaThreads + 32, 1)
   } else {
     // ---- consumers ------------------------------------------------------
     const int cw = warp - 1;                  // 0..15
-    const int r = cw >> 1;                    // tile row of this warp
-    const int cbase = (cw & 1) * 64 + lane;   // first column (of two) of this lane
+    const int r = cw / kWarpsPerRow;          // tile row of this warp
+    const int cbase = (cw % kWarpsPerRow) * (32 * kNodesPerLane) + lane;  // first column
     int k = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
       const int s = k % kStages;
@@ -193,7 +195,7 @@ __global__ void __launch_bounds__(kTmaThreads + 32, 1)
                   (const uint32_t*)(st + kOffWord), r, 0};
       const int x0 = (t % ntx) * kTW, y = (t / ntx) * kTH + r;
 #pragma unroll 1
-      for (int j = 0; j < 2; ++j) {
+      for (int j = 0; j < kNodesPerLane; ++j) {
         const int xl = cbase + 32 * j;
         const int x = x0 + xl;
         src.c = xl + 4;
