@@ -65,7 +65,9 @@ struct AdjArgs {
   const Real* __restrict__ kf;      // [rows][pitch] or null
   const Real* __restrict__ u_n;     // u^n, the input of step n's collision
   const unsigned char* __restrict__ root;  // Neumann root taken at step n, per edge slot
-  double* __restrict__ gk;          // [rows][pitch] dJ/dk
+  double* __restrict__ gk;          // [rows][pitch] dJ/dk (FP64 lattice)
+  float* __restrict__ gk32;         // [rows][pitch] dJ/dk of the current segment (FP32
+                                    // lattice), folded into gk after every segment
   double* __restrict__ g_ua;        // [nedge] dJ/d(start data)
   double* __restrict__ g_ub;        // [nedge] dJ/d(end data)
   double* __restrict__ g_q;         // [nedge] dJ/dq
@@ -101,7 +103,10 @@ __device__ __forceinline__ void adjoint_node(const AdjArgs<Real>& a, int x, int 
   Real wl = (Real)w_of(0) * lam[0];
 #pragma unroll
   for (int i = 1; i < 9; ++i) wl += (Real)w_of(i) * lam[i];
-  if (reactive && a.gk) a.gk[n] -= (double)a.u_n[n] * (double)wl;
+  if (reactive) {
+    if constexpr (sizeof(Real) == 4) a.gk32[n] -= a.u_n[n] * wl;
+    else a.gk[n] -= (double)a.u_n[n] * (double)wl;
+  }
   if (kInit) return;
   const Real kr = reactive ? (a.kf ? a.kf[n] : a.k_scalar) : (Real)0;
   const Real vx = a.vel[n], vy = a.vel[a.plane + n];
@@ -130,30 +135,37 @@ __device__ __forceinline__ void adjoint_node(const AdjArgs<Real>& a, int x, int 
     if (unknown) {
       int dside, nside, sx, sy;
       edge_kind(a.edge, x, y, a.nx, a.ny, &dside, &nside, &sx, &sy);
-      double wu = 0.0, t = 0.0;
+      // t = sum_U w_i nu_i / W_U, in the lattice's precision (the
+      // FP32 lattice's boundary solves are FP32 too)
+      Real t = (Real)0;
 #pragma unroll
       for (int i = 0; i < 9; ++i)
-        if (unknown & (1u << i)) {
-          wu += w_of(i);
-          t += w_of(i) * (double)nu[i];
-        }
-      t /= wu;
+        if (unknown & (1u << i)) t += (Real)w_of(i) * nu[i];
+      if constexpr (sizeof(Real) == 4) {
+        t *= inv_weight_sum(unknown);
+      } else {
+        double wu = 0.0;
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+          if (unknown & (1u << i)) wu += w_of(i);
+        t /= wu;
+      }
       if (dside >= 0) {
         const int slot = edge_slot(dside, x, y, a.nx, a.ny);
 #pragma unroll
         for (int i = 0; i < 9; ++i)
-          if (!(unknown & (1u << i))) nu[i] = (Real)((double)nu[i] - t);
-        a.g_ua[slot] += (1.0 - a.frac) * t;
-        a.g_ub[slot] += a.frac * t;
+          if (!(unknown & (1u << i))) nu[i] -= t;
+        atomicAdd(a.g_ua + slot, (1.0 - a.frac) * (double)t);
+        atomicAdd(a.g_ub + slot, a.frac * (double)t);
       } else {
         const int slot = edge_slot(nside, x, y, a.nx, a.ny);
         if (a.root[slot]) {
 #pragma unroll
           for (int i = 0; i < 9; ++i) {
             const int d = cx_of(i) * sx + cy_of(i) * sy;
-            if (!(unknown & (1u << i)) && d != 0) nu[i] = (Real)((double)nu[i] + d * t);
+            if (!(unknown & (1u << i)) && d != 0) nu[i] += (Real)d * t;
           }
-          a.g_q[slot] -= t;
+          atomicAdd(a.g_q + slot, -(double)t);
         }
       }
 #pragma unroll
@@ -181,6 +193,18 @@ __global__ void __launch_bounds__(lbm::kBX * lbm::kBY) lbm_adjoint_step(const Ad
     adjoint_node<Real, kInit, true>(a, x, y, n);
 }
 
+// gk += gk32 (FP64), gk32 = 0: the end of a segment of the FP32 lattice.
+__global__ void k_fold_gk(double* __restrict__ gk, float* __restrict__ gk32, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float g = gk32[i];
+    if (g != 0.f) {
+      gk[i] += (double)g;
+      gk32[i] = 0.f;
+    }
+  }
+}
+
 }  // namespace
 
 // Buffers of the reverse sweep, kept in the context between calls.
@@ -194,6 +218,7 @@ struct AdjWork {
   char* u0 = nullptr;        // u at the start of the call
   unsigned char* roots = nullptr;  // Neumann branches of one segment, cap_l x nedge
   double* gk = nullptr;      // [rows][pitch]
+  float* gk32 = nullptr;     // [rows][pitch], FP32 lattice: one segment's share
   double* ge = nullptr;      // [3][nedge]: start, end, Neumann gradients
   double* jn0 = nullptr;     // east-edge sums before the call, [ny]
   double* part = nullptr;    // recompute scratch: mass partials
@@ -205,7 +230,7 @@ void ctx_adjoint_free(lbm_ctx* c) {
   AdjWork* w = c->adj;
   if (!w) return;
   void* ptrs[] = {w->ck, w->fin, w->mu[0], w->mu[1], w->uh, w->u0, w->roots,
-                  w->gk, w->ge,  w->jn0,   w->part,  w->jn, w->inf};
+                  w->gk, w->ge,  w->jn0,   w->part,  w->jn, w->inf, w->gk32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete w;
@@ -233,6 +258,7 @@ lbm_status ensure_work(lbm_ctx* c, int K, int L) {
   ACK(cudaMalloc((void**)&w->u0, w->plane_b));
   ACK(cudaMalloc((void**)&w->roots, (size_t)L * ne + 1));
   ACK(cudaMalloc((void**)&w->gk, (size_t)c->plane * sizeof(double)));
+  ACK(cudaMalloc((void**)&w->gk32, (size_t)c->plane * sizeof(float)));
   ACK(cudaMalloc((void**)&w->ge, 3 * ne * sizeof(double)));
   ACK(cudaMalloc((void**)&w->jn0, (size_t)c->p.ny * sizeof(double)));
   const size_t parts = (size_t)c->grid.x * c->grid.y;
@@ -254,6 +280,7 @@ AdjArgs<Real> adj_args(lbm_ctx* c, AdjWork* w, int mc, const Real* u_n,
   a.u_n = u_n;
   a.root = root;
   a.gk = w->gk;
+  a.gk32 = w->gk32;
   a.g_ua = w->ge;
   a.g_ub = w->ge + c->nedge;
   a.g_q = w->ge + 2 * c->nedge;
@@ -301,9 +328,12 @@ lbm_status adjoint_impl(lbm_ctx* c, int n, int eta, int L) {
   ACK(cudaMemsetAsync(w->mu[0], 0, fb, st));
   ACK(cudaMemsetAsync(w->mu[1], 0, fb, st));
   ACK(cudaMemsetAsync(w->gk, 0, (size_t)c->plane * sizeof(double), st));
+  ACK(cudaMemsetAsync(w->gk32, 0, (size_t)c->plane * sizeof(float), st));
   ACK(cudaMemsetAsync(w->ge, 0, 3 * ne * sizeof(double), st));
   ACK(cudaMemsetAsync(w->roots, 0, (size_t)L * ne, st));
   int mc = 0;
+  const long long fb_blocks = (c->plane + 255) / 256;
+  const int fold_grid = (int)(fb_blocks < 4LL * c->num_sms ? fb_blocks : 4LL * c->num_sms);
   for (int s = K - 1; s >= 0; --s) {
     const int n0 = s * L, n1 = n0 + L < n ? n0 + L : n;
     ACK(cudaMemcpyAsync(c->f[0], w->ck + (size_t)s * fb, fb, cudaMemcpyDeviceToDevice, st));
@@ -325,10 +355,18 @@ lbm_status adjoint_impl(lbm_ctx* c, int n, int eta, int L) {
       ACK(cudaGetLastError());
       mc ^= 1;
     }
+    if (sizeof(Real) == 4) {
+      k_fold_gk<<<fold_grid, 256, 0, st>>>(w->gk, w->gk32, c->plane);
+      ACK(cudaGetLastError());
+    }
   }
   const auto a0 = adj_args<Real>(c, w, mc, (const Real*)w->u0, w->roots, 0.0);
   lbm_adjoint_step<Real, true><<<grid, block, 0, st>>>(a0);
   ACK(cudaGetLastError());
+  if (sizeof(Real) == 4) {
+    k_fold_gk<<<fold_grid, 256, 0, st>>>(w->gk, w->gk32, c->plane);
+    ACK(cudaGetLastError());
+  }
 
   // the context ends where the forward run left it
   ACK(cudaMemcpyAsync(c->f[cur_final], w->fin, fb, cudaMemcpyDeviceToDevice, st));

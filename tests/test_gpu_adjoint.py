@@ -90,7 +90,9 @@ def test_adjoint_neumann_zero_limit(pkg, oracle_mod):
 @pytest.mark.parametrize("prec", [64, 32])
 def test_stride_independence_and_final_state(pkg, prec):
     """Every checkpoint stride recomputes the same steps, so the gradients
-    are bitwise equal; the context ends as after lbm_substeps."""
+    are bitwise equal -- except dJ/dk of the FP32 lattice, which sums each
+    segment in FP32 before adding it to the FP64 total, so its rounding
+    follows the segment boundaries; the context ends as after lbm_substeps."""
     case, ua, ub, q = _case(4, 100, 30)
     n, eta = 77, 3
     results = []
@@ -99,8 +101,13 @@ def test_stride_independence_and_final_state(pkg, prec):
         results.append(m.adjoint(n, eta, ua, ub, q, stride=stride))
     for r in results[1:]:
         assert r["J"] == results[0]["J"]
-        for key in ("k", "ua", "ub", "q"):
+        for key in ("ua", "ub", "q"):
             assert np.array_equal(r[key], results[0][key])
+        if prec == 64:
+            assert np.array_equal(r["k"], results[0]["k"])
+        else:
+            scale = np.abs(results[0]["k"]).max()
+            assert np.abs(r["k"] - results[0]["k"]).max() <= 1e-6 * scale
     a = pkg.LBM(precision=prec, **case)
     b = pkg.LBM(precision=prec, **case)
     ra = a.adjoint(n, eta, ua, ub, q)
