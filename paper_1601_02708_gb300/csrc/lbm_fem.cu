@@ -18,9 +18,9 @@
 // arrays of A = M + theta dt K and B = M - (1 - theta) dt K.  The rows of
 // Dirichlet and inactive nodes are the identity in A and zero in B.  Each step
 // solves A x = B d^n (+ prescribed values) by Jacobi-preconditioned
-// BiCGSTAB in FP64: five vector kernels and three one-block scalar kernels
-// per iteration, dot products folded in a fixed order (deterministic), the
-// scalars kept on the device, the residual read back every few iterations.
+// BiCGSTAB in FP64 inside one cooperative launch (grid-wide barriers between
+// the phases of an iteration, dot products folded in a fixed order, so the
+// result is deterministic); the host reads the outcome once per step.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -48,7 +48,6 @@ namespace {
   } while (0)
 
 constexpr int kThreads = 256;
-constexpr int kCheckEvery = 8;  // iterations between residual read-backs
 
 // Device scalars of the solver.
 struct Scal {
@@ -64,7 +63,7 @@ struct Vec {
 
 // Row (i, j) of A x for the 9-diagonal matrix: A[k][row] multiplies the
 // neighbour at offset di = k % 3 - 1, dj = k / 3 - 1.
-__device__ __forceinline__ double spmv_row(const double* __restrict__ A, const double* __restrict__ x,
+__device__ __forceinline__ double spmv_row(const double* __restrict__ A, const double* x,
                                            int i, int j, int nxn, int nyn, long long n) {
   const long long row = (long long)j * nxn + i;
   double acc = 0.0;
@@ -73,200 +72,237 @@ __device__ __forceinline__ double spmv_row(const double* __restrict__ A, const d
     const int di = k % 3 - 1, dj = k / 3 - 1;
     const int ii = i + di, jj = j + dj;
     if (ii < 0 || ii >= nxn || jj < 0 || jj >= nyn) continue;
-    acc += A[k * n + row] * x[(long long)jj * nxn + ii];
+    // x may have been written by other blocks of this launch (behind a grid
+    // barrier): read it through L2, not the non-coherent L1
+    acc += A[k * n + row] * __ldcg(x + (long long)jj * nxn + ii);
   }
   return acc;
 }
 
-__device__ __forceinline__ void block_dot(double v0, double v1, double* part0, double* part1) {
+// ---- the linear solve as one cooperative launch -----------------------------
+// Every block runs the same BiCGSTAB iteration over a grid-stride share of the
+// nodes; the five points per iteration where a vector must be complete (a
+// sparse product reads neighbours) or a dot product summed are grid-wide
+// barriers.  Partial dots are written per block and folded by every block in
+// the same fixed order, so all blocks take the same decisions.  Each barrier
+// wait is bounded: on expiry the status word is set and the blocks return.
+
+constexpr long long kBarrierSpin = 1ll << 24;
+
+struct Solve {
+  const double* A;       // [9][n]
+  const double* B;       // [9][n]
+  double* d;             // state: d^n in, d^{n+1} out
+  const int* fixed_id;   // -1 free, -2 inactive, >= 0 index into fixed_val
+  const double* fixed_val;
+  double* b;
+  Vec w;
+  double* part;          // [4][gridDim.x] partial dots
+  unsigned* bar;         // [2] barrier count and generation
+  int* status;           // 0, or 1 after an expired barrier wait
+  Scal* sc;              // results: iterations, norms, breakdown
+  int* iters;
+  int nxn, nyn;
+  long long n;
+  double tol;
+  int max_iter;
+};
+
+// Grid-wide barrier (all blocks are resident: cooperative launch).  Returns
+// false if the wait expired.
+__device__ __forceinline__ bool grid_sync(unsigned* bar, int* status) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = bar + 1;
+    const unsigned g = *gen;
+    __threadfence();
+    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+      bar[0] = 0u;
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+      ok = 1;
+    } else {
+      long long i = 0;
+      while (*gen == g && ++i < kBarrierSpin) {
+      }
+      ok = *gen != g;
+      if (!ok) atomicExch(status, 1);
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// Block partials of two dot products into part0/part1 [blockIdx.x].
+__device__ __forceinline__ void block_dot2(double v0, double v1, double* part0, double* part1) {
   __shared__ double s0[kThreads / 32], s1[kThreads / 32];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     v0 += __shfl_down_sync(0xffffffffu, v0, o);
     v1 += __shfl_down_sync(0xffffffffu, v1, o);
   }
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   if (lane == 0) {
-    s0[w] = v0;
-    s1[w] = v1;
+    s0[wp] = v0;
+    s1[wp] = v1;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double a = 0.0, b = 0.0;
+    double a = 0.0, c = 0.0;
     for (int k = 0; k < kThreads / 32; ++k) {
       a += s0[k];
-      b += s1[k];
+      c += s1[k];
     }
-    if (part0) part0[blockIdx.x] = a;
-    if (part1) part1[blockIdx.x] = b;
+    part0[blockIdx.x] = a;
+    if (part1) part1[blockIdx.x] = c;
   }
 }
 
-__device__ __forceinline__ double fold(const double* part, int nb) {
-  double s = 0.0;
-  for (int k = 0; k < nb; ++k) s += part[k];
-  return s;
+// Sum of the gridDim.x partials, the same in every block: warp 0 adds a
+// strided share per lane, then a fixed shuffle tree; broadcast to the block.
+__device__ __forceinline__ double grid_fold(const double* part) {
+  __shared__ double r;
+  if (threadIdx.x < 32) {
+    double v = 0.0;
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += 32) v += ((const volatile double*)part)[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) r = v;
+  }
+  __syncthreads();
+  const double out = r;
+  __syncthreads();
+  return out;
 }
 
-// rhs b = B d (rows of fixed nodes: their values), x0 = d with the fixed
-// values, r = b - A x0 computed by the next kernel.
-__global__ void __launch_bounds__(kThreads)
-    k_rhs(const double* __restrict__ B, const double* __restrict__ d, const int* __restrict__ fixed_id,
-          const double* __restrict__ fixed_val, double* __restrict__ b, double* __restrict__ x,
-          int nxn, int nyn, double* part_bb) {
-  const long long n = (long long)nxn * nyn;
-  const long long p = blockIdx.x * (long long)kThreads + threadIdx.x;
+__global__ void __launch_bounds__(kThreads) k_bicgstab(const Solve S) {
+  const long long n = S.n;
+  const int nxn = S.nxn, nyn = S.nyn;
+  const long long stride = (long long)gridDim.x * kThreads;
+  const long long p0 = blockIdx.x * (long long)kThreads + threadIdx.x;
+  double* P0 = S.part;
+  double* P1 = S.part + gridDim.x;
+  double* P2 = S.part + 2 * gridDim.x;
+  double* P3 = S.part + 3 * gridDim.x;
+  const Vec w = S.w;
+  const double* A = S.A;
+
+  // right-hand side (prescribed rows: their values), initial guess
   double bb = 0.0;
-  if (p < n) {
+  for (long long p = p0; p < n; p += stride) {
     const int i = (int)(p % nxn), j = (int)(p / nxn);
-    const int f = fixed_id[p];
+    const int f = S.fixed_id[p];
     double bv, xv;
     if (f >= 0) {
-      bv = fixed_val[f];
+      bv = S.fixed_val[f];
       xv = bv;
     } else if (f == -2) {  // inactive
       bv = 0.0;
       xv = 0.0;
     } else {
-      bv = spmv_row(B, d, i, j, nxn, nyn, n);
-      xv = d[p];
+      bv = spmv_row(S.B, S.d, i, j, nxn, nyn, n);
+      xv = S.d[p];
     }
-    b[p] = bv;
-    x[p] = xv;
+    S.b[p] = bv;
+    w.x[p] = xv;
     // the residual is measured against the free rows' right-hand side (the
     // prescribed rows are met exactly from the start and stay so)
-    bb = f == -1 ? bv * bv : 0.0;
+    if (f == -1) bb += bv * bv;
   }
-  block_dot(bb, 0.0, part_bb, nullptr);
-}
+  block_dot2(bb, 0.0, P0, nullptr);
+  if (!grid_sync(S.bar, S.status)) return;
 
-// r = b - A x, rhat = r, p = 0, v = 0, partials of (r, r).
-__global__ void __launch_bounds__(kThreads)
-    k_init_res(const double* __restrict__ A, const double* __restrict__ b, Vec w, int nxn, int nyn,
-               double* part_rr) {
-  const long long n = (long long)nxn * nyn;
-  const long long p = blockIdx.x * (long long)kThreads + threadIdx.x;
+  // r = b - A x, rhat = r, p = r
   double rr = 0.0;
-  if (p < n) {
+  for (long long p = p0; p < n; p += stride) {
     const int i = (int)(p % nxn), j = (int)(p / nxn);
-    const double r = b[p] - spmv_row(A, w.x, i, j, nxn, nyn, n);
+    const double r = S.b[p] - spmv_row(A, w.x, i, j, nxn, nyn, n);
     w.r[p] = r;
     w.rhat[p] = r;
-    w.p[p] = 0.0;
-    w.v[p] = 0.0;
-    rr = r * r;
+    w.p[p] = r;
+    rr += r * r;
   }
-  block_dot(rr, 0.0, part_rr, nullptr);
-}
-
-__global__ void k_scal_init(Scal* sc, const double* part_bb, const double* part_rr, int nb,
-                            double tol) {
-  if (threadIdx.x != 0) return;
-  sc->bnorm2 = fold(part_bb, nb);
-  sc->rnorm2 = fold(part_rr, nb);
-  sc->rho = sc->rnorm2;  // rhat = r0
-  sc->alpha = 1.0;
-  sc->omega = 1.0;
-  sc->beta = 0.0;
-  sc->breakdown = 0;
-  sc->done = (sc->rnorm2 <= tol * tol * sc->bnorm2) ? 1 : 0;
-}
-
-// p = r + beta (p - omega v); phat = p / diag(A)
-__global__ void __launch_bounds__(kThreads)
-    k_update_p(const double* __restrict__ A, Vec w, const Scal* sc, long long n) {
-  if (sc->done) return;
-  const long long p = blockIdx.x * (long long)kThreads + threadIdx.x;
-  if (p >= n) return;
-  const double pv = w.r[p] + sc->beta * (w.p[p] - sc->omega * w.v[p]);
-  w.p[p] = pv;
-  w.phat[p] = pv / A[4 * n + p];
-}
-
-// y = A xin and the partial dots (rhat, y) [mode 0] or (y, s), (y, y) [mode 1]
-template <int kMode>
-__global__ void __launch_bounds__(kThreads)
-    k_spmv_dot(const double* __restrict__ A, const double* __restrict__ xin, double* __restrict__ y,
-               const double* __restrict__ other, const Scal* sc, int nxn, int nyn,
-               double* part0, double* part1) {
-  if (sc->done) return;
-  const long long n = (long long)nxn * nyn;
-  const long long p = blockIdx.x * (long long)kThreads + threadIdx.x;
-  double d0 = 0.0, d1 = 0.0;
-  if (p < n) {
-    const int i = (int)(p % nxn), j = (int)(p / nxn);
-    const double yv = spmv_row(A, xin, i, j, nxn, nyn, n);
-    y[p] = yv;
-    d0 = yv * other[p];
-    d1 = yv * yv;
+  block_dot2(rr, 0.0, P1, nullptr);
+  if (!grid_sync(S.bar, S.status)) return;
+  const double bnorm2 = grid_fold(P0);
+  double rnorm2 = grid_fold(P1);
+  double rho = rnorm2, alpha = 0.0, omega = 0.0;
+  const double tol2 = S.tol * S.tol * bnorm2;
+  bool done = rnorm2 <= tol2, breakdown = false;
+  int it = 0;
+  while (!done && it < S.max_iter) {
+    for (long long p = p0; p < n; p += stride) w.phat[p] = w.p[p] / A[4 * n + p];
+    if (!grid_sync(S.bar, S.status)) return;
+    double d0 = 0.0;
+    for (long long p = p0; p < n; p += stride) {
+      const int i = (int)(p % nxn), j = (int)(p / nxn);
+      const double v = spmv_row(A, w.phat, i, j, nxn, nyn, n);
+      w.v[p] = v;
+      d0 += w.rhat[p] * v;
+    }
+    block_dot2(d0, 0.0, P0, nullptr);
+    if (!grid_sync(S.bar, S.status)) return;
+    const double rv = grid_fold(P0);
+    if (rv == 0.0 || !isfinite(rv)) {
+      breakdown = true;
+      break;
+    }
+    alpha = rho / rv;
+    for (long long p = p0; p < n; p += stride) {
+      const double sv = w.r[p] - alpha * w.v[p];
+      w.s[p] = sv;
+      w.shat[p] = sv / A[4 * n + p];
+    }
+    if (!grid_sync(S.bar, S.status)) return;
+    double ts = 0.0, tt = 0.0;
+    for (long long p = p0; p < n; p += stride) {
+      const int i = (int)(p % nxn), j = (int)(p / nxn);
+      const double t = spmv_row(A, w.shat, i, j, nxn, nyn, n);
+      w.t[p] = t;
+      ts += t * w.s[p];
+      tt += t * t;
+    }
+    block_dot2(ts, tt, P0, P1);
+    if (!grid_sync(S.bar, S.status)) return;
+    const double tsum = grid_fold(P1);
+    omega = tsum > 0.0 ? grid_fold(P0) / tsum : 0.0;
+    double rh = 0.0;
+    rr = 0.0;
+    for (long long p = p0; p < n; p += stride) {
+      w.x[p] += alpha * w.phat[p] + omega * w.shat[p];
+      const double r = w.s[p] - omega * w.t[p];
+      w.r[p] = r;
+      rh += w.rhat[p] * r;
+      rr += r * r;
+    }
+    block_dot2(rh, rr, P2, P3);
+    if (!grid_sync(S.bar, S.status)) return;
+    const double rho_new = grid_fold(P2);
+    rnorm2 = grid_fold(P3);
+    ++it;
+    if (rnorm2 <= tol2) {
+      done = true;
+      break;
+    }
+    if (rho_new == 0.0 || omega == 0.0 || !isfinite(rho_new)) {
+      breakdown = true;
+      break;
+    }
+    const double beta = (rho_new / rho) * (alpha / omega);
+    rho = rho_new;
+    for (long long p = p0; p < n; p += stride) w.p[p] = w.r[p] + beta * (w.p[p] - omega * w.v[p]);
   }
-  block_dot(d0, kMode ? d1 : 0.0, part0, kMode ? part1 : nullptr);
-}
-
-// alpha = rho / (rhat, v)
-__global__ void k_scal_alpha(Scal* sc, const double* part, int nb) {
-  if (threadIdx.x != 0 || sc->done) return;
-  const double rv = fold(part, nb);
-  if (rv == 0.0 || !isfinite(rv)) {
-    sc->breakdown = 1;
-    sc->done = 1;
-    return;
+  // every block copies its own share of x: no barrier needed
+  for (long long p = p0; p < n; p += stride) S.d[p] = w.x[p];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    S.sc->bnorm2 = bnorm2;
+    S.sc->rnorm2 = rnorm2;
+    S.sc->done = done ? 1 : 0;
+    S.sc->breakdown = breakdown ? 1 : 0;
+    *S.iters = it;
   }
-  sc->alpha = sc->rho / rv;
-}
-
-// s = r - alpha v; shat = s / diag(A)
-__global__ void __launch_bounds__(kThreads)
-    k_update_s(const double* __restrict__ A, Vec w, const Scal* sc, long long n) {
-  if (sc->done) return;
-  const long long p = blockIdx.x * (long long)kThreads + threadIdx.x;
-  if (p >= n) return;
-  const double s = w.r[p] - sc->alpha * w.v[p];
-  w.s[p] = s;
-  w.shat[p] = s / A[4 * n + p];
-}
-
-// omega = (t, s) / (t, t)
-__global__ void k_scal_omega(Scal* sc, const double* part_ts, const double* part_tt, int nb) {
-  if (threadIdx.x != 0 || sc->done) return;
-  const double ts = fold(part_ts, nb), tt = fold(part_tt, nb);
-  sc->omega = tt > 0.0 ? ts / tt : 0.0;
-}
-
-// x += alpha phat + omega shat; r = s - omega t; partials (rhat, r), (r, r)
-__global__ void __launch_bounds__(kThreads)
-    k_update_x(Vec w, const Scal* sc, long long n, double* part_rr_hat, double* part_rr) {
-  if (sc->done) return;
-  const long long p = blockIdx.x * (long long)kThreads + threadIdx.x;
-  double a = 0.0, b = 0.0;
-  if (p < n) {
-    w.x[p] += sc->alpha * w.phat[p] + sc->omega * w.shat[p];
-    const double r = w.s[p] - sc->omega * w.t[p];
-    w.r[p] = r;
-    a = w.rhat[p] * r;
-    b = r * r;
-  }
-  block_dot(a, b, part_rr_hat, part_rr);
-}
-
-// rho_new, beta, convergence
-__global__ void k_scal_rho(Scal* sc, const double* part_a, const double* part_b, int nb,
-                           double tol, int* iters) {
-  if (threadIdx.x != 0 || sc->done) return;
-  const double rho_new = fold(part_a, nb);
-  sc->rnorm2 = fold(part_b, nb);
-  *iters += 1;
-  if (sc->rnorm2 <= tol * tol * sc->bnorm2) {
-    sc->done = 1;
-    return;
-  }
-  if (rho_new == 0.0 || sc->omega == 0.0 || !isfinite(rho_new)) {
-    sc->breakdown = 1;
-    sc->done = 1;
-    return;
-  }
-  sc->beta = (rho_new / sc->rho) * (sc->alpha / sc->omega);
-  sc->rho = rho_new;
 }
 
 // FE interpolation (bilinear on the containing element) of d at points
@@ -307,6 +343,9 @@ struct lbm_fem {
   double* part = nullptr;   // 4 x nb partials
   Scal* sc = nullptr;
   int* iters = nullptr;
+  unsigned* bar = nullptr;  // grid barrier [2]
+  int* status = nullptr;
+  int grid = 0;             // blocks of the cooperative solve (all resident)
   double* scratch = nullptr;  // staging of host points / results of lbm_fem_interpolate
   size_t scratch_n = 0;
   int last_iters = 0;
@@ -317,7 +356,7 @@ namespace {
 
 void fem_free(lbm_fem* f) {
   void* ptrs[] = {f->A, f->B, f->d, f->b, f->vecs, f->fixed_id, f->fixed_val, f->part,
-                  f->sc, f->iters, f->scratch};
+                  f->sc, f->iters, f->scratch, f->bar, f->status};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete f;
@@ -456,9 +495,28 @@ lbm_status lbm_fem_init(lbm_fem** out, const lbm_fem_params* p, const uint8_t* e
   al((void**)&f->vecs, 9 * n * sizeof(double));
   al((void**)&f->fixed_id, n * sizeof(int));
   al((void**)&f->fixed_val, (n_dir > 0 ? n_dir : 1) * sizeof(double));
-  al((void**)&f->part, 4 * (size_t)f->nb * sizeof(double));
+  {
+    int dev = 0, sms = 0, coop = 0, per_sm = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bicgstab, kThreads, 0);
+    if (e == cudaSuccess && (!coop || per_sm < 1)) {
+      fem_free(f);
+      return ctx_fail(LBM_ERR_CUDA, "lbm_fem_init: the device has no cooperative launch");
+    }
+    const long long need = (n + kThreads - 1) / kThreads;
+    const long long cap = (long long)sms * (per_sm < 2 ? per_sm : 2);
+    f->grid = (int)(need < cap ? need : cap);
+  }
+  al((void**)&f->part, 4 * (size_t)(f->grid > 0 ? f->grid : 1) * sizeof(double));
   al((void**)&f->sc, sizeof(Scal));
   al((void**)&f->iters, sizeof(int));
+  al((void**)&f->bar, 2 * sizeof(unsigned));
+  al((void**)&f->status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(f->bar, 0, 2 * sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemset(f->status, 0, sizeof(int));
   if (e != cudaSuccess) {
     fem_free(f);
     return ctx_fail(LBM_ERR_NOMEM, "lbm_fem_init: %s", cudaGetErrorString(e));
@@ -478,47 +536,49 @@ lbm_status lbm_fem_step(lbm_fem* f, const double* dir_values) {
   if (!f) return ctx_fail(LBM_ERR_ARG, "lbm_fem_step: null solver");
   if (f->n_dir > 0 && !dir_values) return ctx_fail(LBM_ERR_ARG, "lbm_fem_step: null values");
   cudaStream_t s = f->stream;
-  const long long n = f->n;
-  const int nb = f->nb, nxn = f->nxn, nyn = f->nyn;
-  double* P0 = f->part;
-  double* P1 = f->part + nb;
-  double* P2 = f->part + 2 * nb;
-  double* P3 = f->part + 3 * nb;
   if (f->n_dir > 0)
     FCK(cudaMemcpyAsync(f->fixed_val, dir_values, f->n_dir * sizeof(double), cudaMemcpyDefault, s));
-  FCK(cudaMemsetAsync(f->iters, 0, sizeof(int), s));
-  k_rhs<<<nb, kThreads, 0, s>>>(f->B, f->d, f->fixed_id, f->fixed_val, f->b, f->w.x, nxn, nyn, P0);
-  k_init_res<<<nb, kThreads, 0, s>>>(f->A, f->b, f->w, nxn, nyn, P1);
-  k_scal_init<<<1, 32, 0, s>>>(f->sc, P0, P1, nb, f->p.tol);
-  FCK(cudaGetLastError());
-  int done = 0, it = 0;
-  while (!done && it < f->p.max_iter) {
-    for (int k = 0; k < kCheckEvery; ++k, ++it) {
-      k_update_p<<<nb, kThreads, 0, s>>>(f->A, f->w, f->sc, n);
-      k_spmv_dot<0><<<nb, kThreads, 0, s>>>(f->A, f->w.phat, f->w.v, f->w.rhat, f->sc, nxn, nyn, P0, nullptr);
-      k_scal_alpha<<<1, 32, 0, s>>>(f->sc, P0, nb);
-      k_update_s<<<nb, kThreads, 0, s>>>(f->A, f->w, f->sc, n);
-      k_spmv_dot<1><<<nb, kThreads, 0, s>>>(f->A, f->w.shat, f->w.t, f->w.s, f->sc, nxn, nyn, P0, P1);
-      k_scal_omega<<<1, 32, 0, s>>>(f->sc, P0, P1, nb);
-      k_update_x<<<nb, kThreads, 0, s>>>(f->w, f->sc, n, P2, P3);
-      k_scal_rho<<<1, 32, 0, s>>>(f->sc, P2, P3, nb, f->p.tol, f->iters);
-    }
-    FCK(cudaGetLastError());
-    Scal h;
-    FCK(cudaMemcpyAsync(&h, f->sc, sizeof(Scal), cudaMemcpyDeviceToHost, s));
-    FCK(cudaStreamSynchronize(s));
-    done = h.done;
-    f->last_resid = h.bnorm2 > 0 ? std::sqrt(h.rnorm2 / h.bnorm2) : std::sqrt(h.rnorm2);
-    if (h.breakdown && !(h.rnorm2 <= f->p.tol * f->p.tol * h.bnorm2))
-      return ctx_fail(LBM_ERR_STATE, "lbm_fem_step: BiCGSTAB broke down (relative residual %.3e)",
-                      f->last_resid);
-  }
-  FCK(cudaMemcpyAsync(&f->last_iters, f->iters, sizeof(int), cudaMemcpyDeviceToHost, s));
+  Solve S;
+  S.A = f->A;
+  S.B = f->B;
+  S.d = f->d;
+  S.fixed_id = f->fixed_id;
+  S.fixed_val = f->fixed_val;
+  S.b = f->b;
+  S.w = f->w;
+  S.part = f->part;
+  S.bar = f->bar;
+  S.status = f->status;
+  S.sc = f->sc;
+  S.iters = f->iters;
+  S.nxn = f->nxn;
+  S.nyn = f->nyn;
+  S.n = f->n;
+  S.tol = f->p.tol;
+  S.max_iter = f->p.max_iter;
+  void* args[] = {&S};
+  FCK(cudaLaunchCooperativeKernel((const void*)k_bicgstab, dim3(f->grid), dim3(kThreads), args, 0, s));
+  struct {
+    Scal sc;
+    int iters, status;
+  } h;
+  FCK(cudaMemcpyAsync(&h.sc, f->sc, sizeof(Scal), cudaMemcpyDeviceToHost, s));
+  FCK(cudaMemcpyAsync(&h.iters, f->iters, sizeof(int), cudaMemcpyDeviceToHost, s));
+  FCK(cudaMemcpyAsync(&h.status, f->status, sizeof(int), cudaMemcpyDeviceToHost, s));
   FCK(cudaStreamSynchronize(s));
-  if (!done)
+  f->last_iters = h.iters;
+  f->last_resid = h.sc.bnorm2 > 0 ? std::sqrt(h.sc.rnorm2 / h.sc.bnorm2) : std::sqrt(h.sc.rnorm2);
+  if (h.status) {
+    cudaMemsetAsync(f->status, 0, sizeof(int), s);
+    cudaMemsetAsync(f->bar, 0, 2 * sizeof(unsigned), s);
+    return ctx_fail(LBM_ERR_TIMEOUT, "lbm_fem_step: a grid barrier wait of the solve expired");
+  }
+  if (h.sc.breakdown && !h.sc.done)
+    return ctx_fail(LBM_ERR_STATE, "lbm_fem_step: BiCGSTAB broke down (relative residual %.3e)",
+                    f->last_resid);
+  if (!h.sc.done)
     return ctx_fail(LBM_ERR_STATE, "lbm_fem_step: no convergence in %d iterations (residual %.3e)",
                     f->p.max_iter, f->last_resid);
-  FCK(cudaMemcpyAsync(f->d, f->w.x, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   return LBM_OK;
 }
 
