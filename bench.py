@@ -41,6 +41,11 @@ METRIC = "LBM-ADE GLUPS & % HBM roofline (FP32 vs FP64); adjoint/forward time ra
 # the information content.)
 BYTES_FLUID = {32: 9 * 4 * 2 + 2 * 4 + 1, 64: 9 * 8 * 2 + 2 * 8 + 1}
 BYTES_SOLID = 1
+# FP64 arithmetic of the fused step per fluid node: 8 adds for u, 4 for the
+# velocity terms shared by all directions, 17 per opposite pair (4 pairs) and
+# 3 for the rest population and relaxation factor (an FMA counts 2).
+FLOPS_FLUID_FP64 = 83
+FP64_PEAK_GFLOPS = 1250.0  # nominal dense FP64 of one GB300
 
 
 def _env_int(name, default):
@@ -320,11 +325,18 @@ def main():
         torch.cuda.empty_cache()
         b64 = BYTES_FLUID[64] * (nodes - d64["n_solid"]) + BYTES_SOLID * d64["n_solid"]
         a64 = b64 / (s64_ms / max(s64_n, 1) / 1e3) / 1e9
+        f64_gflops = FLOPS_FLUID_FP64 * (nodes - d64["n_solid"]) / (s64_ms / max(s64_n, 1) / 1e3) / 1e9
         fp64 = {"value": world * nodes * args.fp64_steps / (ms64 / 1e3) / 1e9,
                 "unit": "GLUPS", "steps": args.fp64_steps,
                 "ms_per_step": ms64 / args.fp64_steps,
                 "roofline": {"bound": "hbm", "achieved": a64, "peak": peak,
-                             "unit": "GB/s", "frac": a64 / peak}}
+                             "unit": "GB/s", "frac": a64 / peak},
+                # GB300 runs FP64 at 1/64 of FP32: the FP64 lattice is bound by
+                # its FP64 arithmetic, 83 FP64 flops per fluid node (moments,
+                # equilibrium and collision with the sink; FMA = 2)
+                "alu_roofline": {"bound": "alu", "achieved": f64_gflops, "peak": FP64_PEAK_GFLOPS,
+                                 "unit": "GFLOP/s", "frac": f64_gflops / FP64_PEAK_GFLOPS,
+                                 "peak_kind": "nominal FP64 rate of the part"}}
 
     # ---- end to end through the public API with host buffers -----------------
     e2e = None
