@@ -45,6 +45,9 @@ class Diag(ctypes.Structure):
 
 
 def lib_path() -> str:
+    """liblbmade.so, or its debug-bounds build when LBM_ADE_DEBUG_BOUNDS=1."""
+    if os.environ.get("LBM_ADE_DEBUG_BOUNDS") == "1":
+        return _build.DEBUG_LIB
     return _build.LIB
 
 

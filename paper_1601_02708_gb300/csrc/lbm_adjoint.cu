@@ -71,6 +71,7 @@ struct AdjArgs {
   double* __restrict__ g_ua;        // [nedge] dJ/d(start data)
   double* __restrict__ g_ub;        // [nedge] dJ/d(end data)
   double* __restrict__ g_q;         // [nedge] dJ/dq
+  int* status;  // the context's status word (index checks of the debug build)
   long long plane;
   int nx, ny, pitch, per_x, per_y;
   int edge[4];
@@ -82,19 +83,22 @@ struct AdjArgs {
 template <typename Real, bool kInit, bool kEdge>
 __device__ __forceinline__ void adjoint_node(const AdjArgs<Real>& a, int x, int y, long long n) {
   using namespace lbm;
-  const uint32_t w = a.link[n];
+  const long long nn = dbg_idx(n, a.plane, a.status, kSiteAdjNode);
+  const long long lim = 9 * a.plane;
+  const uint32_t w = a.link[nn];
   if (w & kOwnSolid) return;
   Real lam[9];
-  lam[0] = a.mu_in[n];
+  lam[0] = a.mu_in[nn];
 #pragma unroll
   for (int j = 1; j < 9; ++j) {
     const int jb = opp_of(j);
     if (kEdge && (w & up_bit(kUpOutShift, jb))) {
       lam[j] = (Real)0;
     } else if (w & up_bit(kUpSolidShift, jb)) {
-      lam[j] = a.mu_in[jb * a.plane + n];
+      lam[j] = a.mu_in[dbg_idx(jb * a.plane + n, lim, a.status, kSiteAdjGather)];
     } else {
-      lam[j] = a.mu_in[j * a.plane + n + cx_of(j) + (long long)cy_of(j) * a.pitch];
+      lam[j] = a.mu_in[dbg_idx(j * a.plane + n + cx_of(j) + (long long)cy_of(j) * a.pitch, lim,
+                               a.status, kSiteAdjGather)];
     }
   }
   const uint32_t post = (w >> kUpPostShift) & 0xFFu;
@@ -104,12 +108,12 @@ __device__ __forceinline__ void adjoint_node(const AdjArgs<Real>& a, int x, int 
 #pragma unroll
   for (int i = 1; i < 9; ++i) wl += (Real)w_of(i) * lam[i];
   if (reactive) {
-    if constexpr (sizeof(Real) == 4) a.gk32[n] -= a.u_n[n] * wl;
-    else a.gk[n] -= (double)a.u_n[n] * (double)wl;
+    if constexpr (sizeof(Real) == 4) a.gk32[nn] -= a.u_n[nn] * wl;
+    else a.gk[nn] -= (double)a.u_n[nn] * (double)wl;
   }
   if (kInit) return;
-  const Real kr = reactive ? (a.kf ? a.kf[n] : a.k_scalar) : (Real)0;
-  const Real vx = a.vel[n], vy = a.vel[a.plane + n];
+  const Real kr = reactive ? (a.kf ? a.kf[nn] : a.k_scalar) : (Real)0;
+  const Real vx = a.vel[nn], vy = a.vel[a.plane + nn];
   const Real base = (Real)1 - (Real)1.5 * (vx * vx + vy * vy);
   // sum_i w_i P_i lambda_i, by opposite pairs (P differs in the sign of 3 e.v)
   Real wp = (Real)w_of(0) * base * lam[0];
@@ -176,7 +180,7 @@ __device__ __forceinline__ void adjoint_node(const AdjArgs<Real>& a, int x, int 
 #pragma unroll
   for (int i = 0; i < 9; ++i)
     store_node(a.mu_out + i * a.plane, n, nu[i], ghosts, x, y, a.nx, a.ny, a.pitch, a.per_x,
-               a.per_y);
+               a.per_y, a.plane, a.status);
 }
 
 // One adjoint step (kInit: the gather of lambda^0 and the first collision's
@@ -284,6 +288,7 @@ AdjArgs<Real> adj_args(lbm_ctx* c, AdjWork* w, int mc, const Real* u_n,
   a.g_ua = w->ge;
   a.g_ub = w->ge + c->nedge;
   a.g_q = w->ge + 2 * c->nedge;
+  a.status = c->status;
   a.plane = c->plane;
   a.nx = c->p.nx;
   a.ny = c->p.ny;

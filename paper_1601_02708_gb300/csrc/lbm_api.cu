@@ -584,6 +584,8 @@ lbm_status check_status(lbm_ctx* c) {
   int st = 0;
   CK(cudaMemcpyAsync(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
+  if (st >= lbm::kSiteBase)
+    return fail(LBM_ERR_STATE, "index check %d failed (debug-bounds build)", st);
   if (st) return fail(LBM_ERR_TIMEOUT, "a kernel's bounded wait expired (status %d)", st);
   return LBM_OK;
 }

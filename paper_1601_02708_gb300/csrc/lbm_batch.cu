@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(lbm::kTmaThreads + 32, 1)
       const int4 td = *reinterpret_cast<const int4*>(st + kOffTd);
       const StepArgs<float>& a = *reinterpret_cast<const StepArgs<float>*>(st + kOffArgs);
       SmemSrc src{(const float*)st, (const float*)(st + kOffVel), (const float*)(st + kOffK),
-                  (const uint32_t*)(st + kOffWord), r, 0};
+                  (const uint32_t*)(st + kOffWord), r, 0, a.status};
       const int x0 = td.y, y = td.z + r;
       double tile_u = 0.0;
 #pragma unroll 1
@@ -306,10 +306,10 @@ __global__ void __launch_bounds__(lbm::kDThreads)
     }
     const uint32_t fluid = ~((w >> lbm::kUpPostShift) | (w >> lbm::kUpOutShift)) & 0xFFu;
     if (!fluid) continue;
-    const double m = d.smin[e] - (double)lbm::mineral_take(rlink, n, d.pitch, fluid);
+    const double m = d.smin[e] - (double)lbm::mineral_take(rlink, n, d, fluid);
     d.smin[e] = m;
     if (m <= 0.0) {
-      d.flip_list[atomicAdd(d.flip_count, 1)] = n;
+      d.flip_list[lbm::dbg_idx(atomicAdd(d.flip_count, 1), (long long)d.nx * d.ny, d.status, lbm::kSiteList)] = n;
       flipped = true;
     }
   }

@@ -128,6 +128,7 @@ inline lbm::DissolveArgs dissolve_args(lbm_ctx* c) {
   d.slist = c->slist;
   d.smin = c->smin;
   d.flips_total = c->counters;
+  d.status = c->status;
   d.nx = c->p.nx;
   d.ny = c->p.ny;
   d.pitch = c->pitch;

@@ -41,20 +41,13 @@ namespace {
                       __FILE__, __LINE__);                                       \
   } while (0)
 
-#define FTRY(...)                   \
-  do {                              \
-    lbm_status s_ = (__VA_ARGS__);  \
-    if (s_ != LBM_OK) return s_;    \
-  } while (0)
-
 constexpr int kThreads = 256;
 
-// Device scalars of the solver.
+// Outcome of one solve, written by the solver for the host.
 struct Scal {
-  double rho, alpha, omega, beta;
-  double bnorm2, rnorm2;
-  int done;      // converged (or broken down): every kernel returns at once
-  int breakdown;
+  double bnorm2, rnorm2;  // squared norms of the free rows' rhs and final residual
+  int done;               // converged
+  int breakdown;          // BiCGSTAB broke down before converging
 };
 
 struct Vec {
@@ -329,7 +322,6 @@ struct lbm_fem {
   lbm_fem_params p;
   int nxn = 0, nyn = 0;
   long long n = 0;
-  int nb = 0;  // blocks of the vector kernels
   int n_dir = 0;
   cudaStream_t stream = nullptr;
   double* A = nullptr;  // [9][n]
@@ -340,7 +332,7 @@ struct lbm_fem {
   double* vecs = nullptr;   // storage of w
   int* fixed_id = nullptr;  // per node: index into the prescribed values, -1 free, -2 inactive
   double* fixed_val = nullptr;
-  double* part = nullptr;   // 4 x nb partials
+  double* part = nullptr;   // [4][grid] partial dots
   Scal* sc = nullptr;
   int* iters = nullptr;
   unsigned* bar = nullptr;  // grid barrier [2]
@@ -480,7 +472,6 @@ lbm_status lbm_fem_init(lbm_fem** out, const lbm_fem_params* p, const uint8_t* e
   f->nxn = p->nex + 1;
   f->nyn = p->ney + 1;
   f->n = (long long)f->nxn * f->nyn;
-  f->nb = (int)((f->n + kThreads - 1) / kThreads);
   f->n_dir = n_dir;
   f->stream = (cudaStream_t)stream;
   const long long n = f->n;

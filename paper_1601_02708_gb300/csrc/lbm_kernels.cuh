@@ -131,11 +131,12 @@ __device__ __forceinline__ float share(float a, float b) { return __fdividef(a, 
 template <typename Real>
 __device__ __forceinline__ void store_node(Real* __restrict__ base, long long n, Real v,
                                            bool ghosts, int x, int y, int nx, int ny,
-                                           int pitch, int per_x, int per_y) {
-  base[n] = v;
+                                           int pitch, int per_x, int per_y,
+                                           long long limit = 1ll << 62, int* flag = nullptr) {
+  base[dbg_idx(n, limit, flag, kSiteStore)] = v;
   if (ghosts)
     for_each_ghost(x, y, nx, ny, per_x, per_y, [&](int gx, int gy) {
-      base[(long long)gy * pitch + gx] = v;
+      base[dbg_idx((long long)gy * pitch + gx, limit, flag, kSiteStore)] = v;
     });
 }
 
@@ -147,17 +148,21 @@ struct GlobalSrc {
   __device__ __forceinline__ long long up(int i) const {  // index of x - e_i
     return n - (long long)cx_of(i) - (long long)cy_of(i) * a.pitch;
   }
-  __device__ __forceinline__ uint32_t word() const { return a.link[n]; }
-  __device__ __forceinline__ Real pull(int i) const { return a.fin[i * a.plane + up(i)]; }
-  __device__ __forceinline__ Real own(int i) const { return a.fin[i * a.plane + n]; }
+  __device__ __forceinline__ long long nd() const { return dbg_idx(n, a.plane, a.status, kSiteNode); }
+  __device__ __forceinline__ long long pop(long long i) const {
+    return dbg_idx(i, 9 * a.plane, a.status, kSitePull);
+  }
+  __device__ __forceinline__ uint32_t word() const { return a.link[nd()]; }
+  __device__ __forceinline__ Real pull(int i) const { return a.fin[pop(i * a.plane + up(i))]; }
+  __device__ __forceinline__ Real own(int i) const { return a.fin[pop(i * a.plane + n)]; }
   // pull of direction i, or halfway bounce-back of the node's own opposite
   // population: one load from the chosen address
   __device__ __forceinline__ Real pull_or_bounce(int i, bool bounce) const {
-    return a.fin[bounce ? (long long)opp_of(i) * a.plane + n : i * a.plane + up(i)];
+    return a.fin[pop(bounce ? (long long)opp_of(i) * a.plane + n : i * a.plane + up(i))];
   }
-  __device__ __forceinline__ Real vx() const { return a.vel[n]; }
-  __device__ __forceinline__ Real vy() const { return a.vel[a.plane + n]; }
-  __device__ __forceinline__ Real kf() const { return a.kf[n]; }
+  __device__ __forceinline__ Real vx() const { return a.vel[nd()]; }
+  __device__ __forceinline__ Real vy() const { return a.vel[a.plane + nd()]; }
+  __device__ __forceinline__ Real kf() const { return a.kf[nd()]; }
 };
 
 // One node's step.  (x, y) interior coordinates, n its padded index.  Writes
@@ -187,12 +192,12 @@ __device__ __forceinline__ double step_node(const StepArgs<Real>& a, const Src& 
 #pragma unroll
       for (int i = 0; i < 9; ++i)
         store_node(a.fout + i * a.plane, n, (Real)0, ghosts, x, y, a.nx, a.ny, a.pitch,
-                   a.per_x, a.per_y);
+                   a.per_x, a.per_y, a.plane, a.status);
       if (a.dissolution && (w & kOwnPending))
         store_node(a.ureact, n, (Real)0, ghosts, x, y, a.nx, a.ny, a.pitch, a.per_x,
-                   a.per_y);
+                   a.per_y, a.plane, a.status);
     }
-    if (kFinal) a.u_out[n] = (Real)0;
+    if (kFinal) a.u_out[dbg_idx(n, a.plane, a.status, kSiteNode)] = (Real)0;
     return 0.0;
   }
   Real f[9];
@@ -249,17 +254,17 @@ __device__ __forceinline__ double step_node(const StepArgs<Real>& a, const Src& 
 #pragma unroll
   for (int i = 0; i < 9; ++i)
     store_node(a.fout + i * a.plane, n, f[i], ghosts, x, y, a.nx, a.ny, a.pitch,
-               a.per_x, a.per_y);
+               a.per_x, a.per_y, a.plane, a.status);
   // mass this node takes from each solid neighbour per unit link weight
   if (a.dissolution && near_solid) {
     const Real wsolid = (Real)__popc(post & 0x0Fu) * (Real)w_of(1) +
                         (Real)__popc(post & 0xF0u) * (Real)w_of(5);
     store_node(a.ureact, n, share(kr * u, wsolid), ghosts, x, y, a.nx, a.ny, a.pitch,
-               a.per_x, a.per_y);
+               a.per_x, a.per_y, a.plane, a.status);
   }
   // one node per row adds to its row's sum: a reduction without a read-back
   if (kEdge && x == a.nx - 1) atomicAdd(a.jnode + y, (double)u);
-  if (kFinal) a.u_out[n] = u;
+  if (kFinal) a.u_out[dbg_idx(n, a.plane, a.status, kSiteNode)] = u;
   return (double)u;
 }
 
@@ -327,10 +332,10 @@ __global__ void __launch_bounds__(kBX * kBY)
 #pragma unroll
       for (int i = 0; i < 9; ++i)
         store_node(a.fout + i * a.plane, n, f[i], ghosts, x, y, a.nx, a.ny, a.pitch,
-                   a.per_x, a.per_y);
+                   a.per_x, a.per_y, a.plane, a.status);
       if (a.dissolution && near_solid)
         store_node(a.ureact, n, kr * u / wsolid, ghosts, x, y, a.nx, a.ny, a.pitch,
-                   a.per_x, a.per_y);
+                   a.per_x, a.per_y, a.plane, a.status);
       a.u_out[n] = u;
       my_u = (double)u;
     }
@@ -350,6 +355,7 @@ struct DissolveArgs {
   int* flip_count;
   unsigned* done;
   long long* flips_total;
+  int* status;    // the context's status word (index checks of the debug build)
   int nx, ny, pitch, per_x, per_y;
   int check_all;  // also flip untouched solid nodes whose mineral is <= 0
 };
@@ -392,12 +398,15 @@ __device__ __forceinline__ void clear_in_neighbours(const DissolveArgs& d, int x
 // enters the FP64 mineral.
 template <typename Real>
 __device__ __forceinline__ Real mineral_take(const Real* __restrict__ rlink, long long n,
-                                             int pitch, uint32_t fluid) {
+                                             const DissolveArgs& d, uint32_t fluid) {
+  const long long plane = (long long)d.pitch * padded_rows(d.ny);
   Real take = (Real)0;
 #pragma unroll
   for (int j = 1; j < 9; ++j)
     if (fluid & (1u << (j - 1)))
-      take += (Real)w_of(j) * rlink[n - cx_of(j) - (long long)cy_of(j) * pitch];
+      take += (Real)w_of(j) *
+              rlink[dbg_idx(n - cx_of(j) - (long long)cy_of(j) * d.pitch, plane, d.status,
+                            kSiteShare)];
   return take;
 }
 
@@ -420,7 +429,8 @@ __device__ inline void apply_flips(const DissolveArgs& d, int tid, int nthreads)
       const uint32_t old = atomicAnd(d.link + z, ~up_bit(kUpPostShift, i));
       if ((old & kOwnSolid) && !(old & kListed) &&
           !(atomicOr(d.link + z, kListed) & kListed)) {
-        const int slot = atomicAdd(d.scount, 1);
+        const long long slot =
+            dbg_idx(atomicAdd(d.scount, 1), (long long)d.nx * d.ny, d.status, kSiteList);
         d.slist[slot] = z;
         d.smin[slot] = d.mineral[z];
       }
@@ -462,10 +472,10 @@ __global__ void __launch_bounds__(kDThreads)
     }
     const uint32_t fluid = ~((w >> kUpPostShift) | (w >> kUpOutShift)) & 0xFFu;
     if (!fluid) continue;
-    const double m = d.smin[e] - (double)mineral_take(rlink, n, d.pitch, fluid);
+    const double m = d.smin[e] - (double)mineral_take(rlink, n, d, fluid);
     d.smin[e] = m;
     if (m <= 0.0) {
-      d.flip_list[atomicAdd(d.flip_count, 1)] = n;
+      d.flip_list[dbg_idx(atomicAdd(d.flip_count, 1), (long long)d.nx * d.ny, d.status, kSiteList)] = n;
       flipped = true;
     }
   }
@@ -502,10 +512,10 @@ __global__ void __launch_bounds__(kDThreads)
     }
     const uint32_t fluid = ~((w >> kUpPostShift) | (w >> kUpOutShift)) & 0xFFu;
     if (!fluid && !d.check_all) continue;
-    const double m = d.mineral[n] - (double)mineral_take(rlink, n, d.pitch, fluid);
+    const double m = d.mineral[n] - (double)mineral_take(rlink, n, d, fluid);
     if (fluid) d.mineral[n] = m;
     if (m <= 0.0) {
-      d.flip_list[atomicAdd(d.flip_count, 1)] = n;
+      d.flip_list[dbg_idx(atomicAdd(d.flip_count, 1), (long long)d.nx * d.ny, d.status, kSiteList)] = n;
       flipped = true;
     }
   }

@@ -39,6 +39,34 @@ constexpr int kUpPostShift = 8;
 constexpr int kUpOutShift = 16;
 __host__ __device__ constexpr uint32_t up_bit(int shift, int i) { return 1u << (shift + i - 1); }
 
+// Index checks of the debug-bounds build (compiled with LBM_DEBUG_BOUNDS, in
+// place of a memory checker): an index outside [0, limit) records its check
+// site in *flag (the first one wins, the host reports it) and is replaced by
+// 0, so the access stays inside the array.  The normal build compiles the
+// check away.
+#ifdef LBM_DEBUG_BOUNDS
+__device__ __forceinline__ long long dbg_idx(long long i, long long limit, int* flag, int site) {
+  if (i >= 0 && i < limit) return i;
+  if (flag) atomicCAS(flag, 0, site);
+  return 0;
+}
+#else
+__device__ __forceinline__ long long dbg_idx(long long i, long long, int*, int) { return i; }
+#endif
+// Sites (values of the status word >= kSiteBase name the failed check).
+enum {
+  kSiteBase = 100,
+  kSitePull = 101,     // global population read of the step
+  kSiteNode = 102,     // per-node global field of the step (word, velocity, rate, u)
+  kSiteStore = 103,    // global store of a node value or ghost image
+  kSiteSmemPop = 111,  // shared-memory population read (tile pipeline)
+  kSiteSmemNode = 112, // shared-memory per-node field (tile pipeline)
+  kSiteShare = 121,    // reaction share read by the dissolution
+  kSiteList = 122,     // surface-list or flip-list entry
+  kSiteAdjGather = 131,  // adjoint state read by the reverse step
+  kSiteAdjNode = 132,    // per-node field of the reverse step
+};
+
 // Padded layout of every node field: interior node (x, y) lives at column
 // x + kXO and row y + kYO of a [rows][pitch] array, pitch a multiple of 32
 // with pitch >= nx + 16, rows >= ny + 2.  Column kXO - 1, column nx + kXO,

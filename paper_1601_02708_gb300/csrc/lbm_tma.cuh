@@ -93,21 +93,28 @@ struct SmemSrc {
   const float* kfield;   // [kTH][kTW]
   const uint32_t* words; // [kTH][kTW] link words
   int r, c;              // node's row in the tile, column in the halo box (xl + 4)
+  int* flag;             // status word (index checks of the debug build)
   __device__ __forceinline__ int at(int i) const {  // box offset of x - e_i
     return (r + 1 - cy_of(i)) * kBoxW + (c - cx_of(i));
   }
-  __device__ __forceinline__ uint32_t word() const { return words[r * kTW + (c - 4)]; }
-  __device__ __forceinline__ float pull(int i) const { return pop[i * kBoxH * kBoxW + at(i)]; }
+  __device__ __forceinline__ long long pb(long long i) const {
+    return dbg_idx(i, 9 * kBoxH * kBoxW, flag, kSiteSmemPop);
+  }
+  __device__ __forceinline__ long long nb(long long i, int planes = 1) const {
+    return dbg_idx(i, planes * kTH * kTW, flag, kSiteSmemNode);
+  }
+  __device__ __forceinline__ uint32_t word() const { return words[nb(r * kTW + (c - 4))]; }
+  __device__ __forceinline__ float pull(int i) const { return pop[pb(i * kBoxH * kBoxW + at(i))]; }
   __device__ __forceinline__ float own(int i) const {
-    return pop[i * kBoxH * kBoxW + (r + 1) * kBoxW + c];
+    return pop[pb(i * kBoxH * kBoxW + (r + 1) * kBoxW + c)];
   }
   __device__ __forceinline__ float pull_or_bounce(int i, bool bounce) const {
-    return pop[bounce ? opp_of(i) * kBoxH * kBoxW + (r + 1) * kBoxW + c
-                      : i * kBoxH * kBoxW + at(i)];
+    return pop[pb(bounce ? opp_of(i) * kBoxH * kBoxW + (r + 1) * kBoxW + c
+                         : i * kBoxH * kBoxW + at(i))];
   }
-  __device__ __forceinline__ float vx() const { return vel[r * kTW + (c - 4)]; }
-  __device__ __forceinline__ float vy() const { return vel[(kTH + r) * kTW + (c - 4)]; }
-  __device__ __forceinline__ float kf() const { return kfield[r * kTW + (c - 4)]; }
+  __device__ __forceinline__ float vx() const { return vel[nb(r * kTW + (c - 4), 2)]; }
+  __device__ __forceinline__ float vy() const { return vel[nb((kTH + r) * kTW + (c - 4), 2)]; }
+  __device__ __forceinline__ float kf() const { return kfield[nb(r * kTW + (c - 4))]; }
 };
 
 struct TmaMaps {
@@ -192,7 +199,7 @@ __global__ void __launch_bounds__(kTmaThreads + 32, 1)
       if (*(volatile int*)&abort_flag) break;
       const unsigned char* st = smem + s * kStageBytes;
       SmemSrc src{(const float*)st, (const float*)(st + kOffVel), (const float*)(st + kOffK),
-                  (const uint32_t*)(st + kOffWord), r, 0};
+                  (const uint32_t*)(st + kOffWord), r, 0, a.status};
       const int x0 = (t % ntx) * kTW, y = (t / ntx) * kTH + r;
 #pragma unroll 1
       for (int j = 0; j < kNodesPerLane; ++j) {
