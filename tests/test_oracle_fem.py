@@ -212,3 +212,54 @@ def test_coupled_steady_linear_profile(oracle_mod):
     assert np.abs(f.d - (1.0 + x_fem)).max() <= 1e-9
     x_lat = 0.5 + np.arange(nfx + 1) * h
     assert np.abs(lbm.u() - (1.0 + x_lat)[None, :]).max() <= 1e-9
+
+
+def _coupled_gaussian(level, T=0.02, D=0.05):
+    """A Gaussian pulse centred in the overlap diffuses across both
+    subdomains (pure diffusion, y-invariant data): FEM on [0, 0.6], lattice
+    on [0.5, 1.0], eta = 4 substeps per coarse step, 3 Schwarz iterations,
+    both grids refined together with a diffusive time step.  Returns the
+    max errors against the free-space solution at T in each subdomain."""
+    from oracle import LBMOracle
+    fem = _fem()
+    nfx = 32 * 2 ** level
+    h = 0.5 / nfx
+    tau = 1.0
+    dt_f = (tau - 0.5) / 3.0 * h * h / D      # physical time of one lattice step
+    eta = 4
+    nex = 12 * 2 ** level
+    hx = 0.6 / nex
+    ny_f = 4
+    x0, s0 = 0.55, 0.03 ** 2
+
+    def exact(x, t):
+        return math.sqrt(s0 / (s0 + 2 * D * t)) * np.exp(-(x - x0) ** 2 / (2 * (s0 + 2 * D * t)))
+
+    xl = 0.5 + np.arange(nfx + 1) * h
+    lbm = LBMOracle(nfx + 1, ny_f, tau, edges=(1, 2, 0, 0), u0=np.tile(exact(xl, 0), (ny_f, 1)))
+    nxn = nex + 1
+    west, east = _x_sides(nex, 1)
+    xf = (np.arange(2 * nxn) % nxn) * hx
+    f = fem.Q1FEM(nex, 1, 0.0, 0.0, hx, ny_f * h, D=D, dt=eta * dt_f, dirichlet=west + east,
+                  d0=exact(xf, 0))
+    gamma = np.array([[(0.6 - 0.5) / h, 0.0]] * 2)
+    pts = np.array([[0.5, y * h] for y in range(ny_f)])
+    slots = np.arange(ny_f)
+    ncoarse = int(round(T / (eta * dt_f)))
+    for _ in range(ncoarse):
+        fem.schwarz_step(f, lbm, eta, 3, [0.0, 0.0], gamma, pts, slots)
+    t = ncoarse * eta * dt_f
+    ec = np.abs(f.d[:nxn] - exact(xf[:nxn], t)).max()
+    ef = np.abs(lbm.u()[0] - exact(xl, t)).max()
+    return ec, ef
+
+
+def test_coupled_gaussian_converges_to_the_exact_solution(oracle_mod):
+    """The transient coupled solution (Algorithm 1 with the multi-time-step
+    interpolation) approaches the continuum solution in both subdomains as
+    both grids are refined together."""
+    errs = [_coupled_gaussian(level) for level in range(3)]
+    (c0, f0), (c1, f1), (c2, f2) = errs
+    assert c2 <= 4e-3 and f2 <= 1.2e-3
+    assert c0 / c1 >= 2.0 and c1 / c2 >= 2.0
+    assert f0 / f1 >= 1.8 and f1 / f2 >= 1.8
