@@ -127,3 +127,50 @@ def test_block_hybrid_full_size_one_coarse_step(pkg, oracle_mod):
     assert np.abs(run.continuum() - fem.d).max() <= 1e-5
     u = run.lbm.concentration()
     assert np.abs(u - lbm.u()).max() <= 1e-5
+
+
+def _gaussian_layout(level=1, T=0.02, D=0.05):
+    """Pure diffusion of a Gaussian centred in the overlap (the oracle's
+    transient coupling pin), as a layout for the library's driver."""
+    import math
+    nfx, ny_f, eta, tau = 32 * 2 ** level, 4, 4, 1.0
+    h = 0.5 / nfx
+    dt_f = (tau - 0.5) / 3.0 * h * h / D
+    nex = 12 * 2 ** level
+    hx = 0.6 / nex
+    x0, s0 = 0.55, 0.03 ** 2
+
+    def exact(x, t):
+        return math.sqrt(s0 / (s0 + 2 * D * t)) * np.exp(-(x - x0) ** 2 / (2 * (s0 + 2 * D * t)))
+
+    xl = 0.5 + np.arange(nfx + 1) * h
+    nxn = nex + 1
+    xf = (np.arange(2 * nxn) % nxn) * hx
+    ncoarse = int(round(T / (eta * dt_f)))
+    layout = dict(
+        lbm=dict(nx=nfx + 1, ny=ny_f, tau=tau, edges=(1, 2, 0, 0),
+                 u0=np.tile(exact(xl, 0), (ny_f, 1))),
+        fem=dict(nex=nex, ney=1, x0=0.0, y0=0.0, hx=hx, hy=ny_f * h, D=D, v=(0.0, 0.0),
+                 theta=0.5, dt=eta * dt_f, supg=False, elem_active=None,
+                 dirichlet=[0, nxn, nex, nxn + nex], d0=exact(xf, 0)),
+        fixed_values=np.zeros(2), gamma_lattice_xy=np.array([[(0.6 - 0.5) / h, 0.0]] * 2),
+        lbm_points=np.array([[0.5, y * h] for y in range(ny_f)]), lbm_slots=(0, ny_f),
+        q_neu=None, eta=eta, max_iter=3, n_coarse=ncoarse, h=h)
+    return layout, exact, xl, xf[:nxn], ncoarse * eta * dt_f
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_coupled_gaussian_against_oracle_and_exact(pkg, oracle_mod, prec):
+    from paper_1601_02708_gb300.hybrid import Hybrid
+    layout, exact, xl, xf, t = _gaussian_layout()
+    run = Hybrid(layout, precision=prec)
+    run.run()
+    fem, lbm = _oracle_run(layout, layout["n_coarse"])
+    tol = 1e-9 if prec == 64 else 1e-5
+    d = run.continuum()
+    u = run.lbm.concentration()
+    assert np.abs(d - fem.d).max() <= tol
+    assert np.abs(u - lbm.u()).max() <= tol
+    nxn = len(xf)
+    assert np.abs(d[:nxn] - exact(xf, t)).max() <= 1.2e-2   # level-1 errors of the pin
+    assert np.abs(u[0] - exact(xl, t)).max() <= 3.5e-3
