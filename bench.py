@@ -448,7 +448,8 @@ def main():
         hybrid = {}
         for name, layout, ncoarse in (
                 ("plain", inputs.hybrid_plain_layout(), 100),
-                ("pore_block", inputs.hybrid_block_layout(), args.hybrid_coarse)):
+                ("pore_block", inputs.hybrid_block_layout(), args.hybrid_coarse),
+                ("many_blocks", inputs.hybrid_multiblock_layout(), 50)):
             run = Hybrid(layout, precision=32)
             run.run(1)  # warm-up: allocations, first solves
             barrier()
@@ -459,12 +460,13 @@ def main():
             ev1.synchronize()
             wall = time.perf_counter() - t0
             hms = max_over_ranks(ev0.elapsed_time(ev1))
-            lat = layout["lbm"]
-            node_steps = lat["nx"] * lat["ny"] * layout["eta"] * layout["max_iter"] * ncoarse
+            lats = layout["lbms"] if "lbms" in layout else [layout["lbm"]]
+            node_steps = sum(a["nx"] * a["ny"] for a in lats) * layout["eta"] * \
+                layout["max_iter"] * ncoarse
             its = run.solver_iters[-ncoarse * layout["max_iter"]:]
             hybrid[name] = {
                 "coarse_steps": ncoarse, "ms_per_coarse_step": hms / ncoarse,
-                "lattice": [lat["nx"], lat["ny"]],
+                "lattices": [[a["nx"], a["ny"]] for a in lats],
                 "fem_elements": [layout["fem"]["nex"], layout["fem"]["ney"]],
                 "substeps": layout["eta"], "schwarz_iterations": layout["max_iter"],
                 "lattice_glups": world * node_steps / (hms / 1e3) / 1e9,

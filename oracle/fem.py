@@ -198,3 +198,32 @@ def schwarz_step(fem, lbm, eta, max_iter, fem_fixed_values, fem_gamma_lattice_xy
         lbm.substeps(eta, eta, ua, ub, q_neu)
         trace = lbm.trace(fem_gamma_lattice_xy)
     return trace
+
+
+def schwarz_step_many(fem, lbms, eta, max_iter, fem_fixed_values, fem_gamma_lattice_xy,
+                      lbm_gamma_points, lbm_gamma_slots, q_neu=None):
+    """One coarse step of Algorithm 2 with one continuum subdomain and several
+    fine ones: the continuum's Dirichlet list is [fixed nodes..., Gamma_f->c
+    nodes of lattice 0..., of lattice 1..., ...]; the per-lattice arguments
+    are lists.  Each Schwarz iteration advances the continuum with the traces
+    of every lattice, then every lattice with the continuum's interpolants at
+    t_n and t_{n+1}; all restart from t_n after the first iteration."""
+    d_n = fem.d.copy()
+    snaps = [l.snapshot() for l in lbms]
+    traces = [l.trace(g) for l, g in zip(lbms, fem_gamma_lattice_xy)]
+    ua_all = []
+    for l, p, s in zip(lbms, lbm_gamma_points, lbm_gamma_slots):
+        ua = np.zeros(l.n_edge)
+        ua[s] = fem.interpolate(p)
+        ua_all.append(ua)
+    for it in range(max_iter):
+        fem.d = d_n.copy()
+        fem.step(np.concatenate([np.asarray(fem_fixed_values, float)] + traces))
+        for k, (l, p, s) in enumerate(zip(lbms, lbm_gamma_points, lbm_gamma_slots)):
+            ub = np.zeros(l.n_edge)
+            ub[s] = fem.interpolate(p)
+            if it > 0:
+                l.rollback(snaps[k])
+            l.substeps(eta, eta, ua_all[k], ub, q_neu)
+        traces = [l.trace(g) for l, g in zip(lbms, fem_gamma_lattice_xy)]
+    return traces

@@ -292,3 +292,59 @@ def hybrid_block_layout(nex: int = 400, ney: int = 100, hole=(170, 230, 20, 80),
         fixed_values=np.ones(len(inlet)), gamma_lattice_xy=gamma_xy,
         lbm_points=pts, lbm_slots=(0, 4 * n_f), q_neu=None,
         eta=eta, max_iter=max_iter, n_coarse=n_coarse, h=h)
+
+
+def hybrid_multiblock_layout(nex: int = 200, ney: int = 50,
+                             holes=((30, 60, 10, 40), (100, 120, 20, 40), (150, 190, 5, 25)),
+                             n_f=(512, 256, 384), seed: int = 7, porosity: float = 0.55,
+                             k: float = 5e-4, tau: float = 0.7, eta: int = 20,
+                             max_iter: int = 3, n_coarse: int = 50, rmin: float = 8.0,
+                             rmax: float = 24.0) -> dict:
+    """Several pore blocks in one continuum (the many-subdomain coupling of
+    Algorithm 2 with one continuum subdomain): [0, 4] x [0, 1] on nex x ney
+    Q1 elements with one element-aligned hole per block; block b covers its
+    hole plus two elements per side and holds an n_f[b] x n_f[b] lattice of
+    the disk / stream-function generator (seed + b) with surface reaction and
+    dissolution.  One diffusivity D = (tau - 1/2)/3 h_min^2 (h_min the finest
+    block spacing, time unit one lattice step) holds everywhere: block b
+    relaxes with tau_b = 1/2 + 3 D / h_b^2.  c = 1 at the inlet x = 0 and
+    c0 = 1 everywhere.  Blocks must not overlap."""
+    hc = 4.0 / nex
+    assert abs(1.0 / ney - hc) < 1e-12 and len(holes) == len(n_f)
+    act = np.ones((ney, nex), np.uint8)
+    nxn = nex + 1
+    inlet = [j * nxn for j in range(ney + 1)]
+    lbms, gammas, points, slots, rings = [], [], [], [], []
+    h_min = min(((i1 - i0 + 4) * hc) / (nf - 1) for (i0, i1, _, _), nf in zip(holes, n_f))
+    D = (tau - 0.5) / 3.0 * h_min * h_min
+    for b, ((i0, i1, j0, j1), nf) in enumerate(zip(holes, n_f)):
+        act[j0:j1, i0:i1] = 0
+        bx0, bx1 = (i0 - 2) * hc, (i1 + 2) * hc
+        by0, by1 = (j0 - 2) * hc, (j1 + 2) * hc
+        nfx = nf
+        h = (bx1 - bx0) / (nfx - 1)
+        nfy = int(round((by1 - by0) / h)) + 1
+        tau_b = 0.5 + 3.0 * D / (h * h)
+        ring = [j * nxn + i for j in range(j0, j1 + 1) for i in range(i0, i1 + 1)
+                if i in (i0, i1) or j in (j0, j1)]
+        rings += ring
+        gammas.append(np.array([[((r % nxn) * hc - bx0) / h, ((r // nxn) * hc - by0) / h]
+                                for r in ring]))
+        xs = bx0 + np.arange(nfx) * h
+        ys = by0 + np.arange(nfy) * h
+        points.append(np.concatenate([
+            np.stack([np.full(nfy, bx0), ys], 1), np.stack([np.full(nfy, bx0 + (nfx - 1) * h), ys], 1),
+            np.stack([xs, np.full(nfx, by0)], 1), np.stack([xs, np.full(nfx, by0 + (nfy - 1) * h)], 1)]))
+        slots.append((0, 2 * (nfx + nfy)))
+        solid = disk_packing(nfx, nfy, porosity, seed + b, rmin=rmin, rmax=rmax)
+        vel = streamfunction_velocity(nfx, nfy, seed + b + 1_000_003, solid=solid)
+        lbms.append(dict(nx=nfx, ny=nfy, tau=tau_b, edges=(1, 1, 1, 1), solid=solid, vel=vel,
+                         u0=np.where(solid != 0, 0.0, 1.0), react_mode=1, k=k, dissolution=True,
+                         mineral=np.ones((nfy, nfx))))
+    return dict(
+        lbms=lbms,
+        fem=dict(nex=nex, ney=ney, x0=0.0, y0=0.0, hx=hc, hy=hc, D=D, v=(0.0, 0.0),
+                 theta=0.5, dt=float(eta), supg=False, elem_active=act,
+                 dirichlet=inlet + rings, d0=np.ones((ney + 1) * nxn)),
+        fixed_values=np.ones(len(inlet)), gamma_lattice_xy=gammas, lbm_points=points,
+        lbm_slots=slots, q_neu=None, eta=eta, max_iter=max_iter, n_coarse=n_coarse)

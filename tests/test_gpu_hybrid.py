@@ -174,3 +174,34 @@ def test_coupled_gaussian_against_oracle_and_exact(pkg, oracle_mod, prec):
     nxn = len(xf)
     assert np.abs(d[:nxn] - exact(xf, t)).max() <= 1.2e-2   # level-1 errors of the pin
     assert np.abs(u[0] - exact(xl, t)).max() <= 3.5e-3
+
+
+@pytest.mark.parametrize("prec,k", [(64, 5e-2), (32, 5e-4)])
+def test_many_blocks_in_one_continuum(pkg, oracle_mod, prec, k):
+    """Algorithm 2 with one continuum and two pore blocks of different
+    spacing, stepped together as a batch, against the oracle's
+    many-subdomain step."""
+    from oracle import LBMOracle
+    from oracle.fem import Q1FEM, schwarz_step_many
+    from paper_1601_02708_gb300 import inputs
+    from paper_1601_02708_gb300.hybrid import Hybrid
+    layout = inputs.hybrid_multiblock_layout(nex=40, ney=10, holes=((5, 9, 2, 6), (20, 26, 3, 7)),
+                                             n_f=(64, 72), k=k, eta=10, max_iter=3,
+                                             n_coarse=3, rmin=2, rmax=5)
+    run = Hybrid(layout, precision=prec)
+    run.run()
+    fem = Q1FEM(**layout["fem"])
+    lbms = [LBMOracle(**a) for a in layout["lbms"]]
+    slots = [np.arange(a, b) for a, b in layout["lbm_slots"]]
+    for _ in range(3):
+        schwarz_step_many(fem, lbms, layout["eta"], layout["max_iter"], layout["fixed_values"],
+                          layout["gamma_lattice_xy"], layout["lbm_points"], slots)
+    tol = 1e-9 if prec == 64 else 1e-5
+    assert np.abs(run.continuum() - fem.d).max() <= tol
+    flips = 0
+    for lat, ref in zip(run.lbms, lbms):
+        assert np.abs(lat.concentration() - ref.u()).max() <= tol
+        assert np.array_equal(lat.solid(), ref.solid())
+        flips += ref.diag()["flips"]
+    assert flips > 0 or prec == 32
+    assert fem.d[fem.free].min() < 1.0 - 1e-9  # the blocks draw the continuum down
