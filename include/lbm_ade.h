@@ -242,7 +242,7 @@ lbm_status lbm_batch_substeps(lbm_batch* b, int n, int eta, const double* const*
 /* Tile shape of the step kernel.  Shapes 0 .. 5: one thread per node, tiles
  * of 32 x tile_h nodes, `threads` threads per block, each thread
  * 32 * tile_h / threads rows apart.  Shape 6 (pipelined = 1): the TMA-fed pipeline of the
- * single-lattice FP32 kernel over 128 x 8 tiles, one CTA per SM, available
+ * single-lattice FP32 kernel over 96 x 8 tiles, one CTA per SM, available
  * for FP32 members (LBM_ERR_ARG otherwise) and the default where available.
  * Results do not depend on the shape; the speed does.  lbm_batch_time_steps
  * times n steps (eta = 1, the current edge data) in milliseconds, advancing

@@ -320,10 +320,10 @@ lbm_status launch_step_impl<float>(lbm_ctx* c, const lbm::StepArgs<float>& a,
   if (c->use_tma) {
     const lbm::TmaMaps& m = c->maps[c->cur];
     if (final_step)
-      lbm::lbm_step_tma<true><<<c->tma_grid, lbm::kTmaThreads + 32, lbm::kTmaSmem, c->stream>>>(
+      lbm::lbm_step_tma<true><<<c->tma_grid, lbm::kTmaBlock, lbm::kTmaSmem, c->stream>>>(
           a, m, c->ntx, c->nty);
     else
-      lbm::lbm_step_tma<false><<<c->tma_grid, lbm::kTmaThreads + 32, lbm::kTmaSmem, c->stream>>>(
+      lbm::lbm_step_tma<false><<<c->tma_grid, lbm::kTmaBlock, lbm::kTmaSmem, c->stream>>>(
           a, m, c->ntx, c->nty);
     if (final_step) c->nparts = c->tma_grid;
   } else {

@@ -48,9 +48,9 @@ constexpr int kTileMask = kRateBit - 1;
 
 // Tile shapes of the plain kernel: 32 columns x kBY rows of threads, each
 // thread kR rows apart.  Shape kTmaShape is the TMA-fed pipeline (FP32):
-// 128 x 8 tiles, one CTA per SM.  Every shape covers at least 32 x 8 nodes,
-// so a member never has more tiles than the partial-sum slots its context
-// allocated (one per 32 x 8 block).
+// kTW x kTH (96 x 8) tiles, one CTA per SM.  Every shape covers at least
+// 32 x 8 nodes, so a member never has more tiles than the partial-sum slots
+// its context allocated (one per 32 x 8 block).
 struct Shape {
   int by, r;
 };
@@ -128,14 +128,6 @@ constexpr int kBTmaSmem = lbm::kStages * kBStage;
 static_assert(kArgBytes % 16 == 0, "bulk copies move whole 16-byte units");
 static_assert(kBTmaSmem + 1024 <= 227 * 1024, "stages exceed shared memory");
 
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes,
-                                          uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-          "r"(lbm::smem_addr(dst)),
-      "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(lbm::smem_addr(bar))
-      : "memory");
-}
 // A tensor map written to global memory by the host is made visible to the
 // tensor-map proxy of this thread before its first use.
 __device__ __forceinline__ void tensormap_acquire(const CUtensorMap* m) {
@@ -151,7 +143,7 @@ __device__ __forceinline__ void tensormap_acquire(const CUtensorMap* m) {
 // each tile's mass partial is summed in a fixed order by consumer warp 0
 // once the other warps have posted theirs (an mbarrier per stage).
 template <bool kFinal>
-__global__ void __launch_bounds__(lbm::kTmaThreads + 32, 1)
+__global__ void __launch_bounds__(lbm::kTmaBlock, 1)
     lbm_step_tma_batch(const ArgSlot<float>* __restrict__ args,
                        const MemberMaps* __restrict__ maps, int par,
                        const int4* __restrict__ tiles, int ntiles, double frac) {
@@ -404,7 +396,7 @@ template <typename Real, bool kFinal>
 void launch_step_shape(lbm_batch* b, int shape, int par, double frac) {
   if (shape == kTmaShape) {  // FP32 only (set_shape checks)
     const int grid = b->ntiles[shape] < b->num_sms ? b->ntiles[shape] : b->num_sms;
-    lbm_step_tma_batch<kFinal><<<grid, lbm::kTmaThreads + 32, kBTmaSmem, b->stream>>>(
+    lbm_step_tma_batch<kFinal><<<grid, lbm::kTmaBlock, kBTmaSmem, b->stream>>>(
         (const ArgSlot<float>*)b->args[par], b->maps, par, b->tiles[shape], b->ntiles[shape],
         frac);
     return;
@@ -616,7 +608,7 @@ lbm_status lbm_batch_shape_info(int shape, int* tile_w, int* tile_h, int* thread
   const bool tma = shape == kTmaShape;
   if (tile_w) *tile_w = tma ? lbm::kTW : 32;
   if (tile_h) *tile_h = tma ? lbm::kTH : kShapes[shape].by * kShapes[shape].r;
-  if (threads) *threads = tma ? lbm::kTmaThreads + 32 : 32 * kShapes[shape].by;
+  if (threads) *threads = tma ? lbm::kTmaBlock : 32 * kShapes[shape].by;
   if (pipelined) *pipelined = tma ? 1 : 0;
   return LBM_OK;
 }

@@ -1,15 +1,17 @@
 // lbm_tma.cuh -- the FP32 fused step as a persistent, TMA-fed tile pipeline.
 //
-// One CTA per SM walks the lattice in 128 x 8 node tiles (tile t, t + grid,
+// One CTA per SM walks the lattice in 96 x 8 node tiles (tile t, t + grid,
 // ...).  For each tile one cp.async.bulk.tensor 3-D box brings all nine
-// population planes with a one-node halo (136 x 10 x 9 floats), and two more
-// bring the velocity (128 x 8 x 2) and the link words (128 x 8), optionally
-// the rate field; an mbarrier per stage counts the bytes in.  Three stages
-// keep two tiles in flight while the CTA updates the third from shared memory
-// with step_node(), which is shared with the generic kernel, and stores f*
-// with coalesced row writes.  Every wait on an mbarrier has an iteration
-// limit: on expiry the CTA records a status, drains its copies in flight
-// (again with a limit) and returns.
+// population planes with a one-node halo (104 x 10 x 9 floats), and two more
+// bring the velocity (96 x 8 x 2) and the link words (96 x 8), optionally
+// the rate field; an mbarrier per stage counts the bytes in.  Four stages
+// keep three tiles in flight while the CTA's 24 consumer warps update the
+// fourth from shared memory with step_node(), which is shared with the
+// generic kernel, and store f* with coalesced row writes.  (The update is
+// bound by the consumers' instruction latency, so the tile is sized for as
+// many consumer warps as the register file holds.)  Every wait on an
+// mbarrier has an iteration limit: on expiry the CTA records a status,
+// drains its copies in flight (again with a limit) and returns.
 #pragma once
 #include <cuda.h>
 
@@ -17,15 +19,17 @@
 
 namespace lbm {
 
-constexpr int kTW = 128;           // tile width (nodes)
+constexpr int kTW = 96;            // tile width (nodes)
 constexpr int kTH = 8;             // tile height (rows)
 constexpr int kBoxW = kTW + 8;     // halo box width: 4 columns each side (16 B aligned)
 constexpr int kBoxH = kTH + 2;     // halo box height: one row each side
-constexpr int kStages = 3;
-constexpr int kTmaThreads = 512;   // consumer threads: 16 warps (plus one producer warp)
-constexpr int kWarpsPerRow = 16 / kTH;                    // consumer warps sharing a tile row
+constexpr int kStages = 4;
+constexpr int kTmaThreads = 768;   // consumer threads: 24 warps (plus one producer warp)
+constexpr int kTmaBlock = kTmaThreads + 32;
+constexpr int kWarpsPerRow = (kTmaThreads / 32) / kTH;    // consumer warps sharing a tile row
 constexpr int kNodesPerLane = kTW / (32 * kWarpsPerRow);  // nodes of a row per lane
-static_assert(16 % kTH == 0 && kNodesPerLane * 32 * kWarpsPerRow == kTW, "tile mapping");
+static_assert((kTmaThreads / 32) % kTH == 0 && kNodesPerLane * 32 * kWarpsPerRow == kTW,
+              "tile mapping");
 constexpr long long kSpinLimit = 1ll << 24;
 
 constexpr int round128(int b) { return (b + 127) / 128 * 128; }
@@ -86,6 +90,17 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
+// Bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned)
+// from global to this CTA's shared memory; completion counts on `bar`.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes,
+                                          uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
 // Inputs of one node read from the shared-memory tile of its stage.
 struct SmemSrc {
   const float* pop;      // [9][kBoxH][kBoxW]
@@ -118,10 +133,10 @@ struct SmemSrc {
 };
 
 struct TmaMaps {
-  CUtensorMap pop;   // fin: [9][rows][pitch] float, box {136, 10, 9}
-  CUtensorMap vel;   // [2][rows][pitch] float, box {128, 8, 2}
-  CUtensorMap link;  // [rows][pitch] uint32 link words, box {128, 8}
-  CUtensorMap kf;    // [rows][pitch] float, box {128, 8} (valid if a.kf)
+  CUtensorMap pop;   // fin: [9][rows][pitch] float, box {kBoxW, kBoxH, 9}
+  CUtensorMap vel;   // [2][rows][pitch] float, box {kTW, kTH, 2}
+  CUtensorMap link;  // [rows][pitch] uint32 link words, box {kTW, kTH}
+  CUtensorMap kf;    // [rows][pitch] float, box {kTW, kTH} (valid if a.kf)
 };
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -130,17 +145,17 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 
 // Warp-specialised pipeline: warp 0 is the producer (one lane issues the TMA
 // boxes of tile k into stage k % kStages once all consumer warps have
-// released that stage), warps 1..16 are consumers (each updates its half of
-// one tile row and releases the stage with one arrival).  No CTA-wide barrier
-// sits inside the tile loop.
+// released that stage), warps 1..24 are consumers (each updates a third of
+// one tile row and releases the stage with one arrival).  No CTA-wide
+// barrier sits inside the tile loop.
 template <bool kFinal>
-__global__ void __launch_bounds__(kTmaThreads + 32, 1)
+__global__ void __launch_bounds__(kTmaBlock, 1)
     lbm_step_tma(const StepArgs<float> a, const __grid_constant__ TmaMaps maps, int ntx,
                  int nty) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[kStages];
   __shared__ __align__(8) uint64_t empty[kStages];
-  __shared__ double red[kTmaThreads / 32 + 1];
+  __shared__ double red[kTmaBlock / 32];
   __shared__ int abort_flag;
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
@@ -186,7 +201,7 @@ __global__ void __launch_bounds__(kTmaThreads + 32, 1)
     }
   } else {
     // ---- consumers ------------------------------------------------------
-    const int cw = warp - 1;                  // 0..15
+    const int cw = warp - 1;                  // 0 .. kTmaThreads / 32 - 1
     const int r = cw / kWarpsPerRow;          // tile row of this warp
     const int cbase = (cw % kWarpsPerRow) * (32 * kNodesPerLane) + lane;  // first column
     int k = 0;
