@@ -170,6 +170,32 @@ def test_multi_time_step_interpolation(gb, oracle_mod, prec):
     assert lat.diagnostics()["bc_infeasible"] == ref.diag()["bc_infeasible"]
 
 
+@pytest.mark.parametrize("prec", [64, 32])
+def test_time_interpolated_dirichlet_closed_form(gb, prec):
+    """The library on the closed form that pins Eq. "MTS" in the oracle:
+    u = a + b t + (b / 2D)(x - xc)^2 at tau = 1 (exact for the scheme), with
+    west/east data interpolated in time over coarse steps of 5 substeps;
+    FP64 to rounding, FP32 within its bound."""
+    nx, ny, tau, eta = 33, 4, 1.0, 5
+    D = (tau - 0.5) / 3.0
+    a, b, xc = 1.0, 1e-3, 16.0
+    xs = np.arange(nx, dtype=float)
+
+    def exact(x, t):
+        return a + b * t + b / (2 * D) * (x - xc) ** 2
+
+    lat = gb.LBM(nx, ny, tau, edges=(1, 1, 0, 0), precision=prec,
+                 u0=np.tile(exact(xs, 0.0), (ny, 1)))
+    t, worst = 0, 0.0
+    for _ in range(60):
+        ua = inputs.edge_array(nx, ny, W=exact(0.0, t), E=exact(nx - 1.0, t))
+        ub = inputs.edge_array(nx, ny, W=exact(0.0, t + eta), E=exact(nx - 1.0, t + eta))
+        lat.substeps(eta, eta, ua, ub)
+        t += eta
+        worst = max(worst, np.abs(lat.concentration() - exact(xs, t)[None, :]).max())
+    assert worst <= TOL[prec] * exact(0.0, t), worst
+
+
 def test_neumann_flux_and_interface_trace(gb, oracle_mod):
     """Nonzero Neumann data on N and S, Dirichlet on W/E, then the bilinear
     LBM -> FEM trace at random points (Sec. 6.2 (ii))."""

@@ -143,6 +143,47 @@ def test_linear_profile_between_dirichlet_walls(oracle_mod):
     np.testing.assert_allclose(o.u(), np.broadcast_to(exact, (ny, nx)), atol=1e-12)
 
 
+def _quadratic_in_x_linear_in_t(oracle_mod, eta, ncoarse, late=0):
+    """The lattice over coarse steps of eta substeps, its west and east
+    Dirichlet data interpolated in time (Eq. "MTS") between the closed form
+    u = a + b t + (b / 2D) (x - xc)^2 at the coarse step's two ends, taken
+    `late` substeps late; returns the max error after each coarse step."""
+    nx, ny, tau = 33, 4, 1.0
+    D = (tau - 0.5) / 3.0
+    a, b, xc = 1.0, 1e-3, 16.0
+    xs = np.arange(nx, dtype=float)
+
+    def exact(x, t):
+        return a + b * t + b / (2 * D) * (x - xc) ** 2
+
+    o = oracle_mod.LBMOracle(nx, ny, tau, edges=(1, 1, 0, 0),
+                             u0=np.tile(exact(xs, 0.0), (ny, 1)))
+    errs, t = [], 0
+    for _ in range(ncoarse):
+        ua = inputs.edge_array(nx, ny, W=exact(0.0, t + late), E=exact(nx - 1.0, t + late))
+        ub = inputs.edge_array(nx, ny, W=exact(0.0, t + eta + late),
+                               E=exact(nx - 1.0, t + eta + late))
+        o.substeps(eta, eta, ua, ub)
+        t += eta
+        errs.append(np.abs(o.u() - exact(xs, t)[None, :]).max())
+    return np.array(errs)
+
+
+@pytest.mark.parametrize("eta", [1, 5, 7])
+def test_time_interpolated_dirichlet_data_exact_at_tau1(oracle_mod, eta):
+    """Eq. "MTS" pinned: at tau = 1 the collided populations are w_i u, so a
+    step maps u to sum_i w_i u(x - e_i), which equals u + u_xx / 6 for u
+    quadratic in x: exact for u = a + b t + (b / 2D)(x - xc)^2 with
+    D = (tau - 1/2) / 3 = 1/6.  The wet Dirichlet nodes carry their data
+    exactly, so with data interpolated in time over each coarse step the
+    lattice stays on the closed form to rounding at every coarse step; the
+    same data one substep late miss it by b."""
+    errs = _quadratic_in_x_linear_in_t(oracle_mod, eta, 420 // eta)
+    assert errs.max() < 1e-12, errs.max()
+    late = _quadratic_in_x_linear_in_t(oracle_mod, eta, 420 // eta, late=1)
+    assert abs(late[-1] - 1e-3) < 1e-6, late[-1]
+
+
 def test_linear_profile_with_neumann_flux(oracle_mod):
     """Dirichlet c = 2 on the west, Neumann first moment q = -tau g / 3 on the
     east (the flux of the linear profile with slope g): the steady state is
