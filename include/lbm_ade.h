@@ -268,7 +268,9 @@ const char* lbm_batch_last_error(void);
  * boundary (the mesh edge, the edge of switched-off elements) is zero-flux.
  * Nodes are numbered j (nex + 1) + i; nodal vectors are FP64.
  * The linear system is solved on the GPU (Jacobi-preconditioned BiCGSTAB,
- * FP64, to the relative residual tol).  Pointers may be host or device
+ * FP64, to the relative residual tol), starting from the last converged
+ * solution (after lbm_fem_set, the previous Schwarz iterate: a close guess),
+ * or from d^n before the first.  Pointers may be host or device
  * memory; everything runs on `stream`.  Errors: LBM_ERR_ARG (bad parameters or
  * node ids), LBM_ERR_STATE (no convergence / breakdown of the linear solve),
  * LBM_ERR_NOMEM, LBM_ERR_CUDA; the message is in lbm_last_error(). */

@@ -20,7 +20,9 @@
 // solves A x = B d^n (+ prescribed values) by Jacobi-preconditioned
 // BiCGSTAB in FP64 inside one cooperative launch (grid-wide barriers between
 // the phases of an iteration, dot products folded in a fixed order, so the
-// result is deterministic); the host reads the outcome once per step.
+// result is deterministic); the host reads the outcome once per step.  A
+// solve starts from the last converged solution (the previous Schwarz
+// iterate inside Algorithm 1), else from d^n.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -84,6 +86,7 @@ constexpr long long kBarrierSpin = 1ll << 24;
 
 struct Solve {
   const double* A;       // [9][n]
+  const double* invd;    // [n] 1 / diagonal of A (the Jacobi preconditioner)
   const double* B;       // [9][n]
   double* d;             // state: d^n in, d^{n+1} out
   const int* fixed_id;   // -1 free, -2 inactive, >= 0 index into fixed_val
@@ -99,6 +102,7 @@ struct Solve {
   long long n;
   double tol;
   int max_iter;
+  int warm;  // start from w.x (the last converged solution) instead of d^n
 };
 
 // Grid-wide barrier (all blocks are resident: cooperative launch).  Returns
@@ -153,21 +157,48 @@ __device__ __forceinline__ void block_dot2(double v0, double v1, double* part0, 
   }
 }
 
-// Sum of the gridDim.x partials, the same in every block: warp 0 adds a
-// strided share per lane, then a fixed shuffle tree; broadcast to the block.
-__device__ __forceinline__ double grid_fold(const double* part) {
-  __shared__ double r;
-  if (threadIdx.x < 32) {
-    double v = 0.0;
-    for (int k = threadIdx.x; k < (int)gridDim.x; k += 32) v += ((const volatile double*)part)[k];
+// Sums of the gridDim.x partials of two dot products, the same in every
+// block: thread t adds partials t and t + kThreads, each warp folds its
+// threads with a fixed shuffle tree, and every thread adds the warp sums in
+// warp order.  Each thread issues its loads together, so a fold costs one
+// trip to L2 rather than one per partial.  gridDim.x <= kFoldCap (the host
+// clamps the grid).
+constexpr int kFoldCap = 2 * kThreads;
+__device__ __forceinline__ void grid_fold2(const double* pa, const double* pb, double& ra,
+                                           double& rb) {
+  __shared__ double wa[kThreads / 32], wb[kThreads / 32];
+  const int t = threadIdx.x, nb = (int)gridDim.x;
+  // written by other blocks before the last grid barrier: read through L2
+  const double a0 = t < nb ? __ldcg(pa + t) : 0.0;
+  const double a1 = t + kThreads < nb ? __ldcg(pa + t + kThreads) : 0.0;
+  const double b0 = pb && t < nb ? __ldcg(pb + t) : 0.0;
+  const double b1 = pb && t + kThreads < nb ? __ldcg(pb + t + kThreads) : 0.0;
+  double a = a0 + a1, b = b0 + b1;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (threadIdx.x == 0) r = v;
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  if ((t & 31) == 0) {
+    wa[t >> 5] = a;
+    wb[t >> 5] = b;
   }
   __syncthreads();
-  const double out = r;
-  __syncthreads();
-  return out;
+  a = 0.0;
+  b = 0.0;
+#pragma unroll
+  for (int k = 0; k < kThreads / 32; ++k) {
+    a += wa[k];
+    b += wb[k];
+  }
+  ra = a;
+  rb = b;
+  __syncthreads();  // the warp sums may be overwritten by the next fold
+}
+__device__ __forceinline__ double grid_fold(const double* part) {
+  double a, b;
+  grid_fold2(part, nullptr, a, b);
+  return a;
 }
 
 __global__ void __launch_bounds__(kThreads) k_bicgstab(const Solve S) {
@@ -196,7 +227,7 @@ __global__ void __launch_bounds__(kThreads) k_bicgstab(const Solve S) {
       xv = 0.0;
     } else {
       bv = spmv_row(S.B, S.d, i, j, nxn, nyn, n);
-      xv = S.d[p];
+      xv = S.warm ? w.x[p] : S.d[p];
     }
     S.b[p] = bv;
     w.x[p] = xv;
@@ -219,14 +250,14 @@ __global__ void __launch_bounds__(kThreads) k_bicgstab(const Solve S) {
   }
   block_dot2(rr, 0.0, P1, nullptr);
   if (!grid_sync(S.bar, S.status)) return;
-  const double bnorm2 = grid_fold(P0);
-  double rnorm2 = grid_fold(P1);
+  double bnorm2, rnorm2;
+  grid_fold2(P0, P1, bnorm2, rnorm2);
   double rho = rnorm2, alpha = 0.0, omega = 0.0;
   const double tol2 = S.tol * S.tol * bnorm2;
   bool done = rnorm2 <= tol2, breakdown = false;
   int it = 0;
   while (!done && it < S.max_iter) {
-    for (long long p = p0; p < n; p += stride) w.phat[p] = w.p[p] / A[4 * n + p];
+    for (long long p = p0; p < n; p += stride) w.phat[p] = w.p[p] * S.invd[p];
     if (!grid_sync(S.bar, S.status)) return;
     double d0 = 0.0;
     for (long long p = p0; p < n; p += stride) {
@@ -246,7 +277,7 @@ __global__ void __launch_bounds__(kThreads) k_bicgstab(const Solve S) {
     for (long long p = p0; p < n; p += stride) {
       const double sv = w.r[p] - alpha * w.v[p];
       w.s[p] = sv;
-      w.shat[p] = sv / A[4 * n + p];
+      w.shat[p] = sv * S.invd[p];
     }
     if (!grid_sync(S.bar, S.status)) return;
     double ts = 0.0, tt = 0.0;
@@ -259,8 +290,9 @@ __global__ void __launch_bounds__(kThreads) k_bicgstab(const Solve S) {
     }
     block_dot2(ts, tt, P0, P1);
     if (!grid_sync(S.bar, S.status)) return;
-    const double tsum = grid_fold(P1);
-    omega = tsum > 0.0 ? grid_fold(P0) / tsum : 0.0;
+    double tsum, tsv;
+    grid_fold2(P1, P0, tsum, tsv);
+    omega = tsum > 0.0 ? tsv / tsum : 0.0;
     double rh = 0.0;
     rr = 0.0;
     for (long long p = p0; p < n; p += stride) {
@@ -272,8 +304,8 @@ __global__ void __launch_bounds__(kThreads) k_bicgstab(const Solve S) {
     }
     block_dot2(rh, rr, P2, P3);
     if (!grid_sync(S.bar, S.status)) return;
-    const double rho_new = grid_fold(P2);
-    rnorm2 = grid_fold(P3);
+    double rho_new;
+    grid_fold2(P2, P3, rho_new, rnorm2);
     ++it;
     if (rnorm2 <= tol2) {
       done = true;
@@ -328,6 +360,7 @@ struct lbm_fem {
   double* B = nullptr;  // [9][n]
   double* d = nullptr;  // state
   double* b = nullptr;  // right-hand side
+  double* invd = nullptr;  // 1 / diagonal of A
   Vec w{};
   double* vecs = nullptr;   // storage of w
   int* fixed_id = nullptr;  // per node: index into the prescribed values, -1 free, -2 inactive
@@ -342,13 +375,19 @@ struct lbm_fem {
   size_t scratch_n = 0;
   int last_iters = 0;
   double last_resid = 0.0;
+  // w.x holds the last converged solution: the next solve starts from it.
+  // Within a Schwarz step (Algorithm 1) every iteration after the first
+  // solves the same system with nearby Dirichlet data, so the previous
+  // iterate is a far better start than d^n; in plain time stepping it is
+  // d^n itself.  The answer is the same to the solve's tolerance.
+  bool warm = false;
 };
 
 namespace {
 
 void fem_free(lbm_fem* f) {
   void* ptrs[] = {f->A, f->B, f->d, f->b, f->vecs, f->fixed_id, f->fixed_val, f->part,
-                  f->sc, f->iters, f->scratch, f->bar, f->status};
+                  f->sc, f->iters, f->scratch, f->bar, f->status, f->invd};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete f;
@@ -435,7 +474,11 @@ lbm_status fem_setup(lbm_fem* f, const uint8_t* elem_active, const int* dir_node
         B[k * n + q] = 0.0;
       }
     }
+  std::vector<double> invd(n);
+  for (long long q = 0; q < n; ++q) invd[q] = 1.0 / A[4 * n + q];
   FCK(cudaMemcpyAsync(f->A, A.data(), 9 * n * sizeof(double), cudaMemcpyHostToDevice, f->stream));
+  FCK(cudaMemcpyAsync(f->invd, invd.data(), n * sizeof(double), cudaMemcpyHostToDevice,
+                      f->stream));
   FCK(cudaMemcpyAsync(f->B, B.data(), 9 * n * sizeof(double), cudaMemcpyHostToDevice, f->stream));
   FCK(cudaMemcpyAsync(f->fixed_id, fid.data(), n * sizeof(int), cudaMemcpyHostToDevice, f->stream));
   std::vector<double> d(n, 0.0);
@@ -483,6 +526,7 @@ lbm_status lbm_fem_init(lbm_fem** out, const lbm_fem_params* p, const uint8_t* e
   al((void**)&f->B, 9 * n * sizeof(double));
   al((void**)&f->d, n * sizeof(double));
   al((void**)&f->b, n * sizeof(double));
+  al((void**)&f->invd, n * sizeof(double));
   al((void**)&f->vecs, 9 * n * sizeof(double));
   al((void**)&f->fixed_id, n * sizeof(int));
   al((void**)&f->fixed_val, (n_dir > 0 ? n_dir : 1) * sizeof(double));
@@ -498,7 +542,8 @@ lbm_status lbm_fem_init(lbm_fem** out, const lbm_fem_params* p, const uint8_t* e
       return ctx_fail(LBM_ERR_CUDA, "lbm_fem_init: the device has no cooperative launch");
     }
     const long long need = (n + kThreads - 1) / kThreads;
-    const long long cap = (long long)sms * (per_sm < 2 ? per_sm : 2);
+    long long cap = (long long)sms * (per_sm < 2 ? per_sm : 2);
+    if (cap > kFoldCap) cap = kFoldCap;  // partials one fold can take
     f->grid = (int)(need < cap ? need : cap);
   }
   al((void**)&f->part, 4 * (size_t)(f->grid > 0 ? f->grid : 1) * sizeof(double));
@@ -531,6 +576,7 @@ lbm_status lbm_fem_step(lbm_fem* f, const double* dir_values) {
     FCK(cudaMemcpyAsync(f->fixed_val, dir_values, f->n_dir * sizeof(double), cudaMemcpyDefault, s));
   Solve S;
   S.A = f->A;
+  S.invd = f->invd;
   S.B = f->B;
   S.d = f->d;
   S.fixed_id = f->fixed_id;
@@ -547,6 +593,7 @@ lbm_status lbm_fem_step(lbm_fem* f, const double* dir_values) {
   S.n = f->n;
   S.tol = f->p.tol;
   S.max_iter = f->p.max_iter;
+  S.warm = f->warm ? 1 : 0;
   void* args[] = {&S};
   FCK(cudaLaunchCooperativeKernel((const void*)k_bicgstab, dim3(f->grid), dim3(kThreads), args, 0, s));
   struct {
@@ -559,6 +606,7 @@ lbm_status lbm_fem_step(lbm_fem* f, const double* dir_values) {
   FCK(cudaStreamSynchronize(s));
   f->last_iters = h.iters;
   f->last_resid = h.sc.bnorm2 > 0 ? std::sqrt(h.sc.rnorm2 / h.sc.bnorm2) : std::sqrt(h.sc.rnorm2);
+  f->warm = !h.status && h.sc.done;
   if (h.status) {
     cudaMemsetAsync(f->status, 0, sizeof(int), s);
     cudaMemsetAsync(f->bar, 0, 2 * sizeof(unsigned), s);
