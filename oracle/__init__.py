@@ -27,6 +27,7 @@ _lib = None
 
 EDGE_PERIODIC, EDGE_DIRICHLET, EDGE_NEUMANN = 0, 1, 2
 REACT_NONE, REACT_SURFACE, REACT_BULK = 0, 1, 2
+WALLS = {"bounce": 0, "maxent": 1}  # pore walls: halfway bounce-back or zero-flux max-entropy
 
 # D2Q9 velocities and weights, typed here for the tests' own use (this list
 # is not shared with the CUDA library, which carries its own copy).
@@ -79,6 +80,7 @@ def _load():
         lib.or_lbm_adjoint.argtypes = [P, I, I, P, P, P, P, P, P, P, P]
         lib.or_maxent_neumann.restype = I
         lib.or_maxent_neumann.argtypes = [P, P, D, D, D, P, P]
+        lib.or_lbm_set_wall_mode.argtypes = [P, I]
         _lib = lib
         return lib
 
@@ -104,12 +106,16 @@ class LBMOracle:
     velocity in lattice units, ``tau`` relaxation time, ``edges`` the kinds of
     the W, E, S, N sides, ``u0`` the initial concentration, and the reaction
     (``react_mode``, ``k``/``k_field``, ``dissolution``, ``mineral``).
+    ``walls`` treats the pore walls by halfway bounce-back ("bounce") or as
+    zero-flux boundaries of the maximum-entropy kind (Sec. 4.1.1 (b), "maxent").
     """
 
     def __init__(self, nx, ny, tau, edges=(0, 0, 0, 0), solid=None, vel=None,
                  u0=None, react_mode=REACT_NONE, k=0.0, k_field=None,
-                 dissolution=False, mineral=None):
+                 dissolution=False, mineral=None, walls="bounce"):
         lib = _load()
+        if walls not in WALLS:
+            raise ValueError(f"walls must be one of {sorted(WALLS)}")
         if (edges[0] == EDGE_PERIODIC) != (edges[1] == EDGE_PERIODIC):
             raise ValueError("W and E must both be periodic or both not")
         if (edges[2] == EDGE_PERIODIC) != (edges[3] == EDGE_PERIODIC):
@@ -130,6 +136,7 @@ class LBMOracle:
         if not self._h:
             raise MemoryError("oracle allocation failed")
         self._lib = lib
+        lib.or_lbm_set_wall_mode(self._h, WALLS[walls])
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -181,6 +188,7 @@ class LBMOracle:
         if rc != 0:
             raise ValueError({-1: "the adjoint needs a fixed mask (dissolution off)",
                               -2: "two Neumann sides meet at a corner",
+                              -4: "the adjoint covers bounce-back walls only",
                               -3: "out of memory"}.get(rc, f"error {rc}"))
         return dict(J=J.value, k=gk, ua=ga, ub=gb, q=gq)
 

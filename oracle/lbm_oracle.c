@@ -38,7 +38,13 @@
  *    mineral mass reaches zero or less after a step becomes fluid with all
  *    populations zero;
  *  - Dirichlet data inside a run of eta substeps are interpolated linearly in
- *    time: substep j uses (1 - j/eta) a + (j/eta) b (Eq. "MTS").
+ *    time: substep j uses (1 - j/eta) a + (j/eta) b (Eq. "MTS");
+ *  - pore walls take halfway bounce-back by default; as the option of the
+ *    paper's own kind (Sec. 4.1.1 (b) with zero flux) their normal is the
+ *    lattice-weighted direction to the node's solid neighbours, unknowns
+ *    tangent to it take bounce-back, a cancelling sum (one-node channel)
+ *    takes bounce-back throughout, and nodes on an open lattice side keep
+ *    bounce-back at their solid links (their edge condition sets the rest).
  *
  * Memory: the oracle owns copies of everything it is given.  Arrays are
  * row-major [ny][nx]; populations are [9][ny][nx].
@@ -67,6 +73,7 @@ static int reverse_of(int i) {
 enum { EDGE_PERIODIC = 0, EDGE_DIRICHLET = 1, EDGE_NEUMANN = 2 };
 enum { SIDE_W = 0, SIDE_E = 1, SIDE_S = 2, SIDE_N = 3 };
 enum { REACT_NONE = 0, REACT_SURFACE = 1, REACT_BULK = 2 };
+enum { WALL_BOUNCE = 0, WALL_MAXENT = 1 };
 
 typedef struct {
   int nx, ny;
@@ -75,6 +82,7 @@ typedef struct {
   int react_mode;
   double k_scalar;
   int dissolution;
+  int wall_mode;   /* WALL_BOUNCE or WALL_MAXENT (pore walls)      */
   double *k;       /* [ny][nx] rate, used where reactive          */
   double *vel;     /* [2][ny][nx]                                  */
   uint8_t *solid;  /* [ny][nx] 1 = solid                           */
@@ -353,6 +361,15 @@ static void dissolve_gather(or_lbm *o) {
   (void)N;
 }
 
+/* True at nodes on a side that is not periodic (they have pulls from outside
+   the lattice). */
+static int on_open_side(const or_lbm *o, int x, int y) {
+  return (x == 0 && o->edge[SIDE_W] != EDGE_PERIODIC) ||
+         (x == o->nx - 1 && o->edge[SIDE_E] != EDGE_PERIODIC) ||
+         (y == 0 && o->edge[SIDE_S] != EDGE_PERIODIC) ||
+         (y == o->ny - 1 && o->edge[SIDE_N] != EDGE_PERIODIC);
+}
+
 /* Push streaming with halfway bounce-back at solid neighbours. */
 static void stream(or_lbm *o) {
   size_t N = nn(o);
@@ -371,6 +388,11 @@ static void stream(or_lbm *o) {
         if (!locate(o, x + CX[i], y + CY[i], &tx, &ty)) continue; /* leaves */
         size_t t = at(o, tx, ty);
         if (o->solid[t]) {
+          /* halfway bounce-back; with max-entropy walls the population that
+             would come back is left unknown for apply_walls, except at nodes
+             on a non-periodic lattice side (their edge condition settles
+             them, with bounce-back at their solid links) */
+          if (o->wall_mode == WALL_MAXENT && !on_open_side(o, x, y)) continue;
           int r = reverse_of(i);
           o->fnew[(size_t)r * N + n] = v;
           o->known[(size_t)r * N + n] = 1;
@@ -442,6 +464,55 @@ static void apply_bc(or_lbm *o, int j, int eta, const double *ua,
     }
 }
 
+/* Pore walls as zero-flux boundaries of the maximum-entropy kind, Sec. 4.1.1
+ * (b) with q = 0 (the paper's reading of a wall as a bath in equilibrium, as
+ * against bounce-back).  At a fluid node off the open lattice sides the
+ * unknowns are the populations whose source x - e_i is solid.  The outward
+ * normal is the lattice-weighted direction to the solid neighbours,
+ * n = sum over solid neighbours x + e_k of w_k e_k, normalised; unknowns with
+ * e_i . n >= 0 (tangent to the wall or pointing into it) take halfway
+ * bounce-back, as at a corner of two Neumann sides, and the rest follow from
+ * the Lagrange multiplier of the flux constraint.  Where the weighted
+ * directions cancel (a one-node channel) every unknown takes bounce-back. */
+static void apply_walls(or_lbm *o) {
+  size_t N = nn(o);
+  for (int y = 0; y < o->ny; ++y)
+    for (int x = 0; x < o->nx; ++x) {
+      size_t n = at(o, x, y);
+      if (o->solid[n] || on_open_side(o, x, y)) continue;
+      double f[NQ], nxn = 0.0, nyn = 0.0;
+      int unk[NQ], nunk = 0;
+      for (int i = 0; i < NQ; ++i) {
+        f[i] = o->fnew[(size_t)i * N + n];
+        unk[i] = !o->known[(size_t)i * N + n];
+        nunk += unk[i];
+        if (unk[i]) { /* source x - e_i is solid: the solid neighbour lies along -e_i */
+          nxn -= WT[i] * CX[i];
+          nyn -= WT[i] * CY[i];
+        }
+      }
+      if (!nunk) continue;
+      double len = sqrt(nxn * nxn + nyn * nyn);
+      if (len < 1e-12) {
+        nxn = nyn = 0.0;
+      } else {
+        nxn /= len;
+        nyn /= len;
+      }
+      for (int i = 0; i < NQ; ++i)
+        if (unk[i] && CX[i] * nxn + CY[i] * nyn >= 0.0) {
+          f[i] = o->fpost[(size_t)reverse_of(i) * N + n];
+          unk[i] = 0;
+        }
+      int fail = 0;
+      o->bc_infeasible += or_maxent_neumann(f, unk, nxn, nyn, 0.0, &o->newton_iters, &fail);
+      o->newton_fail += fail;
+      for (int i = 0; i < NQ; ++i) o->fnew[(size_t)i * N + n] = f[i];
+    }
+}
+
+void or_lbm_set_wall_mode(or_lbm *o, int mode) { o->wall_mode = mode; }
+
 /* Run n substeps j = 1..n of a coarse step split eta ways.  ua, ub: Dirichlet
  * data at the start and the end of the coarse step, q: Neumann data, each in
  * the edge layout [W: ny][E: ny][S: nx][N: nx] (NULL means zero). */
@@ -455,6 +526,7 @@ void or_lbm_substeps(or_lbm *o, int n, int eta, const double *ua,
     /* stream, then boundary conditions */
     stream(o);
     apply_bc(o, j, eta, ua, ub, q);
+    if (o->wall_mode == WALL_MAXENT) apply_walls(o);
     memcpy(o->f, o->fnew, NQ * N * sizeof(double));
     /* dissolution: solid nodes whose mineral is used up become fluid */
     if (o->dissolution && o->react_mode == REACT_SURFACE)
@@ -575,6 +647,7 @@ int or_lbm_adjoint(or_lbm *o, int nsteps, int eta, const double *ua,
                    double *grad_k, double *grad_ua, double *grad_ub,
                    double *grad_q) {
   if (o->dissolution) return -1;
+  if (o->wall_mode != WALL_BOUNCE) return -4; /* the transpose covers bounce-back walls */
   const int np_x = o->edge[SIDE_W] != EDGE_PERIODIC;
   const int np_y = o->edge[SIDE_S] != EDGE_PERIODIC;
   if (np_x && np_y) {
@@ -748,6 +821,7 @@ or_lbm *or_lbm_clone(const or_lbm *o) {
   or_lbm *c = or_lbm_new(o->nx, o->ny, o->edge, o->tau, o->react_mode, o->k_scalar,
                          o->k, o->dissolution, o->solid, o->vel, o->mineral, NULL);
   if (!c) return NULL;
+  c->wall_mode = o->wall_mode;
   size_t N = nn(o);
   memcpy(c->f, o->f, NQ * N * sizeof(double));
   memcpy(c->u, o->u, N * sizeof(double));
