@@ -216,6 +216,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--kernel-steps", type=int, default=1000)
+    ap.add_argument("--walls-steps", type=int, default=500,
+                    help="steps of the leg with maximum-entropy pore walls (0: skip)")
     ap.add_argument("--adjoint-steps", type=int, default=5000)
     ap.add_argument("--hybrid-coarse", type=int, default=200)
     ap.add_argument("--batch-steps", type=int, default=2000)
@@ -337,6 +339,34 @@ def main():
                 "alu_roofline": {"bound": "alu", "achieved": f64_gflops, "peak": FP64_PEAK_GFLOPS,
                                  "unit": "GFLOP/s", "frac": f64_gflops / FP64_PEAK_GFLOPS,
                                  "peak_kind": "nominal FP64 rate of the part"}}
+
+    # ---- the same workload with maximum-entropy pore walls ---------------------
+    walls = None
+    if args.walls_steps > 0:
+        latw = LBM(n, n, case["tau"], precision=32, walls="maxent", **kw)
+        latw.substeps(3, 1, ud, ud, q)
+        barrier()
+        ev0.record(stream)
+        latw.substeps(args.walls_steps, 1, ud, ud, q)
+        ev1.record(stream)
+        ev1.synchronize()
+        msw = max_over_ranks(ev0.elapsed_time(ev1))
+        latw.kernel_timing(True)
+        latw.substeps(min(args.kernel_steps, args.walls_steps), 1, ud, ud, q)
+        sw_ms, sw_n, _, _ = latw.kernel_times()
+        dw = latw.diagnostics()
+        latw.close()
+        del latw
+        torch.cuda.empty_cache()
+        bw = BYTES_FLUID[32] * (nodes - dw["n_solid"]) + BYTES_SOLID * dw["n_solid"]
+        aw = bw / (sw_ms / max(sw_n, 1) / 1e3) / 1e9
+        walls = {"value": world * nodes * args.walls_steps / (msw / 1e3) / 1e9,
+                 "unit": "GLUPS", "steps": args.walls_steps,
+                 "ms_per_step": msw / args.walls_steps,
+                 "kernel_ms_per_launch": sw_ms / max(sw_n, 1),
+                 "bc_infeasible": dw["bc_infeasible"],
+                 "roofline": {"bound": "hbm", "achieved": aw, "peak": peak, "unit": "GB/s",
+                              "frac": aw / peak}}
 
     # ---- end to end through the public API with host buffers -----------------
     e2e = None
@@ -506,7 +536,7 @@ def main():
                          "kernel_ms_per_launch": per_launch_ms,
                          "kernel_timing_steps": args.kernel_steps,
                          "dissolve_ms_per_launch": diss_ms / max(diss_n, 1)},
-            "fp64": fp64, "batched": batched, "adjoint": adjoint, "hybrid": hybrid,
+            "fp64": fp64, "maxent_walls": walls, "batched": batched, "adjoint": adjoint, "hybrid": hybrid,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,

@@ -67,6 +67,12 @@ typedef enum {
   LBM_REACT_BULK = 2     /* sink at every fluid node */
 } lbm_react_mode;
 
+typedef enum {
+  LBM_WALL_BOUNCE = 0, /* pore walls: halfway bounce-back (the default) */
+  LBM_WALL_MAXENT = 1  /* pore walls as zero-flux boundaries of the maximum-entropy
+                          kind, Sec. 4.1.1 (b) (see lbm_set_wall_mode) */
+} lbm_wall_mode;
+
 enum { LBM_SIDE_W = 0, LBM_SIDE_E = 1, LBM_SIDE_S = 2, LBM_SIDE_N = 3 };
 
 typedef struct {
@@ -142,6 +148,20 @@ lbm_status lbm_get_mineral(lbm_ctx* c, double* out);
 /* Reductions over the lattice in FP64, in a fixed order (deterministic). */
 lbm_status lbm_diagnostics(lbm_ctx* c, lbm_diag* out);
 
+/* Treatment of the pore walls from the next step on (Sec. 4.1.1 (b) and the
+ * comparison of wall treatments after it).  LBM_WALL_BOUNCE: halfway
+ * bounce-back.  LBM_WALL_MAXENT: at a fluid node beside solid ones (and off
+ * the non-periodic lattice sides, whose nodes keep bounce-back at their solid
+ * links) the populations whose source is solid follow from the zero-flux
+ * maximum-entropy condition with the lattice-weighted normal to the solid
+ * neighbours, n = -sum w_i e_i over those directions (normalised); unknowns
+ * with e_i.n >= 0 keep bounce-back, as does a node where the sum cancels.
+ * Solves with no root set their unknowns to zero and count in
+ * lbm_diag.bc_infeasible.  The adjoint (lbm_adjoint) covers bounce-back walls
+ * only and returns LBM_ERR_STATE otherwise.  Errors: LBM_ERR_ARG for an
+ * unknown mode. */
+lbm_status lbm_set_wall_mode(lbm_ctx* c, int mode);
+
 /* Schwarz rollback (Algorithm 1 restarts every sub-iteration from the state
  * at the start of the coarse step): lbm_state_bytes gives the size of a
  * state blob; lbm_save writes the full state into a caller-owned buffer of
@@ -207,7 +227,8 @@ lbm_status lbm_set_rate_field(lbm_ctx* c, const double* k_field);
  * per step: about three forward passes, with ceil(n / stride) + 3 population
  * sets and `stride` concentration planes of device memory, kept in the
  * context for the next call.
- * Errors: LBM_ERR_STATE if dissolution is on (a flip is not differentiable);
+ * Errors: LBM_ERR_STATE if dissolution is on (a flip is not differentiable)
+ * or the pore walls are of the maximum-entropy kind (not affine in f);
  * LBM_ERR_ARG for n < 1 or eta < 1, or two Neumann sides that meet at a
  * corner (that root is not affine); LBM_ERR_NOMEM; LBM_ERR_TIMEOUT as for
  * lbm_substeps. */

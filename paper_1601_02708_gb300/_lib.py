@@ -74,6 +74,7 @@ def load():
             "lbm_get_solid": [P, P],
             "lbm_get_mineral": [P, P],
             "lbm_diagnostics": [P, ctypes.POINTER(Diag)],
+            "lbm_set_wall_mode": [P, I],
             "lbm_state_bytes": [P, ctypes.POINTER(S)],
             "lbm_save": [P, P, S],
             "lbm_restore": [P, P, S],

@@ -387,6 +387,10 @@ lbm_status check_adjoint(const lbm_ctx* c) {
     return ctx_fail(LBM_ERR_STATE,
                     "lbm_adjoint: needs a fixed mask (the context dissolves; a flip is not "
                     "differentiable)");
+  if (c->wall_mode != LBM_WALL_BOUNCE)
+    return ctx_fail(LBM_ERR_STATE,
+                    "lbm_adjoint: covers bounce-back pore walls only (the maximum-entropy "
+                    "wall solve is not affine in f)");
   const int* e = c->p.edge;
   if (e[0] != LBM_EDGE_PERIODIC && e[2] != LBM_EDGE_PERIODIC)
     for (int xs = 0; xs < 2; ++xs)

@@ -299,42 +299,35 @@ lbm_status sync_mineral(lbm_ctx* c) {
   return LBM_OK;
 }
 
-template <typename Real>
-lbm_status launch_step_impl(lbm_ctx* c, const lbm::StepArgs<Real>& a, bool final_step);
-
-template <>
-lbm_status launch_step_impl<double>(lbm_ctx* c, const lbm::StepArgs<double>& a,
-                                    bool final_step) {
-  if (final_step)
-    lbm::lbm_step<double, true><<<c->grid, c->block, 0, c->stream>>>(a);
-  else
-    lbm::lbm_step<double, false><<<c->grid, c->block, 0, c->stream>>>(a);
-  if (final_step) c->nparts = (int)(c->grid.x * c->grid.y);
-  CK(cudaGetLastError());
-  return LBM_OK;
-}
-
-template <>
-lbm_status launch_step_impl<float>(lbm_ctx* c, const lbm::StepArgs<float>& a,
-                                   bool final_step) {
-  if (c->use_tma) {
+// The step kernels are built with and without the maximum-entropy wall
+// code; a context whose pore walls bounce back runs the kernels without it.
+template <typename Real, bool kWalls>
+lbm_status launch_step_kernels(lbm_ctx* c, const lbm::StepArgs<Real>& a, bool final_step) {
+  if (sizeof(Real) == 4 && c->use_tma) {
     const lbm::TmaMaps& m = c->maps[c->cur];
+    const auto& af = reinterpret_cast<const lbm::StepArgs<float>&>(a);
     if (final_step)
-      lbm::lbm_step_tma<true><<<c->tma_grid, lbm::kTmaBlock, lbm::kTmaSmem, c->stream>>>(
-          a, m, c->ntx, c->nty);
+      lbm::lbm_step_tma<true, kWalls><<<c->tma_grid, lbm::kTmaBlock, lbm::kTmaSmem, c->stream>>>(
+          af, m, c->ntx, c->nty);
     else
-      lbm::lbm_step_tma<false><<<c->tma_grid, lbm::kTmaBlock, lbm::kTmaSmem, c->stream>>>(
-          a, m, c->ntx, c->nty);
+      lbm::lbm_step_tma<false, kWalls><<<c->tma_grid, lbm::kTmaBlock, lbm::kTmaSmem, c->stream>>>(
+          af, m, c->ntx, c->nty);
     if (final_step) c->nparts = c->tma_grid;
   } else {
     if (final_step)
-      lbm::lbm_step<float, true><<<c->grid, c->block, 0, c->stream>>>(a);
+      lbm::lbm_step<Real, true, kWalls><<<c->grid, c->block, 0, c->stream>>>(a);
     else
-      lbm::lbm_step<float, false><<<c->grid, c->block, 0, c->stream>>>(a);
+      lbm::lbm_step<Real, false, kWalls><<<c->grid, c->block, 0, c->stream>>>(a);
     if (final_step) c->nparts = (int)(c->grid.x * c->grid.y);
   }
   CK(cudaGetLastError());
   return LBM_OK;
+}
+
+template <typename Real>
+lbm_status launch_step_impl(lbm_ctx* c, const lbm::StepArgs<Real>& a, bool final_step) {
+  return c->wall_mode == LBM_WALL_BOUNCE ? launch_step_kernels<Real, false>(c, a, final_step)
+                                         : launch_step_kernels<Real, true>(c, a, final_step);
 }
 
 template <typename Real>
@@ -442,6 +435,10 @@ lbm_status setup_tma(lbm_ctx* c) {
   CK(cudaFuncSetAttribute(lbm::lbm_step_tma<true>,
                           cudaFuncAttributeMaxDynamicSharedMemorySize, lbm::kTmaSmem));
   CK(cudaFuncSetAttribute(lbm::lbm_step_tma<false>,
+                          cudaFuncAttributeMaxDynamicSharedMemorySize, lbm::kTmaSmem));
+  CK(cudaFuncSetAttribute(lbm::lbm_step_tma<true, true>,
+                          cudaFuncAttributeMaxDynamicSharedMemorySize, lbm::kTmaSmem));
+  CK(cudaFuncSetAttribute(lbm::lbm_step_tma<false, true>,
                           cudaFuncAttributeMaxDynamicSharedMemorySize, lbm::kTmaSmem));
   c->ntx = (c->p.nx + lbm::kTW - 1) / lbm::kTW;
   c->nty = (c->p.ny + lbm::kTH - 1) / lbm::kTH;
@@ -868,9 +865,17 @@ lbm_status lbm_diagnostics(lbm_ctx* c, lbm_diag* out) {
   out->mass = h.mass;
   out->outlet_J = h.J;
   out->steps = c->steps;
-  out->bc_infeasible = h.infeasible;
+  out->bc_infeasible = h.infeasible + ctr[2];
   out->flips = ctr[0];
   out->n_solid = ctr[1] - ctr[0];
+  return LBM_OK;
+}
+
+lbm_status lbm_set_wall_mode(lbm_ctx* c, int mode) {
+  TRY(check_ctx(c));
+  if (mode != LBM_WALL_BOUNCE && mode != LBM_WALL_MAXENT)
+    return fail(LBM_ERR_ARG, "lbm_set_wall_mode: mode must be LBM_WALL_BOUNCE or LBM_WALL_MAXENT");
+  c->wall_mode = mode;
   return LBM_OK;
 }
 

@@ -66,7 +66,7 @@ struct alignas(16) ArgSlot {
   lbm::StepArgs<Real> a;
 };
 
-template <typename Real, bool kFinal, int kBY, int kR>
+template <typename Real, bool kFinal, int kBY, int kR, bool kWalls = false>
 __global__ void __launch_bounds__(32 * kBY)
     lbm_step_batch(const ArgSlot<Real>* __restrict__ args, const int4* __restrict__ tiles,
                    int ntiles, double frac) {
@@ -98,9 +98,9 @@ __global__ void __launch_bounds__(32 * kBY)
         const long long n = (long long)(y + lbm::kYO) * a.pitch + (x + lbm::kXO);
         lbm::GlobalSrc<Real> src{a, n};
         if (lbm::group_is_interior(td.y, y, a.nx, a.ny))
-          my_u += lbm::step_node<Real, kFinal, false>(a, src, x, y, n, frac);
+          my_u += lbm::step_node<Real, kFinal, false, kWalls>(a, src, x, y, n, frac);
         else
-          my_u += lbm::step_node<Real, kFinal, true>(a, src, x, y, n, frac);
+          my_u += lbm::step_node<Real, kFinal, true, kWalls>(a, src, x, y, n, frac);
       }
     }
     if (kFinal) {
@@ -142,7 +142,7 @@ __device__ __forceinline__ void tensormap_acquire(const CUtensorMap* m) {
 // take member, origin and arguments from the stage.  On the final substep
 // each tile's mass partial is summed in a fixed order by consumer warp 0
 // once the other warps have posted theirs (an mbarrier per stage).
-template <bool kFinal>
+template <bool kFinal, bool kWalls = false>
 __global__ void __launch_bounds__(lbm::kTmaBlock, 1)
     lbm_step_tma_batch(const ArgSlot<float>* __restrict__ args,
                        const MemberMaps* __restrict__ maps, int par,
@@ -233,9 +233,9 @@ __global__ void __launch_bounds__(lbm::kTmaBlock, 1)
         src.c = xl + 4;
         const long long n = (long long)(y + kYO) * a.pitch + (x + kXO);
         if (group_is_interior(x - lane, y, a.nx, a.ny))
-          tile_u += step_node<float, kFinal, false>(a, src, x, y, n, frac);
+          tile_u += step_node<float, kFinal, false, kWalls>(a, src, x, y, n, frac);
         else if (x < a.nx && y < a.ny)
-          tile_u += step_node<float, kFinal, true>(a, src, x, y, n, frac);
+          tile_u += step_node<float, kFinal, true, kWalls>(a, src, x, y, n, frac);
       }
       if (kFinal) {
 #pragma unroll
@@ -334,6 +334,7 @@ struct lbm_batch {
   int2* bmap = nullptr;
   int* nblk = nullptr;
   int dblocks = 0;
+  bool walls = false;  // a member had maximum-entropy pore walls when the batch was made
   std::map<std::tuple<int, int, int, int>, cudaGraphExec_t> graphs;  // (n, eta, parity, shape)
 };
 
@@ -389,14 +390,18 @@ lbm_status upload_maps(lbm_batch* b) {
                            kBTmaSmem));
   BCK(cudaFuncSetAttribute(lbm_step_tma_batch<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            kBTmaSmem));
+  BCK(cudaFuncSetAttribute(lbm_step_tma_batch<true, true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, kBTmaSmem));
+  BCK(cudaFuncSetAttribute(lbm_step_tma_batch<false, true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, kBTmaSmem));
   return LBM_OK;
 }
 
-template <typename Real, bool kFinal>
+template <typename Real, bool kFinal, bool kWalls>
 void launch_step_shape(lbm_batch* b, int shape, int par, double frac) {
   if (shape == kTmaShape) {  // FP32 only (set_shape checks)
     const int grid = b->ntiles[shape] < b->num_sms ? b->ntiles[shape] : b->num_sms;
-    lbm_step_tma_batch<kFinal><<<grid, lbm::kTmaBlock, kBTmaSmem, b->stream>>>(
+    lbm_step_tma_batch<kFinal, kWalls><<<grid, lbm::kTmaBlock, kBTmaSmem, b->stream>>>(
         (const ArgSlot<float>*)b->args[par], b->maps, par, b->tiles[shape], b->ntiles[shape],
         frac);
     return;
@@ -408,17 +413,17 @@ void launch_step_shape(lbm_batch* b, int shape, int par, double frac) {
   const int4* tl = b->tiles[shape];
   const int nt = b->ntiles[shape];
   if (sh.by == 8 && sh.r == 1)
-    lbm_step_batch<Real, kFinal, 8, 1><<<grid, block, 0, b->stream>>>(a, tl, nt, frac);
+    lbm_step_batch<Real, kFinal, 8, 1, kWalls><<<grid, block, 0, b->stream>>>(a, tl, nt, frac);
   else if (sh.by == 16 && sh.r == 1)
-    lbm_step_batch<Real, kFinal, 16, 1><<<grid, block, 0, b->stream>>>(a, tl, nt, frac);
+    lbm_step_batch<Real, kFinal, 16, 1, kWalls><<<grid, block, 0, b->stream>>>(a, tl, nt, frac);
   else if (sh.by == 8 && sh.r == 2)
-    lbm_step_batch<Real, kFinal, 8, 2><<<grid, block, 0, b->stream>>>(a, tl, nt, frac);
+    lbm_step_batch<Real, kFinal, 8, 2, kWalls><<<grid, block, 0, b->stream>>>(a, tl, nt, frac);
   else if (sh.by == 4 && sh.r == 2)
-    lbm_step_batch<Real, kFinal, 4, 2><<<grid, block, 0, b->stream>>>(a, tl, nt, frac);
+    lbm_step_batch<Real, kFinal, 4, 2, kWalls><<<grid, block, 0, b->stream>>>(a, tl, nt, frac);
   else if (sh.by == 8 && sh.r == 4)
-    lbm_step_batch<Real, kFinal, 8, 4><<<grid, block, 0, b->stream>>>(a, tl, nt, frac);
+    lbm_step_batch<Real, kFinal, 8, 4, kWalls><<<grid, block, 0, b->stream>>>(a, tl, nt, frac);
   else
-    lbm_step_batch<Real, kFinal, 4, 4><<<grid, block, 0, b->stream>>>(a, tl, nt, frac);
+    lbm_step_batch<Real, kFinal, 4, 4, kWalls><<<grid, block, 0, b->stream>>>(a, tl, nt, frac);
 }
 
 // Enqueue n steps starting at buffer parity par (no capture logic here).
@@ -426,8 +431,13 @@ template <typename Real>
 void enqueue_steps(lbm_batch* b, int n, int eta, int par, int shape) {
   for (int j = 1; j <= n; ++j) {
     const double frac = (double)j / (double)eta;
-    if (j == n) launch_step_shape<Real, true>(b, shape, par, frac);
-    else launch_step_shape<Real, false>(b, shape, par, frac);
+    if (b->walls) {  // some member has maximum-entropy pore walls
+      if (j == n) launch_step_shape<Real, true, true>(b, shape, par, frac);
+      else launch_step_shape<Real, false, true>(b, shape, par, frac);
+    } else {
+      if (j == n) launch_step_shape<Real, true, false>(b, shape, par, frac);
+      else launch_step_shape<Real, false, false>(b, shape, par, frac);
+    }
     par ^= 1;
     if (b->dblocks > 0)
       lbm_dissolve_batch<Real><<<b->dblocks, lbm::kDThreads, 0, b->stream>>>(
@@ -496,6 +506,7 @@ lbm_status lbm_batch_create(lbm_batch** out, int n, lbm_ctx* const* members) {
   b->esize = (int)members[0]->esize;
   b->stream = members[0]->stream;
   b->num_sms = members[0]->num_sms;
+  for (int i = 0; i < n; ++i) b->walls = b->walls || members[i]->wall_mode != LBM_WALL_BOUNCE;
   lbm_status st = b->esize == 8 ? upload_args<double>(b) : upload_args<float>(b);
   if (st == LBM_OK) st = upload_maps(b);
   if (st != LBM_OK) {

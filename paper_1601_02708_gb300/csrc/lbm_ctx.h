@@ -37,7 +37,9 @@ struct lbm_ctx {
   int* flip_count = nullptr;      // [0] count, [1] done counter, [2] surface list length
   int* slist = nullptr;           // dissolution surface list (padded node indices)
   double* smin = nullptr;         // mineral of the listed nodes
-  long long* counters = nullptr;  // [0] flips total, [1] solid count at init
+  long long* counters = nullptr;  // [0] flips total, [1] solid count at init,
+                                  // [2] wall solves without a root
+  int wall_mode = 0;              // LBM_WALL_BOUNCE or LBM_WALL_MAXENT
   int* status = nullptr;          // device error word
   DiagDev* diag = nullptr;
   void* scratch = nullptr;  // staging for host outputs
@@ -102,6 +104,8 @@ inline lbm::StepArgs<Real> step_args(lbm_ctx* c, double frac) {
   a.partial = c->partial;
   a.status = c->status;
   a.bc_root = nullptr;
+  a.wall_infeasible = c->counters + 2;
+  a.wall_maxent = c->wall_mode == LBM_WALL_MAXENT;
   a.plane = c->plane;
   a.nx = c->p.nx;
   a.ny = c->p.ny;

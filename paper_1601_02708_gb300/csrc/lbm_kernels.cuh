@@ -45,6 +45,8 @@ struct StepArgs {
   int* __restrict__ status;            // device error word (0 = fine)
   unsigned char* __restrict__ bc_root;  // per edge slot: 1 where the Neumann root
                                         // set the unknowns this step (or null)
+  long long* __restrict__ wall_infeasible;  // count of wall solves without a root
+  int wall_maxent;  // pore walls of the maximum-entropy kind (else bounce-back)
   long long plane;  // pitch * rows
   int nx, ny, pitch;
   int per_x, per_y;
@@ -171,7 +173,9 @@ struct GlobalSrc {
 // kEdge false: the caller guarantees the node is at least one node away
 // from every side, so no pull leaves the lattice, no ghost image exists and
 // the node is not on the outlet; the boundary code is then compiled out.
-template <typename Real, bool kFinal, bool kEdge, class Src>
+// kWalls: the kernel may meet maximum-entropy pore walls (a.wall_maxent);
+// kernels built without it carry no wall code.
+template <typename Real, bool kFinal, bool kEdge, bool kWalls = false, class Src>
 __device__ __forceinline__ double step_node(const StepArgs<Real>& a, const Src& src,
                                             int x, int y, long long n, double frac) {
   const uint32_t w = src.word();
@@ -204,6 +208,11 @@ __device__ __forceinline__ double step_node(const StepArgs<Real>& a, const Src& 
   f[0] = src.own(0);
 #pragma unroll
   for (int i = 1; i < 9; ++i) f[i] = src.pull_or_bounce(i, w & up_bit(kUpSolidShift, i));
+  // pore walls of the maximum-entropy kind, at nodes off the open lattice
+  // sides (those keep bounce-back at their solid links)
+  if (kWalls && a.wall_maxent && (w & 0xFFu) && !(w & (0xFFu << kUpOutShift)))
+    if (maxent_wall(f, (w & 0xFFu) << 1))
+      atomicAdd(reinterpret_cast<unsigned long long*>(a.wall_infeasible), 1ull);
   if (kEdge) {
     const unsigned unknown = ((w >> kUpOutShift) & 0xFFu) << 1;  // bit i: direction i
     if (unknown) {
@@ -277,7 +286,7 @@ __device__ __forceinline__ bool group_is_interior(int xs, int y, int nx, int ny)
 
 // Generic step: one thread per node, inputs from global memory.  Used in
 // FP64 mode; the FP32 path runs the TMA kernel instead.
-template <typename Real, bool kFinal>
+template <typename Real, bool kFinal, bool kWalls = false>
 __global__ void __launch_bounds__(kBX * kBY, sizeof(Real) == 4 ? 4 : 4)
     lbm_step(const StepArgs<Real> a) {
   __shared__ double red[kBX * kBY / 32];
@@ -288,9 +297,9 @@ __global__ void __launch_bounds__(kBX * kBY, sizeof(Real) == 4 ? 4 : 4)
     const long long n = (long long)(y + kYO) * a.pitch + (x + kXO);
     GlobalSrc<Real> src{a, n};
     if (group_is_interior(blockIdx.x * kBX, y, a.nx, a.ny))
-      my_u = step_node<Real, kFinal, false>(a, src, x, y, n, a.frac);
+      my_u = step_node<Real, kFinal, false, kWalls>(a, src, x, y, n, a.frac);
     else
-      my_u = step_node<Real, kFinal, true>(a, src, x, y, n, a.frac);
+      my_u = step_node<Real, kFinal, true, kWalls>(a, src, x, y, n, a.frac);
   }
   if (kFinal) {
     const double s = block_sum(my_u, red);

@@ -264,4 +264,89 @@ __device__ __forceinline__ void edge_kind(const int (&edge)[4], int x, int y, in
   }
 }
 
+// Pore wall of the maximum-entropy kind: Sec. 4.1.1 (b) with zero flux, the
+// option beside halfway bounce-back.  `solid` has bit i set where the source
+// x - e_i of pull i is solid; on entry f holds the halfway bounce-back value
+// in those directions.  The outward normal is the lattice-weighted direction
+// to the solid neighbours, n = -sum_{i in solid} w_i e_i, normalised (where it
+// cancels, as in a one-node channel, bounce-back stays throughout; which
+// unknowns are tangent is decided on 36 n, an integer vector).  Unknowns
+// with e_i.n >= 0 keep bounce-back; the others become
+// w_i exp(-1 - gamma e_i.n) with gamma making sum_i f_i e_i.n zero.  With
+// a_i = e_i.n < 0 the flux of those unknowns is -L(gamma),
+// L(gamma) = sum |a_i| w_i exp(-1 + gamma |a_i|), so the root solves
+// log L(gamma) = log(-R), R = -sum_{others} a_j f_j; log L is convex and
+// increasing with slope between the smallest and largest |a_i|, so Newton's
+// method converges from any start (in one step when every |a_i| is equal, as
+// on a flat wall).  Returns true if R > 0 (no root: those unknowns are set to
+// zero, the gamma -> -infinity limit).
+template <typename Real>
+__device__ bool maxent_wall(Real (&f)[9], unsigned solid) {
+  // the normal scaled by 36 (the weights are 4/36 and 1/36): integers, so
+  // which unknowns are tangent to it, and whether it cancels, is exact
+  int mx = 0, my = 0;
+#pragma unroll
+  for (int i = 1; i < 9; ++i)
+    if (solid & (1u << i)) {
+      const int w36 = (cx_of(i) != 0 && cy_of(i) != 0) ? 1 : 4;
+      mx -= w36 * cx_of(i);
+      my -= w36 * cy_of(i);
+    }
+  if (mx == 0 && my == 0) return false;
+  const Real inv = (Real)1 / sqrt((Real)(mx * mx + my * my));
+  const Real nx = (Real)mx * inv, ny = (Real)my * inv;
+  Real a[9], R = (Real)0, s1 = (Real)0, s2 = (Real)0;
+  unsigned neg = 0u;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    a[i] = (Real)cx_of(i) * nx + (Real)cy_of(i) * ny;
+    if (((solid >> i) & 1u) && cx_of(i) * mx + cy_of(i) * my < 0) {
+      neg |= 1u << i;
+      s1 -= (Real)w_of(i) * a[i];
+      s2 += (Real)w_of(i) * a[i] * a[i];
+    } else {
+      R -= a[i] * f[i];
+    }
+  }
+  if (!neg) return false;
+  if (!(R < (Real)0)) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+      if (neg & (1u << i)) f[i] = (Real)0;
+    return R > (Real)0;
+  }
+  if (sizeof(Real) == 4 && -R < (Real)1e-30) {
+    // far below FP32's normal range the exponentials would underflow: the
+    // flux-conserving split w_i (-R) / sum w |a| meets the constraint exactly
+    // and differs from the maximum-entropy values by less than 1e-30
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+      if (neg & (1u << i)) f[i] = (Real)w_of(i) * (-R / s1);
+    return false;
+  }
+  constexpr int kIters = sizeof(Real) == 8 ? 60 : 24;
+  const Real tol = sizeof(Real) == 8 ? (Real)1e-15 : (Real)1e-7;
+  const Real logR = log(-R);
+  // start: the root if every |a_i| were their weighted mean s2 / s1
+  Real g = (logR - log(s1) + (Real)1) * (s1 / s2);
+  for (int it = 0; it < kIters; ++it) {
+    Real L = (Real)0, dL = (Real)0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+      if (neg & (1u << i)) {
+        const Real e = (Real)w_of(i) * exp(g * -a[i] - (Real)1);
+        L -= a[i] * e;
+        dL += a[i] * a[i] * e;
+      }
+    if (!(dL > (Real)0)) break;
+    const Real step = (log(L) - logR) * (L / dL);
+    g -= step;
+    if (fabs(step) <= tol * ((Real)1 + fabs(g))) break;
+  }
+#pragma unroll
+  for (int i = 0; i < 9; ++i)
+    if (neg & (1u << i)) f[i] = (Real)w_of(i) * exp(g * -a[i] - (Real)1);
+  return false;
+}
+
 }  // namespace lbm

@@ -148,7 +148,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // released that stage), warps 1..24 are consumers (each updates a third of
 // one tile row and releases the stage with one arrival).  No CTA-wide
 // barrier sits inside the tile loop.
-template <bool kFinal>
+template <bool kFinal, bool kWalls = false>
 __global__ void __launch_bounds__(kTmaBlock, 1)
     lbm_step_tma(const StepArgs<float> a, const __grid_constant__ TmaMaps maps, int ntx,
                  int nty) {
@@ -223,9 +223,9 @@ __global__ void __launch_bounds__(kTmaBlock, 1)
         src.c = xl + 4;
         const long long n = (long long)(y + kYO) * a.pitch + (x + kXO);
         if (group_is_interior(x - lane, y, a.nx, a.ny))
-          my_u += step_node<float, kFinal, false>(a, src, x, y, n, a.frac);
+          my_u += step_node<float, kFinal, false, kWalls>(a, src, x, y, n, a.frac);
         else if (x < a.nx && y < a.ny)
-          my_u += step_node<float, kFinal, true>(a, src, x, y, n, a.frac);
+          my_u += step_node<float, kFinal, true, kWalls>(a, src, x, y, n, a.frac);
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[s]);

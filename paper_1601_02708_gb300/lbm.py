@@ -16,6 +16,7 @@ from ._lib import Diag, LBMError, Params, check
 
 PERIODIC, DIRICHLET, NEUMANN = 0, 1, 2
 REACT_NONE, REACT_SURFACE, REACT_BULK = 0, 1, 2
+WALLS = {"bounce": 0, "maxent": 1}  # lbm_wall_mode: halfway bounce-back, zero-flux max-entropy
 
 
 def _torch():
@@ -89,12 +90,14 @@ class LBM:
     [2, ny, nx], initial concentration, and the first-order reaction
     (``react_mode``, ``k`` or ``k_field``, ``dissolution``, ``mineral``).
     ``precision`` 32 runs FP32 populations with FP64 boundary solves and
-    sums; 64 runs FP64 throughout.
+    sums; 64 runs FP64 throughout.  ``walls`` treats the pore walls by
+    halfway bounce-back ("bounce") or as zero-flux boundaries of the
+    maximum-entropy kind (Sec. 4.1.1 (b), "maxent").
     """
 
     def __init__(self, nx, ny, tau, edges=(PERIODIC,) * 4, precision=32,
                  solid=None, vel=None, u0=None, react_mode=REACT_NONE, k=0.0,
-                 k_field=None, dissolution=False, mineral=None, stream=None):
+                 k_field=None, dissolution=False, mineral=None, stream=None, walls="bounce"):
         self._lib = _lib.load()
         self.nx, self.ny = int(nx), int(ny)
         self.precision = int(precision)
@@ -119,6 +122,15 @@ class LBM:
         h = ctypes.c_void_p()
         check(self._lib.lbm_init(ctypes.byref(h), ctypes.byref(p), *args, stream))
         self._h = h
+        self.set_walls(walls)
+
+    def set_walls(self, walls):
+        """Pore walls from the next step on: "bounce" (halfway bounce-back) or
+        "maxent" (zero-flux maximum-entropy condition, lbm_set_wall_mode)."""
+        if walls not in WALLS:
+            raise ValueError(f"walls must be one of {sorted(WALLS)}")
+        check(self._lib.lbm_set_wall_mode(self.handle, WALLS[walls]))
+        self.walls = walls
 
     # -- lifetime --------------------------------------------------------------
     def close(self):
