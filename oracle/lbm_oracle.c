@@ -480,27 +480,29 @@ static void apply_walls(or_lbm *o) {
     for (int x = 0; x < o->nx; ++x) {
       size_t n = at(o, x, y);
       if (o->solid[n] || on_open_side(o, x, y)) continue;
-      double f[NQ], nxn = 0.0, nyn = 0.0;
-      int unk[NQ], nunk = 0;
+      double f[NQ];
+      /* the normal scaled by 36 (the weights are 4/36 and 1/36): integers, so
+         which unknowns are tangent to it, and whether it cancels, is exact */
+      int unk[NQ], nunk = 0, mx = 0, my = 0;
       for (int i = 0; i < NQ; ++i) {
         f[i] = o->fnew[(size_t)i * N + n];
         unk[i] = !o->known[(size_t)i * N + n];
         nunk += unk[i];
         if (unk[i]) { /* source x - e_i is solid: the solid neighbour lies along -e_i */
-          nxn -= WT[i] * CX[i];
-          nyn -= WT[i] * CY[i];
+          int w36 = (CX[i] != 0 && CY[i] != 0) ? 1 : 4;
+          mx -= w36 * CX[i];
+          my -= w36 * CY[i];
         }
       }
       if (!nunk) continue;
-      double len = sqrt(nxn * nxn + nyn * nyn);
-      if (len < 1e-12) {
-        nxn = nyn = 0.0;
-      } else {
-        nxn /= len;
-        nyn /= len;
+      double nxn = 0.0, nyn = 0.0;
+      if (mx != 0 || my != 0) {
+        double len = sqrt((double)(mx * mx + my * my));
+        nxn = mx / len;
+        nyn = my / len;
       }
       for (int i = 0; i < NQ; ++i)
-        if (unk[i] && CX[i] * nxn + CY[i] * nyn >= 0.0) {
+        if (unk[i] && CX[i] * mx + CY[i] * my >= 0) {
           f[i] = o->fpost[(size_t)reverse_of(i) * N + n];
           unk[i] = 0;
         }
