@@ -216,6 +216,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--kernel-steps", type=int, default=1000)
+    ap.add_argument("--bimolecular-steps", type=int, default=300,
+                    help="steps of the two-invariant leg (instantaneous A + 2B -> C; 0: skip)")
     ap.add_argument("--walls-steps", type=int, default=500,
                     help="steps of the leg with maximum-entropy pore walls (0: skip)")
     ap.add_argument("--adjoint-steps", type=int, default=5000)
@@ -367,6 +369,51 @@ def main():
                  "bc_infeasible": dw["bc_infeasible"],
                  "roofline": {"bound": "hbm", "achieved": aw, "peak": peak, "unit": "GB/s",
                               "frac": aw / peak}}
+
+    # ---- instantaneous bimolecular reaction: two invariants, then species ------
+    bimol = None
+    if args.bimolecular_steps > 0:
+        from paper_1601_02708_gb300 import Bimolecular, species_from_invariants
+        fluid = kw["solid"] == 0
+        uA0 = np.zeros((n, n))
+        uB0 = np.where(fluid, 0.5, 0.0)  # B resident; A enters at the inlet
+        coeffs = (1.0, 2.0, 1.0)
+        bm = Bimolecular(n, n, case["tau"], coeffs, uA0, uB0, precision=32,
+                         edges=kw["edges"], solid=kw["solid"], vel=kw["vel"])
+        a_in = ud  # alpha = u_A + u_C at the inlet: the inlet value of A
+        b_in = torch.zeros_like(ud)
+        bm.substeps(3, 1, (a_in, a_in), (b_in, b_in))
+        barrier()
+        ev0.record(stream)
+        bm.substeps(args.bimolecular_steps, 1, (a_in, a_in), (b_in, b_in))
+        ev1.record(stream)
+        ev1.synchronize()
+        msb = max_over_ranks(ev0.elapsed_time(ev1))
+        al = torch.empty((n, n), dtype=torch.float64, device="cuda")
+        be = torch.empty_like(al)
+        bm.alpha.concentration(out=al)
+        bm.beta.concentration(out=be)
+        spc = tuple(torch.empty_like(al) for _ in range(3))
+        species_from_invariants(al, be, coeffs, out=spc)  # warm
+        torch.cuda.synchronize()
+        reps = 20  # back to back, so the host's share of each call overlaps the GPU's
+        ev0.record(stream)
+        for _ in range(reps):
+            species_from_invariants(al, be, coeffs, out=spc)
+        ev1.record(stream)
+        ev1.synchronize()
+        epi_ms = ev0.elapsed_time(ev1) / reps
+        uA, uB, uC = spc
+        produced = float(uC.sum())
+        bm.close()
+        del bm, al, be, uA, uB, uC
+        torch.cuda.empty_cache()
+        bimol = {"value": world * 2 * nodes * args.bimolecular_steps / (msb / 1e3) / 1e9,
+                 "unit": "GLUPS (both invariants)", "steps": args.bimolecular_steps,
+                 "ms_per_step": msb / args.bimolecular_steps,
+                 "species_ms": epi_ms, "species_gbs": 5 * 8 * nodes / (epi_ms / 1e3) / 1e9,
+                 "sum_uC": produced,
+                 "reaction": "A + 2B -> C, instantaneous; A enters at the inlet, B resident"}
 
     # ---- end to end through the public API with host buffers -----------------
     e2e = None
@@ -536,7 +583,7 @@ def main():
                          "kernel_ms_per_launch": per_launch_ms,
                          "kernel_timing_steps": args.kernel_steps,
                          "dissolve_ms_per_launch": diss_ms / max(diss_n, 1)},
-            "fp64": fp64, "maxent_walls": walls, "batched": batched, "adjoint": adjoint, "hybrid": hybrid,
+            "fp64": fp64, "maxent_walls": walls, "bimolecular": bimol, "batched": batched, "adjoint": adjoint, "hybrid": hybrid,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,

@@ -162,6 +162,26 @@ lbm_status lbm_diagnostics(lbm_ctx* c, lbm_diag* out);
  * unknown mode. */
 lbm_status lbm_set_wall_mode(lbm_ctx* c, int mode);
 
+/* Instantaneous bimolecular reaction n_A A + n_B B -> n_C C (Sec. 7.2): the
+ * invariants alpha = u_A + (n_A / n_C) u_C and beta = u_B + (n_B / n_C) u_C
+ * carry no reaction (two lattices transport them like any concentration),
+ * and the species follow node by node:
+ *   u_A = max(alpha - (n_A / n_B) beta, 0),
+ *   u_B = (n_B / n_A) max((n_A / n_B) beta - alpha, 0),
+ *   u_C = (n_C / n_A) (alpha - u_A).
+ * Arrays of n FP64 values, host or device memory (host arrays are staged
+ * and the call returns once the results are written; with device arrays it
+ * is asynchronous on `stream`).  Each operation is rounded on its own (no
+ * fused multiply-add).  Errors: LBM_ERR_ARG (n < 0, a coefficient not finite
+ * and positive, a NULL array), LBM_ERR_NOMEM, LBM_ERR_CUDA. */
+lbm_status lbm_species_from_invariants(long long n, double nA, double nB, double nC,
+                                       const double* alpha, const double* beta, double* uA,
+                                       double* uB, double* uC, void* stream);
+/* The invariants of given species concentrations (initial data). */
+lbm_status lbm_invariants_from_species(long long n, double nA, double nB, double nC,
+                                       const double* uA, const double* uB, const double* uC,
+                                       double* alpha, double* beta, void* stream);
+
 /* Schwarz rollback (Algorithm 1 restarts every sub-iteration from the state
  * at the start of the coarse step): lbm_state_bytes gives the size of a
  * state blob; lbm_save writes the full state into a caller-owned buffer of
