@@ -147,6 +147,12 @@ lbm_status lbm_get_mineral(lbm_ctx* c, double* out);
 
 /* Reductions over the lattice in FP64, in a fixed order (deterministic). */
 lbm_status lbm_diagnostics(lbm_ctx* c, lbm_diag* out);
+/* The smallest stored (post-collision) population over the fluid nodes: the
+ * check that the populations stay non-negative (Sec. 4.1, Eq. "NN_Cond", and
+ * the maximum-entropy boundary data).  +infinity without fluid nodes.  Waits
+ * for the context's stream.  Errors: LBM_ERR_ARG (NULL out), LBM_ERR_NOMEM,
+ * LBM_ERR_CUDA. */
+lbm_status lbm_min_population(lbm_ctx* c, double* out);
 
 /* Treatment of the pore walls from the next step on (Sec. 4.1.1 (b) and the
  * comparison of wall treatments after it).  LBM_WALL_BOUNCE: halfway

@@ -75,6 +75,7 @@ def load():
             "lbm_get_mineral": [P, P],
             "lbm_diagnostics": [P, ctypes.POINTER(Diag)],
             "lbm_set_wall_mode": [P, I],
+            "lbm_min_population": [P, ctypes.POINTER(D)],
             "lbm_species_from_invariants": [ctypes.c_longlong, D, D, D, P, P, P, P, P, P],
             "lbm_invariants_from_species": [ctypes.c_longlong, D, D, D, P, P, P, P, P, P],
             "lbm_state_bytes": [P, ctypes.POINTER(S)],

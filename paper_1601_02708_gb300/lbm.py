@@ -234,6 +234,12 @@ class LBM:
             self.handle, _out_ptr(out, kind, self.nx * self.ny), int(precision)))
         return out
 
+    def min_population(self):
+        """Smallest stored population over the fluid nodes (FP64)."""
+        v = ctypes.c_double()
+        check(self._lib.lbm_min_population(self.handle, ctypes.byref(v)))
+        return v.value
+
     def populations(self, out=None):
         """Stored post-collision populations [9, ny, nx] (FP64)."""
         if out is None:

@@ -358,3 +358,29 @@ def test_fp32_bound_over_ten_thousand_steps(gb, oracle_mod, dissolution):
         assert np.array_equal(lat.solid(), ref.solid())
     if dissolution:
         assert ref.diag()["flips"] > 1000
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_min_population(gb, oracle_mod, prec):
+    """The smallest stored population over the fluid nodes against the
+    oracle's post-collision populations; non-negative at tau >= 1 with
+    feasible data (Eq. "NN_Cond"), negative ones appear at tau < 1."""
+    for tau, nonneg in ((1.2, True), (0.55, False)):
+        nx, ny = 70, 41
+        kw = _porous(nx, ny, seed=5)
+        kw["u0"] = np.where(kw["solid"] != 0, 0.0, np.random.default_rng(3).uniform(0, 1, (ny, nx)))
+        ud = inputs.edge_array(nx, ny, W=1.0)
+        ref = oracle_mod.LBMOracle(nx, ny, tau, **kw)
+        lat = gb.LBM(nx, ny, tau, precision=prec, **kw)
+        ref.substeps(40, 1, ud, ud)
+        lat.substeps(40, 1, ud, ud)
+        fluid = lat.solid() == 0
+        want = ref.fpost()[:, fluid].min()
+        got = lat.min_population()
+        assert got == lat.populations()[:, fluid].min()
+        scale = np.abs(ref.fpost()).max()
+        assert abs(got - want) <= TOL[prec] * scale
+        if nonneg:
+            assert got >= -TOL[prec] * scale
+        else:
+            assert got < -1e-3  # the oracle's smallest is -5.4e-3 here
