@@ -52,3 +52,15 @@ def test_product_path_has_no_oracle_dependency():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "lbm_oracle" not in text, f
+
+
+def test_bimolecular_refuses_reaction_arguments():
+    """The invariants carry no reaction: a sink or dissolution is refused
+    before any lattice is made (host logic, no GPU needed)."""
+    import numpy as np
+    import pytest
+    from paper_1601_02708_gb300 import Bimolecular
+    z = np.zeros((4, 5))
+    for kw in ({"k": 1e-3}, {"dissolution": True}, {"react_mode": 1}, {"u0": z}):
+        with pytest.raises(ValueError):
+            Bimolecular(5, 4, 0.8, (1, 2, 1), z, z, **kw)
