@@ -164,8 +164,9 @@ lbm_status lbm_min_population(lbm_ctx* c, double* out);
  * with e_i.n >= 0 keep bounce-back, as does a node where the sum cancels.
  * Solves with no root set their unknowns to zero and count in
  * lbm_diag.bc_infeasible.  The adjoint (lbm_adjoint) covers bounce-back walls
- * only and returns LBM_ERR_STATE otherwise.  Errors: LBM_ERR_ARG for an
- * unknown mode. */
+ * only and returns LBM_ERR_STATE otherwise.  A batch (lbm_batch_create) takes
+ * its members' wall modes when it is created; set them before.  Errors:
+ * LBM_ERR_ARG for an unknown mode. */
 lbm_status lbm_set_wall_mode(lbm_ctx* c, int mode);
 
 /* Instantaneous bimolecular reaction n_A A + n_B B -> n_C C (Sec. 7.2): the
