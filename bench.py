@@ -90,28 +90,88 @@ def measured_peak_gbs():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """SM clocks and clock-event (throttle) reasons of the benchmark's GPU,
+    sampled during the timed region.  Reads NVML through ctypes every
+    millisecond on a thread (so even a few-millisecond region gets samples);
+    without NVML it falls back to nvidia-smi every 200 ms.  Reads only: no
+    setting of the GPU is changed."""
 
+    # NVML clock-event reason bits
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index):
-        self.gpu = gpu_index
+    def __init__(self, cuda_index):
+        self.cuda_index = cuda_index
+        self.samples = []  # (sm_mhz, reason bits)
+        self.sm_max = None
         self.proc = None
+        self.source = None
+
+    def _uuid(self):
+        try:
+            import torch
+            u = torch.cuda.get_device_properties(self.cuda_index).uuid
+            return "GPU-" + str(u)
+        except Exception:
+            return None
+
+    def _start_nvml(self):
+        import ctypes
+        import threading
+        nv = ctypes.CDLL("libnvidia-ml.so.1")
+        if nv.nvmlInit_v2() != 0:
+            return False
+        h = ctypes.c_void_p()
+        uuid = self._uuid()
+        if uuid is None or nv.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(h)) != 0:
+            nv.nvmlShutdown()
+            return False
+        mx = ctypes.c_uint()
+        if nv.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0:  # NVML_CLOCK_SM
+            self.sm_max = float(mx.value)
+        reasons_fn = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            nv.nvmlDeviceGetCurrentClocksThrottleReasons
+        self._stop = threading.Event()
+
+        def loop():
+            mhz, bits = ctypes.c_uint(), ctypes.c_ulonglong()
+            while not self._stop.is_set():
+                if nv.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(mhz)) == 0 and \
+                        reasons_fn(h, ctypes.byref(bits)) == 0:
+                    self.samples.append((float(mhz.value), int(bits.value)))
+                self._stop.wait(0.001)
+
+        self._nv = nv
+        self._thread = threading.Thread(target=loop, daemon=True)
+        self._thread.start()
+        self.source = "nvml, 1 ms"
+        return True
 
     def __enter__(self):
         try:
+            if self._start_nvml():
+                return self
+        except (OSError, AttributeError):
+            pass
+        try:
+            ident = self._uuid() or str(self.cuda_index)
             self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                ["nvidia-smi", f"--id={ident}", f"--query-gpu={self.FIELDS}",
                  "--format=csv,noheader,nounits", "-lms", "200"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.source = "nvidia-smi, 200 ms"
         except OSError:
             self.proc = None
         return self
 
     def __exit__(self, *exc):
-        self.lines = []
+        if self.source and self.source.startswith("nvml"):
+            self._stop.set()
+            self._thread.join(timeout=2)
+            self._nv.nvmlShutdown()
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -119,25 +179,33 @@ class ClockSampler:
             except subprocess.TimeoutExpired:
                 self.proc.kill()
                 out, _ = self.proc.communicate()
-            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                     "sw_power_cap"]
+            bits = {v: k for k, v in self.REASONS.items()}
+            for ln in out.splitlines():
+                parts = [p.strip() for p in ln.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    mhz = float(parts[1])
+                    self.sm_max = float(parts[2])
+                except ValueError:
+                    continue
+                r = 0
+                for name, val in zip(names, parts[5:9]):
+                    if val.lower() in ("active", "1"):
+                        r |= bits[name]
+                self.samples.append((mhz, r))
 
     def summary(self):
-        sm, smax, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in getattr(self, "lines", []):
-            parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                smax = float(parts[2])
-            except ValueError:
-                continue
-            for name, val in zip(names, parts[5:9]):
-                if val.lower() in ("active", "1"):
+        sm = [m for m, _ in self.samples]
+        reasons = set()
+        for _, r in self.samples:
+            for bit, name in self.REASONS.items():
+                if r & bit:
                     reasons.add(name)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": self.sm_max,
+                "reasons": sorted(reasons), "samples": len(sm), "source": self.source}
 
 
 def workload(n):
@@ -149,6 +217,40 @@ def workload(n):
 def lattice_kwargs(case):
     return {k: case[k] for k in ("edges", "solid", "vel", "u0", "react_mode", "k",
                                  "dissolution", "mineral")}
+
+
+def cpu_model():
+    """The host CPU's model string (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu part")):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def oracle_rate_one_thread(steps, crop):
+    """Oracle node-steps per second on one thread: a child process with
+    OMP_NUM_THREADS=1 (the in-process oracle keeps the threads it started
+    with).  Returns (seconds, nodes)."""
+    code = ("import sys, json; sys.path.insert(0, %r); import bench; "
+            "from paper_1601_02708_gb300 import inputs; "
+            "c = inputs.porous_case(64, 64, seed=2); c['tau'] = 0.7; "
+            "dt, n, _ = bench.run_oracle(c, %d, crop=%d); print(json.dumps([dt, n]))"
+            % (ROOT, steps, crop))
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                       timeout=600)
+    dt, n = json.loads(r.stdout.strip().splitlines()[-1])
+    return dt, n
 
 
 def run_oracle(case, steps, crop=None):
@@ -264,8 +366,24 @@ def main():
     stream = torch.cuda.current_stream()
 
     # ---- FP32 fused step: the headline ------------------------------------
-    lat = LBM(n, n, case["tau"], precision=32, **kw)
-    lat.substeps(args.warmup, 1, ud, ud, q)
+    # one GPU: the 4096 x 4096 lattice; N GPUs: one lattice of 4096 x 4096N
+    # nodes split into row slabs, one 4096 x 4096 slab per rank, the one-row
+    # halo moved by NCCL point-to-point operations between the two halves of
+    # every step (weak scaling: the work per GPU stays fixed)
+    if world > 1:
+        from paper_1601_02708_gb300 import inputs as _inputs
+        from paper_1601_02708_gb300.partition import SlabLattice
+        whole = _inputs.porous_case(n, n * world, seed=2)
+        lat = SlabLattice(n, n * world, whole["tau"], rank=rank, world=world, precision=32,
+                          **lattice_kwargs(whole))
+        ud_w, q_w = dev(whole["u_dir"]), dev(whole["q_neu"])
+        lat.substeps(args.warmup, 1, ud_w, ud_w, q_w)
+        ud, q = ud_w, q_w
+        timed = lat.slabs[0]
+    else:
+        lat = LBM(n, n, case["tau"], precision=32, **kw)
+        lat.substeps(args.warmup, 1, ud, ud, q)
+        timed = lat
     barrier()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -280,16 +398,17 @@ def main():
     launches = 2 * args.steps  # one step and one dissolution launch per step
     # per-kernel durations from CUDA events around every launch, on a
     # separate stretch of steps (the events add small gaps between launches)
-    lat.kernel_timing(True)
+    timed.kernel_timing(True)
     lat.substeps(args.kernel_steps, 1, ud, ud, q)
-    step_ms, step_n, diss_ms, diss_n = lat.kernel_times()
-    lat.kernel_timing(False)
-    diag = lat.diagnostics()
+    step_ms, step_n, diss_ms, diss_n = timed.kernel_times()
+    timed.kernel_timing(False)
+    diag = timed.diagnostics()  # this rank's lattice (or slab): n x n nodes
     n_solid = diag["n_solid"]
     n_fluid = nodes - n_solid
     lat.close()
-    del lat
+    del lat, timed
     torch.cuda.empty_cache()
+    ud, q = dev(case["u_dir"]), dev(case["q_neu"])
 
     value = world * nodes * args.steps / (ms / 1e3) / 1e9
     peak, peak_kind = measured_peak_gbs()
@@ -343,32 +462,38 @@ def main():
                                  "peak_kind": "nominal FP64 rate of the part"}}
 
     # ---- the same workload with maximum-entropy pore walls ---------------------
+    # both precisions of the wall solve: the Lagrange multiplier by Newton's
+    # method in FP64 ("maxent") and in FP32 ("maxent_lattice")
     walls = None
     if args.walls_steps > 0:
-        latw = LBM(n, n, case["tau"], precision=32, walls="maxent", **kw)
-        latw.substeps(3, 1, ud, ud, q)
-        barrier()
-        ev0.record(stream)
-        latw.substeps(args.walls_steps, 1, ud, ud, q)
-        ev1.record(stream)
-        ev1.synchronize()
-        msw = max_over_ranks(ev0.elapsed_time(ev1))
-        latw.kernel_timing(True)
-        latw.substeps(min(args.kernel_steps, args.walls_steps), 1, ud, ud, q)
-        sw_ms, sw_n, _, _ = latw.kernel_times()
-        dw = latw.diagnostics()
-        latw.close()
-        del latw
-        torch.cuda.empty_cache()
-        bw = BYTES_FLUID[32] * (nodes - dw["n_solid"]) + BYTES_SOLID * dw["n_solid"]
-        aw = bw / (sw_ms / max(sw_n, 1) / 1e3) / 1e9
-        walls = {"value": world * nodes * args.walls_steps / (msw / 1e3) / 1e9,
-                 "unit": "GLUPS", "steps": args.walls_steps,
-                 "ms_per_step": msw / args.walls_steps,
-                 "kernel_ms_per_launch": sw_ms / max(sw_n, 1),
-                 "bc_infeasible": dw["bc_infeasible"],
-                 "roofline": {"bound": "hbm", "achieved": aw, "peak": peak, "unit": "GB/s",
-                              "frac": aw / peak}}
+        walls = {}
+        for mode in ("maxent", "maxent_lattice"):
+            latw = LBM(n, n, case["tau"], precision=32, walls=mode, **kw)
+            latw.substeps(3, 1, ud, ud, q)
+            barrier()
+            ev0.record(stream)
+            latw.substeps(args.walls_steps, 1, ud, ud, q)
+            ev1.record(stream)
+            ev1.synchronize()
+            msw = max_over_ranks(ev0.elapsed_time(ev1))
+            latw.kernel_timing(True)
+            latw.substeps(min(args.kernel_steps, args.walls_steps), 1, ud, ud, q)
+            sw_ms, sw_n, _, _ = latw.kernel_times()
+            dw = latw.diagnostics()
+            latw.close()
+            del latw
+            torch.cuda.empty_cache()
+            bw = BYTES_FLUID[32] * (nodes - dw["n_solid"]) + BYTES_SOLID * dw["n_solid"]
+            aw = bw / (sw_ms / max(sw_n, 1) / 1e3) / 1e9
+            walls[mode] = {
+                "value": world * nodes * args.walls_steps / (msw / 1e3) / 1e9,
+                "unit": "GLUPS", "steps": args.walls_steps,
+                "newton_precision": "f64" if mode == "maxent" else "f32",
+                "ms_per_step": msw / args.walls_steps,
+                "kernel_ms_per_launch": sw_ms / max(sw_n, 1),
+                "bc_infeasible": dw["bc_infeasible"], "newton_fail": dw["newton_fail"],
+                "roofline": {"bound": "hbm", "achieved": aw, "peak": peak, "unit": "GB/s",
+                             "frac": aw / peak}}
 
     # ---- instantaneous bimolecular reaction: two invariants, then species ------
     bimol = None
@@ -486,10 +611,14 @@ def main():
         ud4, q4 = dev(c4["u_dir"]), dev(c4["q_neu"])
         start = lat4.save()
         na = args.adjoint_steps
-        lat4.adjoint(na, 1, ud4, ud4, q4)  # warm-up; sizes the checkpoint buffers
-        lat4.restore(start)
-        lat4.substeps(na, 1, ud4, ud4, q4)
-        lat4.restore(start)
+        # two warm-up calls of each path: the first sizes the checkpoint
+        # buffers, the second records its launch sequence into a CUDA graph,
+        # so the timed calls replay recorded graphs (forward and adjoint alike)
+        for _ in range(2):
+            lat4.adjoint(na, 1, ud4, ud4, q4)
+            lat4.restore(start)
+            lat4.substeps(na, 1, ud4, ud4, q4)
+            lat4.restore(start)
         barrier()
         ev0.record(stream)
         lat4.substeps(na, 1, ud4, ud4, q4)
@@ -514,8 +643,10 @@ def main():
                                "1e-3 (1 +- 0.2 U), tau 0.7, Dirichlet 1 west, zero-flux "
                                "east, periodic y; J = outlet breakthrough; gradients "
                                "w.r.t. every node's rate and the inlet value",
+                   "graph_replay": True,
                    "note": "adjoint_ms is one lbm_adjoint call: forward with checkpoints, "
-                           "recompute and reverse sweep, gradients copied to the host"}
+                           "recompute and reverse sweep, gradients copied to the host; "
+                           "both timed calls replay recorded CUDA graphs"}
 
     # ---- hybrid runs (Algorithm 1): Q1 continuum + lattice, Schwarz ---------
     hybrid = None
@@ -558,9 +689,15 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.cpu_steps > 0:
         dt, cn, threads = run_oracle(case, args.cpu_steps)
         cpu = {"value": cn * args.cpu_steps / dt / 1e9, "unit": "GLUPS", "cores": threads,
-               "kind": "oracle",
+               "kind": "oracle", "cpu_model": cpu_model(),
                "sample": f"{args.cpu_steps} steps of the full {n}x{n} lattice, FP64, "
                          f"{dt:.1f} s"}
+        try:  # the same oracle on one thread, 2 steps of a 2048 x 2048 crop
+            dt1, n1 = oracle_rate_one_thread(2, 2048)
+            cpu["one_thread"] = {"value": n1 * 2 / dt1 / 1e9, "unit": "GLUPS", "cores": 1,
+                                 "sample": f"2 steps of a 2048x2048 crop, FP64, {dt1:.1f} s"}
+        except (OSError, ValueError, IndexError, subprocess.SubprocessError):
+            cpu["one_thread"] = None
 
     if rank == 0:
         line = {
@@ -573,7 +710,9 @@ def main():
                                    "tau 0.7, surface k 1e-3 with dissolution, Dirichlet "
                                    "inlet / Neumann outlet, periodic y",
                        "nx": n, "ny": n, "fluid_nodes": n_fluid,
-                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "parallelism": (f"one {n}x{n * world} lattice split in {world} row "
+                                       f"slabs of {n}x{n}, halo over NCCL")
+                                      if world > 1 else "single GPU",
                        "l2": "inputs larger than L2 (2 x 604 MB populations), no flush"},
             "fluid_glups": world * n_fluid * args.steps / (ms / 1e3) / 1e9,
             "roofline": {"bound": "hbm", "kernel": "lbm_step_tma<false>",

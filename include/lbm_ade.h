@@ -41,24 +41,38 @@
 extern "C" {
 #endif
 
-#define LBM_ADE_ABI_VERSION 1
+#define LBM_ADE_ABI_VERSION 2
 
 typedef struct lbm_ctx lbm_ctx; /* opaque; owned by the library until lbm_destroy */
 
 typedef enum {
   LBM_OK = 0,
+  LBM_WARN_BC_INFEASIBLE = 1, /* success, but boundary solves met data with no
+                                 non-negative solution (Sec. 4.1.1: Dirichlet data
+                                 below the known populations' sum are applied
+                                 literally, Neumann data without a root set the
+                                 unknowns to zero); reported once per new count by
+                                 the calls that wait for the stream
+                                 (lbm_synchronize, lbm_diagnostics); the running
+                                 count is lbm_diag.bc_infeasible */
   LBM_ERR_ARG = -1,     /* invalid argument (size, tau <= 1/2, edge kinds, NULL) */
   LBM_ERR_CUDA = -2,    /* a CUDA call failed; the message names it */
-  LBM_ERR_NOMEM = -3,   /* device allocation failed */
-  LBM_ERR_STATE = -4,   /* context misuse (e.g. restore from a foreign blob) */
-  LBM_ERR_TIMEOUT = -5  /* a kernel's bounded wait expired; the context's
+  LBM_ERR_NEWTON = -3,  /* a maximum-entropy wall solve stopped short of its Newton
+                           tolerance (the last iterate was used); reported like the
+                           warning above, counted in lbm_diag.newton_fail */
+  LBM_ERR_TIMEOUT = -4, /* a kernel's bounded wait expired; the context's
                            results since the last good call are invalid */
+  LBM_ERR_STATE = -5,   /* context misuse (e.g. restore from a foreign blob) */
+  LBM_ERR_NOMEM = -6    /* device allocation failed */
 } lbm_status;
 
 typedef enum {
   LBM_EDGE_PERIODIC = 0,  /* wraps to the opposite side (both sides must be periodic) */
   LBM_EDGE_DIRICHLET = 1, /* max-entropy Dirichlet, Sec. 4.1.1 (a) */
-  LBM_EDGE_NEUMANN = 2    /* max-entropy Neumann on the first moment, Sec. 4.1.1 (b) */
+  LBM_EDGE_NEUMANN = 2,   /* max-entropy Neumann on the first moment, Sec. 4.1.1 (b) */
+  LBM_EDGE_EXCHANGE = 3   /* set by lbm_init_slab only: the S or N side a slab shares
+                             with its neighbour; its ghost row comes from the halo
+                             exchange (lbm_init refuses it) */
 } lbm_edge_kind;
 
 typedef enum {
@@ -68,9 +82,13 @@ typedef enum {
 } lbm_react_mode;
 
 typedef enum {
-  LBM_WALL_BOUNCE = 0, /* pore walls: halfway bounce-back (the default) */
-  LBM_WALL_MAXENT = 1  /* pore walls as zero-flux boundaries of the maximum-entropy
-                          kind, Sec. 4.1.1 (b) (see lbm_set_wall_mode) */
+  LBM_WALL_BOUNCE = 0,        /* pore walls: halfway bounce-back (the default) */
+  LBM_WALL_MAXENT = 1,        /* pore walls as zero-flux boundaries of the maximum-entropy
+                                 kind, Sec. 4.1.1 (b), the Lagrange multiplier found by
+                                 Newton's method in FP64 on either lattice (see
+                                 lbm_set_wall_mode) */
+  LBM_WALL_MAXENT_LATTICE = 2 /* the same walls with Newton's method in the lattice's
+                                 own precision (FP32 on an FP32 lattice: faster) */
 } lbm_wall_mode;
 
 enum { LBM_SIDE_W = 0, LBM_SIDE_E = 1, LBM_SIDE_S = 2, LBM_SIDE_N = 3 };
@@ -78,7 +96,8 @@ enum { LBM_SIDE_W = 0, LBM_SIDE_E = 1, LBM_SIDE_S = 2, LBM_SIDE_N = 3 };
 typedef struct {
   int nx, ny;        /* lattice nodes, each >= 2 */
   int precision;     /* 32: FP32 populations and arithmetic (FP64 boundary
-                        solves, mineral and sums); 64: FP64 throughout */
+                        solves, reaction shares, mineral and sums); 64: FP64
+                        throughout */
   int edge[4];       /* lbm_edge_kind of the W, E, S, N sides */
   double tau;        /* BGK relaxation time (Eq. "Collision"), > 1/2 */
   int react_mode;    /* lbm_react_mode */
@@ -93,10 +112,17 @@ typedef struct {
   double mass;             /* sum of u over the lattice at the current time */
   double outlet_J;         /* sum over all steps of the east-edge (x = nx-1)
                               fluid-node concentrations */
+  double outlet_flux;      /* first moment sum_i f_i e_ix over the east-edge fluid
+                              nodes at the last step (after the boundary
+                              conditions, before collision; Eq. "LBM_Macro") */
+  double min_f;            /* smallest stored population over the fluid nodes
+                              (as lbm_min_population; +inf without fluid) */
   long long steps;         /* time steps taken since lbm_init */
   long long bc_infeasible; /* boundary solves whose data had no non-negative
                               solution (Dirichlet: applied literally; Neumann:
                               unknowns set to zero) */
+  long long newton_fail;   /* wall solves whose Newton iteration stopped short of
+                              its tolerance */
   long long flips;         /* solid nodes turned fluid by dissolution */
   long long n_solid;       /* solid nodes at the current time */
 } lbm_diag;
@@ -145,8 +171,18 @@ lbm_status lbm_get_populations(lbm_ctx* c, double* out);
 lbm_status lbm_get_solid(lbm_ctx* c, uint8_t* out);
 lbm_status lbm_get_mineral(lbm_ctx* c, double* out);
 
-/* Reductions over the lattice in FP64, in a fixed order (deterministic). */
+/* Reductions over the lattice in FP64, in a fixed order (deterministic).
+ * Waits for the stream; may return LBM_WARN_BC_INFEASIBLE or LBM_ERR_NEWTON
+ * (out is filled either way). */
 lbm_status lbm_diagnostics(lbm_ctx* c, lbm_diag* out);
+/* Dissolution record [ny][nx]: for every node turned fluid so far the number
+ * of steps after which it was first fluid (the step whose dissolution
+ * exhausted its mineral, plus one: a node exhausted by the consumption of
+ * the first step reads 1), -1 for nodes never turned fluid.  This is the
+ * integer record the FP32 and FP64 lattices, and the oracle, compare for
+ * the exact mask (Sec. 7.4 narrates dissolution; the rule is that of
+ * lbm_params.dissolution).  LBM_ERR_STATE without dissolution. */
+lbm_status lbm_get_flip_steps(lbm_ctx* c, int32_t* out);
 /* The smallest stored (post-collision) population over the fluid nodes: the
  * check that the populations stay non-negative (Sec. 4.1, Eq. "NN_Cond", and
  * the maximum-entropy boundary data).  +infinity without fluid nodes.  Waits
@@ -162,8 +198,14 @@ lbm_status lbm_min_population(lbm_ctx* c, double* out);
  * maximum-entropy condition with the lattice-weighted normal to the solid
  * neighbours, n = -sum w_i e_i over those directions (normalised); unknowns
  * with e_i.n >= 0 keep bounce-back, as does a node where the sum cancels.
+ * The Lagrange multiplier is found by Newton's method in FP64 (tolerance
+ * 1e-15) and the populations are rounded to the lattice's precision once.
+ * LBM_WALL_MAXENT_LATTICE: the same with the Newton iteration in the
+ * lattice's precision (on an FP32 lattice: FP32, tolerance 1e-7; GB300 runs
+ * FP64 at 1/64 of the FP32 rate, so this mode is the faster one there).
  * Solves with no root set their unknowns to zero and count in
- * lbm_diag.bc_infeasible.  The adjoint (lbm_adjoint) covers bounce-back walls
+ * lbm_diag.bc_infeasible; solves short of the tolerance count in
+ * lbm_diag.newton_fail.  The adjoint (lbm_adjoint) covers bounce-back walls
  * only and returns LBM_ERR_STATE otherwise.  A batch (lbm_batch_create) takes
  * its members' wall modes when it is created; set them before.  Errors:
  * LBM_ERR_ARG for an unknown mode. */
@@ -243,9 +285,12 @@ lbm_status lbm_set_rate_field(lbm_ctx* c, const double* k_field);
  *           applies: solid nodes, and non-surface nodes in surface mode);
  *   grad_ua, grad_ub [n_edge]: dJ/d(Dirichlet data at the start / the end of
  *           the coarse step), edge layout as in lbm_substeps;
- *   grad_q  [n_edge]: dJ/d(Neumann data).
- * The gradient with respect to a uniform inlet value is the sum of grad_ua
- * and grad_ub over that side's slots.  J and every gradient are FP64; any
+ *   grad_q  [n_edge]: dJ/d(Neumann data);
+ *   grad_side [4]: dJ/d(one Dirichlet value held on the whole side W, E, S,
+ *           N over the call), i.e. the sum of grad_ua and grad_ub over that
+ *           side's slots (0 for a side that is not Dirichlet): the gradient
+ *           with respect to a uniform inlet concentration.
+ * J and every gradient are FP64; any
  * output may be NULL; outputs may be host or device memory and are complete
  * when the call returns.
  * Work and memory: the state is kept every `stride` steps (stride <= 0:
@@ -261,7 +306,7 @@ lbm_status lbm_set_rate_field(lbm_ctx* c, const double* k_field);
  * lbm_substeps. */
 lbm_status lbm_adjoint(lbm_ctx* c, int n, int eta, int stride, const double* u_dir_t0,
                        const double* u_dir_t1, const double* q_neu, double* J, double* grad_k,
-                       double* grad_ua, double* grad_ub, double* grad_q);
+                       double* grad_ua, double* grad_ub, double* grad_q, double* grad_side);
 
 /* ---- batches: many lattices advanced together (Sec. 6.3, Algorithm 2 runs
  * several pore-scale subdomains; each member steps as lbm_substeps does) -----
@@ -351,15 +396,17 @@ void lbm_fem_destroy(lbm_fem* f);
 
 /* FP64 sum of a concentration field that allocates nothing -- the paper has
  * no counterpart; this entry point exists for callers that cannot allocate
- * device memory when they need the sum: code recording a CUDA graph (an
- * allocation cannot be captured), code running inside a device-memory budget
- * fixed at start-up, or a host framework that owns every allocation.
+ * device memory when they need the sum: code running inside a device-memory
+ * budget fixed at start-up (a later allocation may fail), or a host framework
+ * that owns every allocation and forbids libraries to call cudaMalloc.
  *   u          device pointer to n values (float if precision is 32, double
  *              if 64), e.g. the [ny][nx] field of lbm_get_concentration
  *   n          1 .. 67,108,864 (8192 x 8192 nodes); larger n -> LBM_ERR_ARG
  *   mass_out   host or device pointer to one double; a host result is
- *              complete when the call returns, a device result is ordered on
- *              `stream`
+ *              complete when the call returns (the call waits for the
+ *              stream), a device result is ordered on `stream`.  A host
+ *              mass_out on a stream in capture mode, where no wait is
+ *              allowed, is refused with LBM_ERR_ARG
  *   stream     cudaStream_t of the work (NULL: legacy default stream)
  * The partial sums live in a fixed 64 KB array in the library's device
  * memory (every GPU that loads the library keeps it until the process exits);
@@ -372,6 +419,94 @@ void lbm_fem_destroy(lbm_fem* f);
 lbm_status lbm_mass_noalloc(const void* u, int precision, long long n, double* mass_out,
                             void* stream);
 const char* lbm_mass_noalloc_error(void);
+
+/* ---- one lattice split into row slabs --------------------------------------
+ * Sec. 5 decomposes a domain into overlapping subdomains that exchange data
+ * on their interfaces; the lattice step reaches one node, so a lattice split
+ * by rows needs an overlap of one row.  Each slab is a context of its own,
+ * on its own GPU or several on one, and the caller moves two small messages
+ * across every shared side per time step; the split lattice computes bit for
+ * bit what the whole one does (populations, concentration, solid mask,
+ * mineral, flip record), only the reductions of lbm_diagnostics are per
+ * slab.
+ *
+ * lbm_init_slab makes the slab of rows y0 .. y1 - 1 (at least 2) of the
+ * lattice p describes; every input array is the WHOLE lattice's ([ny][nx],
+ * velocity [2][ny][nx]); the slab reads its rows, and the mask's rows next to
+ * them.  A side inside the lattice (and both S and N of a y-periodic lattice
+ * split in two or more) becomes LBM_EDGE_EXCHANGE.  Edge data of a slab use
+ * its own edge layout [W: y1-y0][E: y1-y0][S: nx][N: nx].
+ *
+ * A time step of the split lattice, with the messages of each shared side
+ * moved from the sender's pack buffer to the neighbour's unpack buffer:
+ *   lbm_step_stream on every slab;
+ *   phase 0: lbm_halo_pack(side, 0) on every shared side of every slab, then
+ *            lbm_halo_unpack(side, 0) with the neighbour's message;
+ *   lbm_step_dissolve on every slab;
+ *   phase 1: the same with phase 1.
+ * After lbm_init_slab, before the first step: phase 0, lbm_step_dissolve
+ * (the first dissolution pass), phase 1.  lbm_substeps refuses a slab
+ * (LBM_ERR_STATE): its halo must move between the halves of each step.
+ *
+ * A message of phase 0 carries the three populations that stream across the
+ * side from the boundary row and, with dissolution, that row's reaction
+ * shares; phase 1 carries the boundary row's solid and turning-fluid flags,
+ * from which the receiver sets its links across the cut and lists the solid
+ * nodes a neighbour's flip exposed.  lbm_halo_bytes gives a message's size
+ * (the same for both sides).  Buffers are device memory of the slab's
+ * device, caller-owned; pack and unpack are asynchronous on the slab's
+ * stream.  Errors: LBM_ERR_ARG (a side that is not shared, a phase other
+ * than 0 or 1, a host buffer), LBM_ERR_STATE (lbm_step_stream before the
+ * first dissolution pass), LBM_ERR_CUDA. */
+lbm_status lbm_init_slab(lbm_ctx** out, const lbm_params* p, int y0, int y1,
+                         const uint8_t* solid, const double* vel, const double* k_field,
+                         const double* mineral, const double* u0, void* stream);
+lbm_status lbm_halo_bytes(lbm_ctx* c, int phase, size_t* bytes);
+lbm_status lbm_halo_pack(lbm_ctx* c, int side, int phase, void* buf);
+/* side: the side the message crossed (its neighbour's opposite side packed it) */
+lbm_status lbm_halo_unpack(lbm_ctx* c, int side, int phase, const void* buf);
+/* The two halves of one substep j of eta (lbm_substeps runs both for every
+ * step of an unsplit lattice): the fused step -- streaming, boundary
+ * conditions, collision; final_step nonzero also writes u and the mass
+ * partials -- with the edge data of the last lbm_stage_edges, and the
+ * dissolution pass (a no-op without dissolution). */
+lbm_status lbm_stage_edges(lbm_ctx* c, const double* u_dir_t0, const double* u_dir_t1,
+                           const double* q_neu);
+lbm_status lbm_step_stream(lbm_ctx* c, int j, int eta, int final_step);
+lbm_status lbm_step_dissolve(lbm_ctx* c);
+
+/* ---- the D1Q2 lattice of the one-dimensional hybrid (Sec. 7.1) ------------
+ * Nodes j = 0 .. n-1 of a line; velocities +-c (c = h / dt), weights 1/2,
+ * c_s^2 = c^2, so in lattice units D dt / h^2 = tau - 1/2 and the equilibrium
+ * (Eq. "LBM_feq") is f_+- = (u/2)(1 +- vl) with vl = v dt / h, |vl| < 1.  A
+ * step streams the stored post-collision populations, sets the one unknown
+ * population at each end by the maximum-entropy conditions of Sec. 4.1.1 --
+ * a Dirichlet end (LBM_EDGE_DIRICHLET): the unknown takes the missing mass,
+ * f = u^p - (the known one); a Neumann end (LBM_EDGE_NEUMANN): its unknown
+ * has e.n = -1, so f = (the known one) - q^p, and zero flux is bounce-back --
+ * takes u = f_+ + f_- and collides.  FP64 throughout; all n substeps of a
+ * call run in one kernel launch.
+ *   lbm1d_init: u0 [n] (NULL: zero), host or device; f = f^eq(u0).
+ *   lbm1d_substeps: substeps j = 1..n of eta with the end data (left,
+ *     right) interpolated as (1 - j/eta) ends_t0 + (j/eta) ends_t1 (Eq.
+ *     "MTS"; ends_t1 NULL: equal to ends_t0; NULL: zero), q (left, right)
+ *     the Neumann data, outward first moments; each a 2-element array, host
+ *     or device.  Returns once the steps are done.
+ *   lbm1d_get: u [n] at the current time (host or device).
+ *   lbm1d_state_bytes / save / restore: the whole state (the Schwarz
+ *     rollback of Algorithm 1), caller-owned buffer, host or device.
+ * Errors: LBM_ERR_ARG (n < 2, tau <= 1/2, |vl| >= 1, an end kind other than
+ * Dirichlet or Neumann, a null argument), LBM_ERR_NOMEM, LBM_ERR_CUDA. */
+typedef struct lbm1d lbm1d;
+lbm_status lbm1d_init(lbm1d** out, int n, double tau, double vl, int left, int right,
+                      const double* u0, void* stream);
+lbm_status lbm1d_substeps(lbm1d* c, int n, int eta, const double* ends_t0,
+                          const double* ends_t1, const double* q);
+lbm_status lbm1d_get(lbm1d* c, double* u);
+lbm_status lbm1d_state_bytes(lbm1d* c, size_t* bytes);
+lbm_status lbm1d_save(lbm1d* c, void* buf, size_t bytes);
+lbm_status lbm1d_restore(lbm1d* c, const void* buf, size_t bytes);
+void lbm1d_destroy(lbm1d* c);
 
 /* Release the context's device memory (waits for its stream first). */
 void lbm_destroy(lbm_ctx* c);

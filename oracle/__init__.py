@@ -65,7 +65,8 @@ def _load():
         lib.or_lbm_free.argtypes = [P]
         lib.or_lbm_substeps.argtypes = [P, I, I, P, P, P]
         for name in ("or_lbm_get_u", "or_lbm_get_f", "or_lbm_get_solid",
-                     "or_lbm_get_mineral", "or_lbm_get_fpost", "or_lbm_diag"):
+                     "or_lbm_get_mineral", "or_lbm_get_fpost", "or_lbm_diag",
+                     "or_lbm_get_flip_steps"):
             getattr(lib, name).argtypes = [P, P]
         lib.or_lbm_H.restype = D
         lib.or_lbm_H.argtypes = [P]
@@ -215,6 +216,14 @@ class LBMOracle:
     def mineral(self):
         out = np.empty((self.ny, self.nx))
         self._lib.or_lbm_get_mineral(self._h, _ptr(out))
+        return out
+
+    def flip_steps(self):
+        """[ny, nx] int32: steps after which each node was first fluid by
+        dissolution (-1 for nodes never turned fluid) -- the integer record
+        behind the exact-mask comparison (reading c16)."""
+        out = np.empty((self.ny, self.nx), dtype=np.int32)
+        self._lib.or_lbm_get_flip_steps(self._h, _ptr(out))
         return out
 
     def diag(self):

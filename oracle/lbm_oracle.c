@@ -87,6 +87,8 @@ typedef struct {
   double *vel;     /* [2][ny][nx]                                  */
   uint8_t *solid;  /* [ny][nx] 1 = solid                           */
   double *mineral; /* [ny][nx] mineral mass of solid nodes         */
+  int *flip_step;  /* [ny][nx] steps after which a node was first fluid
+                      by dissolution (-1: never) -- bookkeeping only */
   double *f;       /* [9][ny][nx] populations after BC (state)     */
   double *fpost;   /* [9][ny][nx] post-collision populations       */
   double *fnew;    /* [9][ny][nx] streamed populations             */
@@ -271,6 +273,7 @@ or_lbm *or_lbm_new(int nx, int ny, const int *edge, double tau,
   o->vel = (double *)malloc(2 * N * sizeof(double));
   o->solid = (uint8_t *)malloc(N);
   o->mineral = (double *)malloc(N * sizeof(double));
+  o->flip_step = (int *)malloc(N * sizeof(int));
   o->f = (double *)calloc(NQ * N, sizeof(double));
   o->fpost = (double *)calloc(NQ * N, sizeof(double));
   o->fnew = (double *)calloc(NQ * N, sizeof(double));
@@ -280,6 +283,7 @@ or_lbm *or_lbm_new(int nx, int ny, const int *edge, double tau,
     o->k[n] = k_field ? k_field[n] : k_scalar;
     o->solid[n] = solid ? (solid[n] ? 1 : 0) : 0;
     o->mineral[n] = mineral ? mineral[n] : 1.0;
+    o->flip_step[n] = -1;
     o->vel[n] = vel ? vel[n] : 0.0;
     o->vel[N + n] = vel ? vel[N + n] : 0.0;
   }
@@ -295,7 +299,7 @@ or_lbm *or_lbm_new(int nx, int ny, const int *edge, double tau,
 
 void or_lbm_free(or_lbm *o) {
   if (!o) return;
-  free(o->k); free(o->vel); free(o->solid); free(o->mineral);
+  free(o->k); free(o->vel); free(o->solid); free(o->mineral); free(o->flip_step);
   free(o->f); free(o->fpost); free(o->fnew); free(o->known); free(o->u);
   free(o);
 }
@@ -535,6 +539,7 @@ void or_lbm_substeps(or_lbm *o, int n, int eta, const double *ua,
       for (size_t m = 0; m < N; ++m)
         if (o->solid[m] && o->mineral[m] <= 0.0) {
           o->solid[m] = 0;
+          o->flip_step[m] = (int)(o->steps + 1);
           for (int i = 0; i < NQ; ++i) o->f[(size_t)i * N + m] = 0.0;
           o->flips += 1;
         }
@@ -551,6 +556,7 @@ void or_lbm_get_u(const or_lbm *o, double *out) { memcpy(out, o->u, nn(o) * size
 void or_lbm_get_f(const or_lbm *o, double *out) { memcpy(out, o->f, NQ * nn(o) * sizeof(double)); }
 void or_lbm_get_solid(const or_lbm *o, uint8_t *out) { memcpy(out, o->solid, nn(o)); }
 void or_lbm_get_mineral(const or_lbm *o, double *out) { memcpy(out, o->mineral, nn(o) * sizeof(double)); }
+void or_lbm_get_flip_steps(const or_lbm *o, int *out) { memcpy(out, o->flip_step, nn(o) * sizeof(int)); }
 
 /* Post-collision populations of the current state (what the next step would
  * stream), for comparing against a solver that stores them. */
@@ -827,6 +833,7 @@ or_lbm *or_lbm_clone(const or_lbm *o) {
   size_t N = nn(o);
   memcpy(c->f, o->f, NQ * N * sizeof(double));
   memcpy(c->u, o->u, N * sizeof(double));
+  memcpy(c->flip_step, o->flip_step, N * sizeof(int));
   c->steps = o->steps; c->bc_infeasible = o->bc_infeasible; c->flips = o->flips;
   c->newton_iters = o->newton_iters; c->newton_fail = o->newton_fail;
   c->J = o->J; c->reacted = o->reacted;
@@ -840,6 +847,7 @@ void or_lbm_assign(or_lbm *dst, const or_lbm *src) {
   memcpy(dst->u, src->u, N * sizeof(double));
   memcpy(dst->solid, src->solid, N);
   memcpy(dst->mineral, src->mineral, N * sizeof(double));
+  memcpy(dst->flip_step, src->flip_step, N * sizeof(int));
   memcpy(dst->k, src->k, N * sizeof(double));
   dst->steps = src->steps; dst->bc_infeasible = src->bc_infeasible; dst->flips = src->flips;
   dst->newton_iters = src->newton_iters; dst->newton_fail = src->newton_fail;

@@ -11,9 +11,11 @@ _lock = threading.Lock()
 _lib = None
 
 LBM_OK = 0
-STATUS_NAMES = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_CUDA",
-                -3: "LBM_ERR_NOMEM", -4: "LBM_ERR_STATE",
-                -5: "LBM_ERR_TIMEOUT"}
+LBM_WARN_BC_INFEASIBLE = 1
+LBM_ERR_NEWTON = -3
+STATUS_NAMES = {0: "LBM_OK", 1: "LBM_WARN_BC_INFEASIBLE", -1: "LBM_ERR_ARG",
+                -2: "LBM_ERR_CUDA", -3: "LBM_ERR_NEWTON", -4: "LBM_ERR_TIMEOUT",
+                -5: "LBM_ERR_STATE", -6: "LBM_ERR_NOMEM"}
 
 
 class LBMError(RuntimeError):
@@ -40,8 +42,10 @@ class FemParams(ctypes.Structure):
 
 class Diag(ctypes.Structure):
     _fields_ = [("mass", ctypes.c_double), ("outlet_J", ctypes.c_double),
+                ("outlet_flux", ctypes.c_double), ("min_f", ctypes.c_double),
                 ("steps", ctypes.c_longlong), ("bc_infeasible", ctypes.c_longlong),
-                ("flips", ctypes.c_longlong), ("n_solid", ctypes.c_longlong)]
+                ("newton_fail", ctypes.c_longlong), ("flips", ctypes.c_longlong),
+                ("n_solid", ctypes.c_longlong)]
 
 
 def lib_path() -> str:
@@ -73,6 +77,7 @@ def load():
             "lbm_get_populations": [P, P],
             "lbm_get_solid": [P, P],
             "lbm_get_mineral": [P, P],
+            "lbm_get_flip_steps": [P, P],
             "lbm_diagnostics": [P, ctypes.POINTER(Diag)],
             "lbm_set_wall_mode": [P, I],
             "lbm_min_population": [P, ctypes.POINTER(D)],
@@ -92,9 +97,22 @@ def load():
             "lbm_fem_get": [P, P],
             "lbm_fem_set": [P, P],
             "lbm_fem_solver_info": [P, ctypes.POINTER(I), ctypes.POINTER(D)],
-            "lbm_adjoint": [P, I, I, I, P, P, P, ctypes.POINTER(D), P, P, P, P],
+            "lbm_adjoint": [P, I, I, I, P, P, P, ctypes.POINTER(D), P, P, P, P, P],
             "lbm_kernel_times_read": [P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong),
                                       ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong)],
+            "lbm_init_slab": [ctypes.POINTER(P), ctypes.POINTER(Params), I, I, P, P, P, P, P, P],
+            "lbm_halo_bytes": [P, I, ctypes.POINTER(S)],
+            "lbm_halo_pack": [P, I, I, P],
+            "lbm_halo_unpack": [P, I, I, P],
+            "lbm_stage_edges": [P, P, P, P],
+            "lbm_step_stream": [P, I, I, I],
+            "lbm_step_dissolve": [P],
+            "lbm1d_init": [ctypes.POINTER(P), I, D, D, I, I, P, P],
+            "lbm1d_substeps": [P, I, I, P, P, P],
+            "lbm1d_get": [P, P],
+            "lbm1d_state_bytes": [P, ctypes.POINTER(S)],
+            "lbm1d_save": [P, P, S],
+            "lbm1d_restore": [P, P, S],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -120,6 +138,8 @@ def load():
         lib.lbm_fem_destroy.restype = None
         lib.lbm_destroy.argtypes = [P]
         lib.lbm_destroy.restype = None
+        lib.lbm1d_destroy.argtypes = [P]
+        lib.lbm1d_destroy.restype = None
         lib.lbm_last_error.argtypes = []
         lib.lbm_last_error.restype = ctypes.c_char_p
         lib.lbm_abi_version.argtypes = []
@@ -128,10 +148,22 @@ def load():
         return lib
 
 
-def check(status: int):
-    if status != LBM_OK:
+# The last LBM_WARN_BC_INFEASIBLE message (the library's calls that wait for
+# the stream report, once per new count, boundary solves whose data had no
+# non-negative solution; they are counted, not failures).
+last_warning = None
+
+
+def check(status: int) -> int:
+    """Raise LBMError on a negative status; a warning (positive status) is
+    kept in ``last_warning`` and returned."""
+    global last_warning
+    if status < 0:
         msg = load().lbm_last_error().decode(errors="replace")
         raise LBMError(status, msg)
+    if status > 0:
+        last_warning = load().lbm_last_error().decode(errors="replace")
+    return status
 
 
 def check_batch(status: int):

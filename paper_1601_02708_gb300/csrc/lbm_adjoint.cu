@@ -139,37 +139,32 @@ __device__ __forceinline__ void adjoint_node(const AdjArgs<Real>& a, int x, int 
     if (unknown) {
       int dside, nside, sx, sy;
       edge_kind(a.edge, x, y, a.nx, a.ny, &dside, &nside, &sx, &sy);
-      // t = sum_U w_i nu_i / W_U, in the lattice's precision (the
-      // FP32 lattice's boundary solves are FP32 too)
-      Real t = (Real)0;
+      // t = sum_U w_i nu_i / W_U over the unknowns, in FP64 on either lattice
+      // (the transpose of the forward solves, which run in FP64)
+      double t = 0.0, wu = 0.0;
 #pragma unroll
       for (int i = 0; i < 9; ++i)
-        if (unknown & (1u << i)) t += (Real)w_of(i) * nu[i];
-      if constexpr (sizeof(Real) == 4) {
-        t *= inv_weight_sum(unknown);
-      } else {
-        double wu = 0.0;
-#pragma unroll
-        for (int i = 0; i < 9; ++i)
-          if (unknown & (1u << i)) wu += w_of(i);
-        t /= wu;
-      }
+        if (unknown & (1u << i)) {
+          t += w_of(i) * (double)nu[i];
+          wu += w_of(i);
+        }
+      t /= wu;
       if (dside >= 0) {
         const int slot = edge_slot(dside, x, y, a.nx, a.ny);
 #pragma unroll
         for (int i = 0; i < 9; ++i)
-          if (!(unknown & (1u << i))) nu[i] -= t;
-        atomicAdd(a.g_ua + slot, (1.0 - a.frac) * (double)t);
-        atomicAdd(a.g_ub + slot, a.frac * (double)t);
+          if (!(unknown & (1u << i))) nu[i] = (Real)((double)nu[i] - t);
+        atomicAdd(a.g_ua + slot, (1.0 - a.frac) * t);
+        atomicAdd(a.g_ub + slot, a.frac * t);
       } else {
         const int slot = edge_slot(nside, x, y, a.nx, a.ny);
         if (a.root[slot]) {
 #pragma unroll
           for (int i = 0; i < 9; ++i) {
             const int d = cx_of(i) * sx + cy_of(i) * sy;
-            if (!(unknown & (1u << i)) && d != 0) nu[i] += (Real)d * t;
+            if (!(unknown & (1u << i)) && d != 0) nu[i] = (Real)((double)nu[i] + d * t);
           }
-          atomicAdd(a.g_q + slot, -(double)t);
+          atomicAdd(a.g_q + slot, -t);
         }
       }
 #pragma unroll
@@ -246,6 +241,7 @@ namespace {
 lbm_status ensure_work(lbm_ctx* c, int K, int L) {
   AdjWork* w = c->adj;
   if (w && w->cap_k >= K && w->cap_l >= L) return LBM_OK;
+  ctx_drop_recorded(c, 1);  // recorded reverse sweeps write the old buffers
   ctx_adjoint_free(c);
   w = new AdjWork();
   c->adj = w;
@@ -306,8 +302,7 @@ AdjArgs<Real> adj_args(lbm_ctx* c, AdjWork* w, int mc, const Real* u_n,
 template <typename Real>
 lbm_status adjoint_impl(lbm_ctx* c, int n, int eta, int L) {
   const int K = (n + L - 1) / L;
-  ATRY(ensure_work(c, K, L));
-  AdjWork* w = c->adj;
+  AdjWork* w = c->adj;  // sized by ensure_work(c, K, L) before the call
   const size_t pb = w->plane_b, fb = 9 * pb;
   const size_t ne = (size_t)c->nedge;
   cudaStream_t st = c->stream;
@@ -344,13 +339,16 @@ lbm_status adjoint_impl(lbm_ctx* c, int n, int eta, int L) {
     ACK(cudaMemcpyAsync(c->f[0], w->ck + (size_t)s * fb, fb, cudaMemcpyDeviceToDevice, st));
     c->cur = 0;
     for (int j = n0 + 1; j <= n1; ++j) {
+      // recompute: u of every step into the history (no mass sums: not a
+      // final substep), the Neumann branches into their record
       lbm::StepArgs<Real> a = step_args<Real>(c, (double)j / eta);
-      a.u_out = (Real*)(w->uh + (size_t)(j - n0 - 1) * pb);
+      a.u_hist = (Real*)(w->uh + (size_t)(j - n0 - 1) * pb);
       a.bc_root = w->roots + (size_t)(j - n0 - 1) * ne;
       a.partial = w->part;
       a.jnode = w->jn;
+      a.jflux = nullptr;  // the context keeps the forward run's last flux
       a.infeasible = w->inf;
-      ATRY(ctx_launch_step<Real>(c, a, true));
+      ATRY(ctx_launch_step<Real>(c, a, false));
       c->cur ^= 1;
     }
     for (int j = n1; j > n0; --j) {
@@ -378,6 +376,15 @@ lbm_status adjoint_impl(lbm_ctx* c, int n, int eta, int L) {
   c->cur = cur_final;
   c->nparts = nparts_final;
   return LBM_OK;
+}
+
+struct AdjCall {
+  int n, eta, L;
+};
+template <typename Real>
+lbm_status enqueue_adjoint(lbm_ctx* c, void* arg) {
+  const AdjCall* a = (const AdjCall*)arg;
+  return adjoint_impl<Real>(c, a->n, a->eta, a->L);
 }
 
 // A context the adjoint can differentiate: fixed mask, and no corner where
@@ -414,20 +421,47 @@ extern "C" {
 
 lbm_status lbm_adjoint(lbm_ctx* c, int n, int eta, int stride, const double* u_dir_t0,
                        const double* u_dir_t1, const double* q_neu, double* J, double* grad_k,
-                       double* grad_ua, double* grad_ub, double* grad_q) {
+                       double* grad_ua, double* grad_ub, double* grad_q, double* grad_side) {
   ATRY(ctx_check(c));
   if (n < 1 || eta < 1) return ctx_fail(LBM_ERR_ARG, "lbm_adjoint: need n >= 1 and eta >= 1");
   ATRY(check_adjoint(c));
   int L = stride > 0 ? stride : (int)std::ceil(std::sqrt((double)n));
   if (L > n) L = n;
   ATRY(ctx_stage_edges(c, u_dir_t0, u_dir_t1, q_neu));
-  ATRY(c->esize == 8 ? adjoint_impl<double>(c, n, eta, L) : adjoint_impl<float>(c, n, eta, L));
+  ATRY(ensure_work(c, (n + L - 1) / L, L));
+  // the whole device sequence (forward with checkpoints, recompute, reverse
+  // sweep) is one launch sequence, recorded on a repeated call and replayed
+  AdjCall call{n, eta, L};
+  const lbm_ctx::GraphKey key{1, n, eta, L, c->cur, walls_variant(c), c->use_tma ? 1 : 0};
+  if (c->timing) ATRY(c->esize == 8 ? adjoint_impl<double>(c, n, eta, L)
+                                    : adjoint_impl<float>(c, n, eta, L));
+  else ATRY(ctx_run_recorded(c, key, c->esize == 8 ? enqueue_adjoint<double>
+                                                    : enqueue_adjoint<float>, &call));
   AdjWork* w = c->adj;
   if (grad_k) ATRY(ctx_field_out_f64(c, w->gk, grad_k));
   const size_t ne = (size_t)c->nedge;
   ATRY(copy_out(c, grad_ua, w->ge, ne));
   ATRY(copy_out(c, grad_ub, w->ge + ne, ne));
   ATRY(copy_out(c, grad_q, w->ge + 2 * ne, ne));
+  if (grad_side) {
+    // dJ/d(a value held on a whole Dirichlet side): its slots' start and end
+    // gradients summed in slot order
+    std::vector<double> ge(2 * ne);
+    ACK(cudaMemcpyAsync(ge.data(), w->ge, 2 * ne * sizeof(double), cudaMemcpyDeviceToHost,
+                        c->stream));
+    ACK(cudaStreamSynchronize(c->stream));
+    const int nx = c->p.nx, ny = c->p.ny;
+    const int first[4] = {0, ny, 2 * ny, 2 * ny + nx}, len[4] = {ny, ny, nx, nx};
+    double side[4];
+    for (int sd = 0; sd < 4; ++sd) {
+      double acc = 0.0;
+      if (c->p.edge[sd] == LBM_EDGE_DIRICHLET)
+        for (int k = first[sd]; k < first[sd] + len[sd]; ++k) acc += ge[k] + ge[ne + k];
+      side[sd] = acc;
+    }
+    ACK(cudaMemcpyAsync(grad_side, side, sizeof(side), cudaMemcpyDefault, c->stream));
+    ACK(cudaStreamSynchronize(c->stream));
+  }
   if (J) {
     std::vector<double> after(c->p.ny), before(c->p.ny);
     ACK(cudaMemcpyAsync(after.data(), c->jnode, c->p.ny * sizeof(double),

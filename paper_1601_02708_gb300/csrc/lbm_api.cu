@@ -14,6 +14,8 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <type_traits>
+#include <vector>
 
 #include "lbm_ade.h"
 #include "lbm_kernels.cuh"
@@ -80,28 +82,41 @@ __global__ void k_pitch_in(const double* __restrict__ src, T* __restrict__ dst, 
 }
 
 // Link word of every interior node (see lbm_lattice.cuh) from the caller's
-// solid array; periodic sides wrap, other sides are outside.
+// solid array of the whole lattice ([nyg][nx]); the context holds rows
+// y0 .. y0 + nyl - 1 of it (all of it unless the lattice is split into
+// slabs).  Periodic sides wrap, other sides are outside.  With ghost_s /
+// ghost_n set (the slab's S / N side is shared with a neighbouring slab) the
+// row beyond it is the neighbour's boundary row: its nodes' own solid bits are
+// written into the ghost row, and the links that cross into it are set from
+// the whole lattice's mask like any other.
 __global__ void k_link_in(const uint8_t* __restrict__ src, uint32_t* __restrict__ link, int nx,
-                          int ny, int pitch, int per_x, int per_y) {
-  const long long total = (long long)nx * ny;
+                          int nyl, int y0, int nyg, int pitch, int per_x, int per_yg,
+                          int ghost_s, int ghost_n) {
+  const int rows = nyl + ghost_s + ghost_n;
+  const long long total = (long long)nx * rows;
   for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
        id += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(id % nx), y = (int)(id / nx);
-    uint32_t w = (src && src[id]) ? lbm::kOwnSolid : 0u;
-    for (int i = 1; i < 9; ++i) {
-      int sx = x - lbm::cx_of(i), sy = y - lbm::cy_of(i);
-      bool out = false;
-      if (sx < 0 || sx >= nx) {
-        if (per_x) sx = (sx + nx) % nx; else out = true;
+    const int x = (int)(id % nx), yl = (int)(id / nx) - ghost_s;
+    int yg = y0 + yl;
+    if (yg < 0 || yg >= nyg) yg = ((yg % nyg) + nyg) % nyg;  // ghost row across the wrap
+    const bool me_solid = src && src[(long long)yg * nx + x];
+    uint32_t w = me_solid ? lbm::kOwnSolid : 0u;
+    if (yl >= 0 && yl < nyl) {
+      for (int i = 1; i < 9; ++i) {
+        int sx = x - lbm::cx_of(i), sy = yg - lbm::cy_of(i);
+        bool out = false;
+        if (sx < 0 || sx >= nx) {
+          if (per_x) sx = (sx + nx) % nx; else out = true;
+        }
+        if (sy < 0 || sy >= nyg) {
+          if (per_yg) sy = (sy + nyg) % nyg; else out = true;
+        }
+        if (out) w |= lbm::up_bit(lbm::kUpOutShift, i);
+        else if (src && src[(long long)sy * nx + sx])
+          w |= lbm::up_bit(lbm::kUpSolidShift, i) | lbm::up_bit(lbm::kUpPostShift, i);
       }
-      if (sy < 0 || sy >= ny) {
-        if (per_y) sy = (sy + ny) % ny; else out = true;
-      }
-      if (out) w |= lbm::up_bit(lbm::kUpOutShift, i);
-      else if (src && src[(long long)sy * nx + sx])
-        w |= lbm::up_bit(lbm::kUpSolidShift, i) | lbm::up_bit(lbm::kUpPostShift, i);
     }
-    link[(long long)(y + kYO) * pitch + (x + kXO)] = w;
+    link[(long long)(yl + kYO) * pitch + (x + kXO)] = w;
   }
 }
 
@@ -144,19 +159,20 @@ __global__ void k_count_solid(const uint32_t* __restrict__ link, int nx, int ny,
 
 // Fixed-order FP64 reductions for lbm_diagnostics (one block).
 __global__ void k_diag(const double* __restrict__ partial, int nparts,
-                       const double* __restrict__ jnode, int ny,
-                       const long long* __restrict__ infeas, int nedge, DiagDev* out) {
+                       const double* __restrict__ jnode, const double* __restrict__ jflux,
+                       int ny, const long long* __restrict__ infeas, int nedge, DiagDev* out) {
   __shared__ double sd[256];
   __shared__ long long sl[256];
   const int t = threadIdx.x;
-  double m = 0.0, j = 0.0;
+  double m = 0.0, j = 0.0, q = 0.0;
   long long c = 0;
   for (int i = t; i < nparts; i += blockDim.x) m += partial[i];
   for (int i = t; i < ny; i += blockDim.x) j += jnode[i];
+  for (int i = t; i < ny; i += blockDim.x) q += jflux[i];
   for (int i = t; i < nedge; i += blockDim.x) c += infeas[i];
-  double* outs[2] = {&out->mass, &out->J};
-  double vals[2] = {m, j};
-  for (int k = 0; k < 2; ++k) {
+  double* outs[3] = {&out->mass, &out->J, &out->flux};
+  double vals[3] = {m, j, q};
+  for (int k = 0; k < 3; ++k) {
     sd[t] = vals[k];
     __syncthreads();
     if (t == 0) {
@@ -203,11 +219,6 @@ __global__ void k_trace(const Real* __restrict__ u, int nx, int ny, int pitch, i
   };
   out[k] = U(ax, ay) * (1 - gx) * (1 - gy) + U(bx, ay) * gx * (1 - gy) +
            U(bx, by) * gx * gy + U(ax, by) * (1 - gx) * gy;
-}
-
-__global__ void k_to_f32(const double* __restrict__ src, float* __restrict__ dst, int n) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) dst[i] = (float)src[i];
 }
 
 int grid1d(long long n) {
@@ -268,11 +279,16 @@ lbm_status time_end(lbm_ctx* c, int which) {
   return LBM_OK;
 }
 
+// The reaction shares the step stores for the dissolution pass: double on
+// the FP64 lattice, ShareF32 on the FP32 lattice.
+template <typename Real>
+using ShareOf = typename std::conditional<sizeof(Real) == 8, double, lbm::ShareF32>::type;
+
 template <typename Real>
 lbm_status launch_dissolve(lbm_ctx* c) {
   TRY(time_begin(c, 1));
-  lbm::lbm_dissolve_list<Real><<<c->dgrid, lbm::kDThreads, 0, c->stream>>>(
-      dissolve_args(c), (const Real*)c->ureact);
+  lbm::lbm_dissolve_list<ShareOf<Real>><<<c->dgrid, lbm::kDThreads, 0, c->stream>>>(
+      dissolve_args(c), (const ShareOf<Real>*)c->ureact);
   CK(cudaGetLastError());
   return time_end(c, 1);
 }
@@ -283,8 +299,8 @@ template <typename Real>
 lbm_status first_dissolve(lbm_ctx* c) {
   lbm::DissolveArgs d = dissolve_args(c);
   d.check_all = 1;
-  lbm::lbm_dissolve_dense<Real><<<c->dgrid, lbm::kDThreads, 0, c->stream>>>(
-      d, (const Real*)c->ureact);
+  lbm::lbm_dissolve_dense<ShareOf<Real>><<<c->dgrid, lbm::kDThreads, 0, c->stream>>>(
+      d, (const ShareOf<Real>*)c->ureact);
   CK(cudaGetLastError());
   lbm::lbm_list_build<<<c->dgrid, lbm::kDThreads, 0, c->stream>>>(dissolve_args(c));
   CK(cudaGetLastError());
@@ -299,9 +315,10 @@ lbm_status sync_mineral(lbm_ctx* c) {
   return LBM_OK;
 }
 
-// The step kernels are built with and without the maximum-entropy wall
-// code; a context whose pore walls bounce back runs the kernels without it.
-template <typename Real, bool kWalls>
+// The step kernels are built without wall code and with the two precisions
+// of the maximum-entropy wall solve (walls_variant); a context runs the one
+// its wall mode needs.
+template <typename Real, int kWalls>
 lbm_status launch_step_kernels(lbm_ctx* c, const lbm::StepArgs<Real>& a, bool final_step) {
   if (sizeof(Real) == 4 && c->use_tma) {
     const lbm::TmaMaps& m = c->maps[c->cur];
@@ -326,8 +343,13 @@ lbm_status launch_step_kernels(lbm_ctx* c, const lbm::StepArgs<Real>& a, bool fi
 
 template <typename Real>
 lbm_status launch_step_impl(lbm_ctx* c, const lbm::StepArgs<Real>& a, bool final_step) {
-  return c->wall_mode == LBM_WALL_BOUNCE ? launch_step_kernels<Real, false>(c, a, final_step)
-                                         : launch_step_kernels<Real, true>(c, a, final_step);
+  switch (walls_variant(c)) {
+    case 0: return launch_step_kernels<Real, 0>(c, a, final_step);
+    case 1: return launch_step_kernels<Real, 1>(c, a, final_step);
+    default:
+      if constexpr (sizeof(Real) == 4) return launch_step_kernels<Real, 2>(c, a, final_step);
+      return launch_step_kernels<Real, 1>(c, a, final_step);
+  }
 }
 
 template <typename Real>
@@ -343,6 +365,19 @@ lbm_status run_steps(lbm_ctx* c, int n, int eta) {
   return LBM_OK;
 }
 
+// Longest call whose launches are recorded into a graph (two kernel nodes a
+// step); longer calls launch directly.
+constexpr int kGraphMaxSteps = 8192;
+
+struct StepsCall {
+  int n, eta;
+};
+template <typename Real>
+lbm_status enqueue_steps_call(lbm_ctx* c, void* arg) {
+  const StepsCall* s = (const StepsCall*)arg;
+  return run_steps<Real>(c, s->n, s->eta);
+}
+
 template <typename Real>
 lbm_status run_init(lbm_ctx* c, const double* u0dev) {
   auto a = step_args<Real>(c, 0.0);
@@ -351,8 +386,13 @@ lbm_status run_init(lbm_ctx* c, const double* u0dev) {
   CK(cudaGetLastError());
   c->nparts = (int)(c->grid.x * c->grid.y);
   c->cur = 0;
-  if (c->p.dissolution) return first_dissolve<Real>(c);
-  return LBM_OK;
+  if (!c->p.dissolution) return LBM_OK;
+  // a slab's first pass gathers shares across its cuts: it waits for the halo
+  if (c->p.edge[2] == LBM_EDGE_EXCHANGE || c->p.edge[3] == LBM_EDGE_EXCHANGE) {
+    c->first_pass_due = true;
+    return LBM_OK;
+  }
+  return first_dissolve<Real>(c);
 }
 
 // Copy a caller array of `count` doubles (host or device) to a device buffer.
@@ -373,6 +413,9 @@ lbm_status stage_doubles(lbm_ctx* c, const double* src, size_t count, double** o
 
 void free_ctx(lbm_ctx* c) {
   if (!c) return;
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
+  c->graphs.clear();
+  if (c->rec_stream) cudaStreamDestroy(c->rec_stream);
   for (int w = 0; w < 2; ++w)
     for (int i = 0; i < lbm_ctx::kPool; ++i)
       for (int k = 0; k < 2; ++k)
@@ -381,7 +424,7 @@ void free_ctx(lbm_ctx* c) {
                   c->u,      c->ureact,   c->mineral,   c->edge,       c->infeasible,
                   c->jnode,  c->partial,  c->flip_list, c->flip_count, c->counters,
                   c->status, c->diag,     c->scratch,   c->slist,      c->smin,
-                  c->edge32};
+                  c->jflux,  c->open_nodes, c->flip_step};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   ctx_adjoint_free(c);
@@ -432,13 +475,17 @@ lbm_status setup_tma(lbm_ctx* c) {
       TRY(make_map("rate", &m.kf, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, c->kf, d2, sf, bk));
     else m.kf = m.link;  // never read without a rate field
   }
-  CK(cudaFuncSetAttribute(lbm::lbm_step_tma<true>,
+  CK(cudaFuncSetAttribute(lbm::lbm_step_tma<true, 0>,
                           cudaFuncAttributeMaxDynamicSharedMemorySize, lbm::kTmaSmem));
-  CK(cudaFuncSetAttribute(lbm::lbm_step_tma<false>,
+  CK(cudaFuncSetAttribute(lbm::lbm_step_tma<false, 0>,
                           cudaFuncAttributeMaxDynamicSharedMemorySize, lbm::kTmaSmem));
-  CK(cudaFuncSetAttribute(lbm::lbm_step_tma<true, true>,
+  CK(cudaFuncSetAttribute(lbm::lbm_step_tma<true, 1>,
                           cudaFuncAttributeMaxDynamicSharedMemorySize, lbm::kTmaSmem));
-  CK(cudaFuncSetAttribute(lbm::lbm_step_tma<false, true>,
+  CK(cudaFuncSetAttribute(lbm::lbm_step_tma<false, 1>,
+                          cudaFuncAttributeMaxDynamicSharedMemorySize, lbm::kTmaSmem));
+  CK(cudaFuncSetAttribute(lbm::lbm_step_tma<true, 2>,
+                          cudaFuncAttributeMaxDynamicSharedMemorySize, lbm::kTmaSmem));
+  CK(cudaFuncSetAttribute(lbm::lbm_step_tma<false, 2>,
                           cudaFuncAttributeMaxDynamicSharedMemorySize, lbm::kTmaSmem));
   c->ntx = (c->p.nx + lbm::kTW - 1) / lbm::kTW;
   c->nty = (c->p.ny + lbm::kTH - 1) / lbm::kTH;
@@ -483,13 +530,33 @@ lbm_status init_impl(lbm_ctx* c, const uint8_t* solid, const double* vel,
     CK(cudaMemsetAsync(c->kf, 0, plane_b, c->stream));
   }
   if (p.dissolution) {
-    CK(cudaMalloc(&c->ureact, plane_b));
-    CK(cudaMemsetAsync(c->ureact, 0, plane_b, c->stream));
+    // reaction shares: 8 bytes a node on either lattice (double, or ShareF32)
+    CK(cudaMalloc(&c->ureact, (size_t)c->plane * 8));
+    CK(cudaMemsetAsync(c->ureact, 0, (size_t)c->plane * 8, c->stream));
     CK(cudaMalloc((void**)&c->mineral, (size_t)c->plane * sizeof(double)));
     CK(cudaMemsetAsync(c->mineral, 0, (size_t)c->plane * sizeof(double), c->stream));
+    CK(cudaMalloc((void**)&c->flip_step, (size_t)c->plane * sizeof(int)));
+    CK(cudaMemsetAsync(c->flip_step, 0xFF, (size_t)c->plane * sizeof(int), c->stream));
     CK(cudaMalloc((void**)&c->flip_list, nxy * sizeof(int)));
     CK(cudaMalloc((void**)&c->slist, nxy * sizeof(int)));
     CK(cudaMalloc((void**)&c->smin, nxy * sizeof(double)));
+  }
+  {
+    // the nodes on non-periodic sides, each once (W, E, S, N order)
+    std::vector<int> open;
+    auto add = [&](int x, int y) { open.push_back((y + kYO) * c->pitch + (x + kXO)); };
+    if (!per_x)
+      for (int x : {0, p.nx - 1})
+        for (int y = 0; y < p.ny; ++y) add(x, y);
+    if (!per_y)
+      for (int y : {0, p.ny - 1})
+        for (int x = per_x ? 0 : 1; x < (per_x ? p.nx : p.nx - 1); ++x) add(x, y);
+    c->n_open = (int)open.size();
+    if (!open.empty()) {
+      CK(cudaMalloc((void**)&c->open_nodes, open.size() * sizeof(int)));
+      CK(cudaMemcpy(c->open_nodes, open.data(), open.size() * sizeof(int),
+                    cudaMemcpyHostToDevice));
+    }
   }
   CK(cudaMalloc((void**)&c->flip_count, 4 * sizeof(int)));
   CK(cudaMemsetAsync(c->flip_count, 0, 4 * sizeof(int), c->stream));
@@ -499,15 +566,22 @@ lbm_status init_impl(lbm_ctx* c, const uint8_t* solid, const double* vel,
   CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
   CK(cudaMalloc((void**)&c->edge, 3 * (size_t)c->nedge * sizeof(double)));
   CK(cudaMemsetAsync(c->edge, 0, 3 * (size_t)c->nedge * sizeof(double), c->stream));
-  if (c->esize == 4) {
-    CK(cudaMalloc((void**)&c->edge32, 3 * (size_t)c->nedge * sizeof(float)));
-    CK(cudaMemsetAsync(c->edge32, 0, 3 * (size_t)c->nedge * sizeof(float), c->stream));
-  }
   CK(cudaMalloc((void**)&c->infeasible, (size_t)c->nedge * sizeof(long long)));
   CK(cudaMemsetAsync(c->infeasible, 0, (size_t)c->nedge * sizeof(long long), c->stream));
   CK(cudaMalloc((void**)&c->jnode, (size_t)p.ny * sizeof(double)));
   CK(cudaMemsetAsync(c->jnode, 0, (size_t)p.ny * sizeof(double), c->stream));
-  CK(cudaMalloc((void**)&c->partial, (size_t)c->grid.x * c->grid.y * sizeof(double)));
+  CK(cudaMalloc((void**)&c->jflux, (size_t)p.ny * sizeof(double)));
+  CK(cudaMemsetAsync(c->jflux, 0, (size_t)p.ny * sizeof(double), c->stream));
+  {
+    // one partial per block of the generic kernel, and enough for a batch's
+    // pipelined tiles plus its boundary-warp chunks of 32 nodes
+    const long long generic = (long long)c->grid.x * c->grid.y;
+    const long long tiles = (long long)((p.nx + lbm::kTW - 1) / lbm::kTW) *
+                            ((p.ny + lbm::kTH - 1) / lbm::kTH) + (c->n_open + 31) / 32;
+    c->partial_cap = (int)((generic > tiles ? generic : tiles) + 1);
+  }
+  CK(cudaMalloc((void**)&c->partial, (size_t)c->partial_cap * sizeof(double)));
+  CK(cudaMemsetAsync(c->partial, 0, (size_t)c->partial_cap * sizeof(double), c->stream));
   CK(cudaMalloc((void**)&c->diag, sizeof(DiagDev)));
 
   // inputs: host arrays are staged through temporary device buffers
@@ -531,22 +605,27 @@ lbm_status init_impl(lbm_ctx* c, const uint8_t* solid, const double* vel,
     cleanup();
     return st;
   }
-  if (solid) {
+  if (solid) {  // the whole lattice's mask (a slab reads its neighbours' rows too)
+    const size_t mask_bytes = (size_t)p.nx * c->ny_global;
     if (on_device(solid)) {
       dsolid = const_cast<uint8_t*>(solid);
     } else {
-      cudaError_t e = cudaMalloc((void**)&dsolid, nxy);
+      cudaError_t e = cudaMalloc((void**)&dsolid, mask_bytes);
       if (e != cudaSuccess) {
         cleanup();
         return fail(LBM_ERR_NOMEM, "cudaMalloc: %s", cudaGetErrorString(e));
       }
       osolid = true;
-      cudaMemcpyAsync(dsolid, solid, nxy, cudaMemcpyHostToDevice, c->stream);
+      cudaMemcpyAsync(dsolid, solid, mask_bytes, cudaMemcpyHostToDevice, c->stream);
     }
   }
   const int g = grid1d((long long)nxy * 2);
-  k_link_in<<<grid1d((long long)nxy), 256, 0, c->stream>>>(dsolid, c->link, p.nx, p.ny,
-                                                           c->pitch, per_x, per_y);
+  {
+    const int gs = p.edge[2] == LBM_EDGE_EXCHANGE, gn = p.edge[3] == LBM_EDGE_EXCHANGE;
+    k_link_in<<<grid1d((long long)p.nx * (p.ny + 2)), 256, 0, c->stream>>>(
+        dsolid, c->link, p.nx, p.ny, c->y0, c->ny_global, c->pitch, per_x, c->per_y_global,
+        gs, gn);
+  }
   if (c->esize == 8) {
     k_pitch_in<double><<<g, 256, 0, c->stream>>>(dvel, (double*)c->vel, p.nx, p.ny, c->pitch, 2, 0.0);
     if (dk) k_pitch_in<double><<<g, 256, 0, c->stream>>>(dk, (double*)c->kf, p.nx, p.ny, c->pitch, 1, 0.0);
@@ -587,6 +666,24 @@ lbm_status check_status(lbm_ctx* c) {
   return LBM_OK;
 }
 
+// The status of a call that waited for the stream, after errors: a wall
+// Newton solve that stopped short of its tolerance since the last report is
+// LBM_ERR_NEWTON; boundary solves whose data had no non-negative solution
+// since the last report are LBM_WARN_BC_INFEASIBLE.
+lbm_status report(lbm_ctx* c, long long infeasible, long long newton_fail) {
+  const long long new_inf = infeasible - c->warned_infeasible;
+  const long long new_newton = newton_fail - c->warned_newton;
+  c->warned_infeasible = infeasible;
+  c->warned_newton = newton_fail;
+  if (new_newton > 0)
+    return fail(LBM_ERR_NEWTON, "%lld maximum-entropy wall solves stopped short of the Newton "
+                "tolerance (the last iterate was used)", new_newton);
+  if (new_inf > 0)
+    return fail(LBM_WARN_BC_INFEASIBLE, "%lld boundary solves had data with no non-negative "
+                "solution", new_inf);
+  return LBM_OK;
+}
+
 // state blob layout (all sections 256-byte aligned)
 struct Section {
   void* ptr;
@@ -600,7 +697,8 @@ int state_sections(lbm_ctx* c, Section* s) {
   s[k++] = {c->u, plane_b};
   s[k++] = {c->infeasible, (size_t)c->nedge * sizeof(long long)};
   s[k++] = {c->jnode, (size_t)c->p.ny * sizeof(double)};
-  s[k++] = {c->partial, (size_t)c->grid.x * c->grid.y * sizeof(double)};
+  s[k++] = {c->partial, (size_t)c->partial_cap * sizeof(double)};
+  s[k++] = {c->jflux, (size_t)c->p.ny * sizeof(double)};
   s[k++] = {c->counters, 4 * sizeof(long long)};
   if (c->p.dissolution) {
     const size_t nxy = (size_t)c->p.nx * c->p.ny;
@@ -608,6 +706,7 @@ int state_sections(lbm_ctx* c, Section* s) {
     s[k++] = {c->flip_count, 4 * sizeof(int)};
     s[k++] = {c->slist, nxy * sizeof(int)};
     s[k++] = {c->smin, nxy * sizeof(double)};
+    s[k++] = {c->flip_step, (size_t)c->plane * sizeof(int)};
   }
   return k;
 }
@@ -617,7 +716,7 @@ struct BlobHeader {
   long long steps;
   int nx, ny, precision, dissolution, nparts, pad;
 };
-const unsigned long long kMagic = 0x4C424D4144453034ull;  // "LBMADE04"
+const unsigned long long kMagic = 0x4C424D4144453035ull;  // "LBMADE05"
 
 // Copy a padded device field out to a caller array (host or device) of
 // `planes` [ny][nx] planes, converting to O.
@@ -666,19 +765,64 @@ lbm_status ctx_stage_edges(lbm_ctx* c, const double* ua, const double* ub, const
   else CK(cudaMemsetAsync(e + c->nedge, 0, eb, c->stream));
   if (q) CK(cudaMemcpyAsync(e + 2 * c->nedge, q, eb, kind_from(q), c->stream));
   else CK(cudaMemsetAsync(e + 2 * c->nedge, 0, eb, c->stream));
-  TRY(ctx_edges_changed(c));
   // host-sourced edge data must not be reused before the copies complete
   if ((ua && !on_device(ua)) || (b && !on_device(b)) || (q && !on_device(q)))
     CK(cudaStreamSynchronize(c->stream));
   return LBM_OK;
 }
 
-lbm_status ctx_edges_changed(lbm_ctx* c) {
-  if (!c->edge32) return LBM_OK;
-  const int n = 3 * c->nedge;
-  k_to_f32<<<(n + 255) / 256, 256, 0, c->stream>>>(c->edge, c->edge32, n);
-  CK(cudaGetLastError());
+lbm_status ctx_run_recorded(lbm_ctx* c, const lbm_ctx::GraphKey& key,
+                            lbm_status (*enqueue)(lbm_ctx*, void*), void* arg) {
+  auto it = c->graphs.find(key);
+  if (it == c->graphs.end()) {
+    if (c->seen.insert(key).second) return enqueue(c, arg);  // first sighting: run directly
+    if (!c->rec_stream) CK(cudaStreamCreateWithFlags(&c->rec_stream, cudaStreamNonBlocking));
+    // record: the launches go to the recording stream, the host bookkeeping
+    // they do is kept and applied again on every replay
+    const int cur0 = c->cur;
+    const long long steps0 = c->steps;
+    cudaStream_t user = c->stream;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(c->rec_stream, cudaStreamCaptureModeThreadLocal));
+    c->stream = c->rec_stream;
+    const lbm_status st = enqueue(c, arg);
+    c->stream = user;
+    const cudaError_t ce = cudaStreamEndCapture(c->rec_stream, &g);
+    if (st != LBM_OK || ce != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      c->cur = cur0;
+      c->steps = steps0;
+      cudaGetLastError();
+      return st != LBM_OK ? st : fail(LBM_ERR_CUDA, "graph recording: %s", cudaGetErrorString(ce));
+    }
+    cudaGraphExec_t ex = nullptr;
+    const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    c->cur = cur0;
+    c->steps = steps0;
+    if (ie != cudaSuccess) return fail(LBM_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ie));
+    it = c->graphs.emplace(key, lbm_ctx::Recorded{ex, c->nparts}).first;
+  }
+  CK(cudaGraphLaunch(it->second.exec, c->stream));
+  // the bookkeeping of the recorded sequence: n steps (key element 1)
+  const int n = std::get<1>(key);
+  c->cur ^= (n & 1);
+  c->steps += n;
+  c->nparts = it->second.nparts;
   return LBM_OK;
+}
+
+void ctx_drop_recorded(lbm_ctx* c, int kind) {
+  for (auto it = c->graphs.begin(); it != c->graphs.end();) {
+    if (std::get<0>(it->first) == kind) {
+      cudaGraphExecDestroy(it->second.exec);
+      it = c->graphs.erase(it);
+    } else {
+      ++it;
+    }
+  }
+  for (auto it = c->seen.begin(); it != c->seen.end();)
+    it = std::get<0>(*it) == kind ? c->seen.erase(it) : std::next(it);
 }
 
 template <typename Real>
@@ -698,12 +842,11 @@ int lbm_abi_version(void) { return LBM_ADE_ABI_VERSION; }
 
 const char* lbm_last_error(void) { return g_err; }
 
-lbm_status lbm_init(lbm_ctx** out, const lbm_params* p, const uint8_t* solid,
-                    const double* vel, const double* k_field, const double* mineral,
-                    const double* u0, void* stream) {
-  g_err[0] = 0;
-  if (!out || !p) return fail(LBM_ERR_ARG, "lbm_init: null out or params");
-  *out = nullptr;
+}  // extern "C"
+
+namespace {
+
+lbm_status check_params(const lbm_params* p) {
   if (p->nx < 2 || p->ny < 2) return fail(LBM_ERR_ARG, "lbm_init: nx, ny must be >= 2");
   if ((long long)lbm::padded_pitch(p->nx) * lbm::padded_rows(p->ny) > INT_MAX)
     return fail(LBM_ERR_ARG, "lbm_init: lattice too large (padded plane > INT_MAX)");
@@ -720,9 +863,39 @@ lbm_status lbm_init(lbm_ctx** out, const lbm_params* p, const uint8_t* solid,
   if (!std::isfinite(p->k_scalar)) return fail(LBM_ERR_ARG, "lbm_init: k_scalar not finite");
   if (p->dissolution && p->react_mode != LBM_REACT_SURFACE)
     return fail(LBM_ERR_ARG, "lbm_init: dissolution needs react_mode = LBM_REACT_SURFACE");
+  return LBM_OK;
+}
+
+// Rows y0 .. y1 - 1 of `planes` [ny][nx] planes of a caller array (host or
+// device) into a new device buffer; *out stays null for a null array.
+lbm_status gather_rows(const double* src, int planes, int nx, int ny, int y0, int y1,
+                       double** out, cudaStream_t st) {
+  *out = nullptr;
+  if (!src) return LBM_OK;
+  const size_t rows = (size_t)(y1 - y0) * nx;
+  CK(cudaMalloc((void**)out, planes * rows * sizeof(double)));
+  for (int k = 0; k < planes; ++k)
+    CK(cudaMemcpyAsync(*out + k * rows, src + (size_t)k * ny * nx + (size_t)y0 * nx,
+                       rows * sizeof(double), cudaMemcpyDefault, st));
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_init(lbm_ctx** out, const lbm_params* p, const uint8_t* solid,
+                    const double* vel, const double* k_field, const double* mineral,
+                    const double* u0, void* stream) {
+  g_err[0] = 0;
+  if (!out || !p) return fail(LBM_ERR_ARG, "lbm_init: null out or params");
+  *out = nullptr;
+  TRY(check_params(p));
   lbm_ctx* c = new (std::nothrow) lbm_ctx();
   if (!c) return fail(LBM_ERR_NOMEM, "lbm_init: host allocation failed");
   c->p = *p;
+  c->ny_global = p->ny;
+  c->per_y_global = p->edge[2] == LBM_EDGE_PERIODIC;
   c->stream = (cudaStream_t)stream;
   lbm_status st = init_impl(c, solid, vel, k_field, mineral, u0);
   if (st != LBM_OK) {
@@ -733,13 +906,97 @@ lbm_status lbm_init(lbm_ctx** out, const lbm_params* p, const uint8_t* solid,
   return LBM_OK;
 }
 
+lbm_status lbm_init_slab(lbm_ctx** out, const lbm_params* p, int y0, int y1,
+                         const uint8_t* solid, const double* vel, const double* k_field,
+                         const double* mineral, const double* u0, void* stream) {
+  g_err[0] = 0;
+  if (!out || !p) return fail(LBM_ERR_ARG, "lbm_init_slab: null out or params");
+  *out = nullptr;
+  TRY(check_params(p));
+  if (y0 < 0 || y1 > p->ny || y1 - y0 < 2)
+    return fail(LBM_ERR_ARG, "lbm_init_slab: need 0 <= y0, y1 <= ny, at least 2 rows");
+  const bool per_yg = p->edge[2] == LBM_EDGE_PERIODIC;
+  lbm_params q = *p;
+  q.ny = y1 - y0;
+  if (!(per_yg && y0 == 0 && y1 == p->ny)) {  // one slab of a periodic lattice stays periodic
+    q.edge[2] = (y0 == 0 && !per_yg) ? p->edge[2] : LBM_EDGE_EXCHANGE;
+    q.edge[3] = (y1 == p->ny && !per_yg) ? p->edge[3] : LBM_EDGE_EXCHANGE;
+  }
+  lbm_ctx* c = new (std::nothrow) lbm_ctx();
+  if (!c) return fail(LBM_ERR_NOMEM, "lbm_init_slab: host allocation failed");
+  c->p = q;
+  c->y0 = y0;
+  c->ny_global = p->ny;
+  c->per_y_global = per_yg;
+  c->stream = (cudaStream_t)stream;
+  double *dv = nullptr, *dk = nullptr, *dm = nullptr, *du = nullptr;
+  lbm_status st = gather_rows(vel, 2, p->nx, p->ny, y0, y1, &dv, c->stream);
+  if (st == LBM_OK) st = gather_rows(k_field, 1, p->nx, p->ny, y0, y1, &dk, c->stream);
+  if (st == LBM_OK) st = gather_rows(mineral, 1, p->nx, p->ny, y0, y1, &dm, c->stream);
+  if (st == LBM_OK) st = gather_rows(u0, 1, p->nx, p->ny, y0, y1, &du, c->stream);
+  if (st == LBM_OK) st = init_impl(c, solid, dv, dk, dm, du);
+  cudaStreamSynchronize(c->stream);
+  for (double* t : {dv, dk, dm, du})
+    if (t) cudaFree(t);
+  if (st != LBM_OK) {
+    free_ctx(c);
+    return st;
+  }
+  *out = c;
+  return LBM_OK;
+}
+
+lbm_status lbm_stage_edges(lbm_ctx* c, const double* u_dir_t0, const double* u_dir_t1,
+                           const double* q_neu) {
+  TRY(check_ctx(c));
+  return ctx_stage_edges(c, u_dir_t0, u_dir_t1, q_neu);
+}
+
+lbm_status lbm_step_stream(lbm_ctx* c, int j, int eta, int final_step) {
+  TRY(check_ctx(c));
+  if (j < 1 || eta < 1) return fail(LBM_ERR_ARG, "lbm_step_stream: need j >= 1, eta >= 1");
+  if (c->first_pass_due)
+    return fail(LBM_ERR_STATE,
+                "lbm_step_stream: the slab's first dissolution pass is due (exchange the "
+                "halo, then call lbm_step_dissolve)");
+  const double frac = (double)j / (double)eta;
+  TRY(time_begin(c, 0));
+  if (c->esize == 8) TRY(launch_step_impl<double>(c, step_args<double>(c, frac), final_step != 0));
+  else TRY(launch_step_impl<float>(c, step_args<float>(c, frac), final_step != 0));
+  TRY(time_end(c, 0));
+  c->cur ^= 1;
+  c->steps += 1;
+  return LBM_OK;
+}
+
+lbm_status lbm_step_dissolve(lbm_ctx* c) {
+  TRY(check_ctx(c));
+  if (!c->p.dissolution) return LBM_OK;
+  if (c->first_pass_due) {
+    TRY(c->esize == 8 ? first_dissolve<double>(c) : first_dissolve<float>(c));
+    c->first_pass_due = false;
+    return LBM_OK;
+  }
+  return c->esize == 8 ? launch_dissolve<double>(c) : launch_dissolve<float>(c);
+}
+
 lbm_status lbm_substeps(lbm_ctx* c, int n, int eta, const double* u_dir_t0,
                         const double* u_dir_t1, const double* q_neu) {
   TRY(check_ctx(c));
   if (n < 0 || eta < 1) return fail(LBM_ERR_ARG, "lbm_substeps: need n >= 0, eta >= 1");
+  if (c->p.edge[2] == LBM_EDGE_EXCHANGE || c->p.edge[3] == LBM_EDGE_EXCHANGE)
+    return fail(LBM_ERR_STATE,
+                "lbm_substeps: a slab steps through lbm_step_stream / lbm_step_dissolve with "
+                "its halo exchange between them");
   if (n == 0) return LBM_OK;
   TRY(ctx_stage_edges(c, u_dir_t0, u_dir_t1, q_neu));
-  return c->esize == 8 ? run_steps<double>(c, n, eta) : run_steps<float>(c, n, eta);
+  if (c->timing || n > kGraphMaxSteps)  // timing records events around every launch
+    return c->esize == 8 ? run_steps<double>(c, n, eta) : run_steps<float>(c, n, eta);
+  StepsCall call{n, eta};
+  const lbm_ctx::GraphKey key{0, n, eta, 0, c->cur, walls_variant(c), c->use_tma ? 1 : 0};
+  return ctx_run_recorded(c, key,
+                          c->esize == 8 ? enqueue_steps_call<double> : enqueue_steps_call<float>,
+                          &call);
 }
 
 lbm_status lbm_set_rate_field(lbm_ctx* c, const double* k_field) {
@@ -853,8 +1110,8 @@ lbm_status lbm_get_mineral(lbm_ctx* c, double* out) {
 lbm_status lbm_diagnostics(lbm_ctx* c, lbm_diag* out) {
   TRY(check_ctx(c));
   if (!out) return fail(LBM_ERR_ARG, "lbm_diagnostics: null out");
-  k_diag<<<1, 256, 0, c->stream>>>(c->partial, c->nparts, c->jnode, c->p.ny, c->infeasible,
-                                   c->nedge, c->diag);
+  k_diag<<<1, 256, 0, c->stream>>>(c->partial, c->nparts, c->jnode, c->jflux, c->p.ny,
+                                   c->infeasible, c->nedge, c->diag);
   CK(cudaGetLastError());
   DiagDev h;
   long long ctr[4];
@@ -862,21 +1119,36 @@ lbm_status lbm_diagnostics(lbm_ctx* c, lbm_diag* out) {
   CK(cudaMemcpyAsync(ctr, c->counters, sizeof(ctr), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   TRY(check_status(c));
+  double min_f = 0.0;
+  TRY(lbm_min_population(c, &min_f));
   out->mass = h.mass;
   out->outlet_J = h.J;
+  out->outlet_flux = h.flux;
+  out->min_f = min_f;
   out->steps = c->steps;
   out->bc_infeasible = h.infeasible + ctr[2];
+  out->newton_fail = ctr[3];
   out->flips = ctr[0];
   out->n_solid = ctr[1] - ctr[0];
-  return LBM_OK;
+  return report(c, out->bc_infeasible, out->newton_fail);
 }
 
 lbm_status lbm_set_wall_mode(lbm_ctx* c, int mode) {
   TRY(check_ctx(c));
-  if (mode != LBM_WALL_BOUNCE && mode != LBM_WALL_MAXENT)
-    return fail(LBM_ERR_ARG, "lbm_set_wall_mode: mode must be LBM_WALL_BOUNCE or LBM_WALL_MAXENT");
+  if (mode != LBM_WALL_BOUNCE && mode != LBM_WALL_MAXENT && mode != LBM_WALL_MAXENT_LATTICE)
+    return fail(LBM_ERR_ARG,
+                "lbm_set_wall_mode: mode must be LBM_WALL_BOUNCE, LBM_WALL_MAXENT or "
+                "LBM_WALL_MAXENT_LATTICE");
   c->wall_mode = mode;
   return LBM_OK;
+}
+
+lbm_status lbm_get_flip_steps(lbm_ctx* c, int32_t* out) {
+  TRY(check_ctx(c));
+  if (!out) return fail(LBM_ERR_ARG, "lbm_get_flip_steps: null out");
+  if (!c->p.dissolution) return fail(LBM_ERR_STATE, "lbm_get_flip_steps: dissolution is off");
+  TRY(field_out<int, int32_t>(c, c->flip_step, out, 1));
+  return check_status(c);
 }
 
 lbm_status lbm_state_bytes(lbm_ctx* c, size_t* bytes) {
@@ -986,7 +1258,15 @@ lbm_status lbm_set_stream(lbm_ctx* c, void* stream) {
 
 lbm_status lbm_synchronize(lbm_ctx* c) {
   TRY(check_ctx(c));
-  return check_status(c);
+  TRY(check_status(c));
+  long long ctr[4], inf = 0;
+  CK(cudaMemcpyAsync(ctr, c->counters, sizeof(ctr), cudaMemcpyDeviceToHost, c->stream));
+  std::vector<long long> per(c->nedge);
+  CK(cudaMemcpyAsync(per.data(), c->infeasible, per.size() * sizeof(long long),
+                     cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  for (long long v : per) inf += v;
+  return report(c, inf + ctr[2], ctr[3]);
 }
 
 void lbm_destroy(lbm_ctx* c) {

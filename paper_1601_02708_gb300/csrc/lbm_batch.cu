@@ -16,10 +16,12 @@
 #include <cstdarg>
 #include <cstdio>
 #include <map>
+#include <type_traits>
 #include <tuple>
 #include <vector>
 
 #include "lbm_ade.h"
+#include "lbm_batch_plain.cuh"
 #include "lbm_ctx.h"
 #include "lbm_kernels.cuh"
 
@@ -43,72 +45,12 @@ lbm_status fail(lbm_status s, const char* fmt, ...) {
                   "%s failed: %s", #call, cudaGetErrorString(e_));                \
   } while (0)
 
-constexpr int kRateBit = 1 << 29;  // tile descriptor .w: the member has a rate field
-constexpr int kTileMask = kRateBit - 1;
-
-// Tile shapes of the plain kernel: 32 columns x kBY rows of threads, each
-// thread kR rows apart.  Shape kTmaShape is the TMA-fed pipeline (FP32):
-// kTW x kTH (96 x 8) tiles, one CTA per SM.  Every shape covers at least
-// 32 x 8 nodes, so a member never has more tiles than the partial-sum slots
-// its context allocated (one per 32 x 8 block).
-struct Shape {
-  int by, r;
-};
-constexpr Shape kShapes[] = {{8, 1}, {16, 1}, {8, 2}, {4, 2}, {8, 4}, {4, 4}};
-constexpr int kPlainShapes = 6;
-constexpr int kTmaShape = kPlainShapes;
+using lbm::ArgSlot;
+constexpr int kRateBit = lbm::kBatchRateBit;
+constexpr int kTileMask = lbm::kBatchTileMask;
+constexpr int kPlainShapes = lbm::kBatchPlainShapes;
+constexpr int kTmaShape = kPlainShapes;  // the TMA-fed pipeline (FP32), 96 x 8 tiles
 constexpr int kNumShapes = kPlainShapes + 1;
-
-// Step arguments of one member, padded to whole 16-byte units so that the
-// pipelined kernel can fetch them with one bulk copy.
-template <typename Real>
-struct alignas(16) ArgSlot {
-  lbm::StepArgs<Real> a;
-};
-
-template <typename Real, bool kFinal, int kBY, int kR, bool kWalls = false>
-__global__ void __launch_bounds__(32 * kBY)
-    lbm_step_batch(const ArgSlot<Real>* __restrict__ args, const int4* __restrict__ tiles,
-                   int ntiles, double frac) {
-  static_assert(sizeof(lbm::StepArgs<Real>) % sizeof(int) == 0 &&
-                    sizeof(lbm::StepArgs<Real>) / sizeof(int) <= 32 * kBY,
-                "one thread per word of the arguments");
-  __shared__ lbm::StepArgs<Real> sa;
-  __shared__ double red[kBY];
-  const int tid = threadIdx.y * 32 + threadIdx.x;
-  int member = -1;  // whose arguments sit in sa (consecutive tiles of a block
-                    // mostly belong to the same member: reload only on change)
-  int4 next = blockIdx.x < ntiles ? tiles[blockIdx.x] : make_int4(0, 0, 0, 0);
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int4 td = next;
-    if (t + (int)gridDim.x < ntiles) next = tiles[t + gridDim.x];  // prefetch
-    if (td.x != member) {
-      __syncthreads();  // the previous tile is done with sa
-      if (tid < (int)(sizeof(sa) / sizeof(int)))
-        reinterpret_cast<int*>(&sa)[tid] = reinterpret_cast<const int*>(&args[td.x].a)[tid];
-      __syncthreads();
-      member = td.x;
-    }
-    const lbm::StepArgs<Real>& a = sa;
-    double my_u = 0.0;
-#pragma unroll
-    for (int rr = 0; rr < kR; ++rr) {
-      const int x = td.y + threadIdx.x, y = td.z + threadIdx.y + rr * kBY;
-      if (x < a.nx && y < a.ny) {
-        const long long n = (long long)(y + lbm::kYO) * a.pitch + (x + lbm::kXO);
-        lbm::GlobalSrc<Real> src{a, n};
-        if (lbm::group_is_interior(td.y, y, a.nx, a.ny))
-          my_u += lbm::step_node<Real, kFinal, false, kWalls>(a, src, x, y, n, frac);
-        else
-          my_u += lbm::step_node<Real, kFinal, true, kWalls>(a, src, x, y, n, frac);
-      }
-    }
-    if (kFinal) {
-      const double s = lbm::block_sum(my_u, red);
-      if (tid == 0) a.partial[td.w & kTileMask] = s;
-    }
-  }
-}
 
 // ---- TMA-fed variant (FP32) ---------------------------------------------
 
@@ -141,12 +83,16 @@ __device__ __forceinline__ void tensormap_acquire(const CUtensorMap* m) {
 // (one bulk copy) with the tile's boxes into the stage, and the consumers
 // take member, origin and arguments from the stage.  On the final substep
 // each tile's mass partial is summed in a fixed order by consumer warp 0
-// once the other warps have posted theirs (an mbarrier per stage).
-template <bool kFinal, bool kWalls = false>
+// once the other warps have posted theirs (an mbarrier per stage).  The
+// boundary warp steps the nodes on every member's non-periodic sides from
+// global memory (FP64 solves), in chunks of 32 nodes of one member:
+// otask[32 c + lane] = (member, padded node index or -1, partial slot, 0).
+template <bool kFinal, int kWalls = 0>
 __global__ void __launch_bounds__(lbm::kTmaBlock, 1)
     lbm_step_tma_batch(const ArgSlot<float>* __restrict__ args,
                        const MemberMaps* __restrict__ maps, int par,
-                       const int4* __restrict__ tiles, int ntiles, double frac) {
+                       const int4* __restrict__ tiles, int ntiles,
+                       const int4* __restrict__ otask, int nchunks, double frac) {
   using namespace lbm;
   constexpr int kCW = kTmaThreads / 32;  // consumer warps
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -205,6 +151,24 @@ __global__ void __launch_bounds__(lbm::kTmaBlock, 1)
           (void)mbar_wait(&full[kk % kStages], (uint32_t)((kk / kStages) & 1));
       }
     }
+  } else if (warp == kBoundaryWarp) {
+    // ---- boundary nodes of every member: FP64 solves beside the pipeline --
+    for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+      const int4 task = otask[32 * ch + lane];
+      const StepArgs<float>& a = args[task.x].a;  // one member per chunk
+      double u = 0.0;
+      if (task.y >= 0) {
+        const int n = task.y;
+        const int y = n / a.pitch - kYO, x = n - (y + kYO) * a.pitch - kXO;
+        GlobalSrc<float> src{a, n};
+        u = step_node<float, kFinal, true, true, kWalls>(a, src, x, y, n, frac);
+      }
+      if (kFinal) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) u += __shfl_down_sync(0xffffffffu, u, o);
+        if (lane == 0) a.partial[task.z] = u;
+      }
+    }
   } else {
     // ---- consumers ------------------------------------------------------
     const int cw = warp - 1;
@@ -233,9 +197,9 @@ __global__ void __launch_bounds__(lbm::kTmaBlock, 1)
         src.c = xl + 4;
         const long long n = (long long)(y + kYO) * a.pitch + (x + kXO);
         if (group_is_interior(x - lane, y, a.nx, a.ny))
-          tile_u += step_node<float, kFinal, false, kWalls>(a, src, x, y, n, frac);
-        else if (x < a.nx && y < a.ny)
-          tile_u += step_node<float, kFinal, true, kWalls>(a, src, x, y, n, frac);
+          tile_u += step_node<float, kFinal, false, false, kWalls, true>(a, src, x, y, n, frac);
+        else if (x < a.nx && y < a.ny && !on_open_side(x, y, a.nx, a.ny, a.open_mask))
+          tile_u += step_node<float, kFinal, true, false, kWalls, true>(a, src, x, y, n, frac);
       }
       if (kFinal) {
 #pragma unroll
@@ -269,20 +233,22 @@ __global__ void __launch_bounds__(lbm::kTmaBlock, 1)
 
 // Dissolution of every member's surface list: block b serves member
 // bmap[b].x as its bmap[b].y-th of nblk[member] blocks; the last block of a
-// member to finish applies that member's flips.
-template <typename Real>
+// member to finish applies that member's flips (and closes its pass).
+template <typename Share>
 __global__ void __launch_bounds__(lbm::kDThreads)
     lbm_dissolve_batch(const lbm::DissolveArgs* __restrict__ dargs,
-                       const Real* const* __restrict__ rlinks, const int2* __restrict__ bmap,
+                       const void* const* __restrict__ rlinks, const int2* __restrict__ bmap,
                        const int* __restrict__ nblk) {
   __shared__ lbm::DissolveArgs d;
   __shared__ bool last;
+  __shared__ double tab[84];
   const int tid = threadIdx.x;
   const int2 bm = bmap[blockIdx.x];
   if (tid == 0) d = dargs[bm.x];
-  __syncthreads();
-  const Real* rlink = rlinks[bm.x];
+  lbm::share_table(tab);  // synchronises the block
+  const Share* rlink = (const Share*)rlinks[bm.x];
   const int nb = nblk[bm.x];
+  const int pass = *(volatile int*)d.pass;
   bool flipped = false;
   const int count = *d.scount;
   for (int e = bm.y * lbm::kDThreads + tid; e < count; e += nb * lbm::kDThreads) {
@@ -290,15 +256,12 @@ __global__ void __launch_bounds__(lbm::kDThreads)
     const uint32_t w = d.link[n];
     if (!(w & lbm::kOwnSolid)) continue;
     if (w & lbm::kOwnPending) {
-      int x, y;
-      lbm::node_xy(d, n, x, y);
-      atomicAnd(d.link + n, ~(lbm::kOwnSolid | lbm::kOwnPending | lbm::kListed));
-      lbm::clear_in_neighbours(d, x, y, lbm::kUpSolidShift);
+      lbm::finish_flip(d, n, pass);
       continue;
     }
     const uint32_t fluid = ~((w >> lbm::kUpPostShift) | (w >> lbm::kUpOutShift)) & 0xFFu;
     if (!fluid) continue;
-    const double m = d.smin[e] - (double)lbm::mineral_take(rlink, n, d, fluid);
+    const double m = d.smin[e] - lbm::mineral_take(rlink, n, d, fluid, tab);
     d.smin[e] = m;
     if (m <= 0.0) {
       d.flip_list[lbm::dbg_idx(atomicAdd(d.flip_count, 1), (long long)d.nx * d.ny, d.status, lbm::kSiteList)] = n;
@@ -327,6 +290,11 @@ struct lbm_batch {
   int4* tiles[kNumShapes] = {};
   int ntiles[kNumShapes] = {};
   std::vector<int> member_tiles[kNumShapes];
+  // boundary-warp tasks of the pipelined shape: chunks of 32 nodes of one
+  // member on its non-periodic sides, and each member's chunk count
+  int4* otask = nullptr;
+  int nchunks = 0;
+  std::vector<int> member_chunks;
   void* args[2] = {nullptr, nullptr};  // ArgSlot<Real>[n] for fin = f[0] / f[1]
   MemberMaps* maps = nullptr;          // [n], FP32 batches whose members all have maps
   lbm::DissolveArgs* dargs = nullptr;
@@ -334,7 +302,7 @@ struct lbm_batch {
   int2* bmap = nullptr;
   int* nblk = nullptr;
   int dblocks = 0;
-  bool walls = false;  // a member had maximum-entropy pore walls when the batch was made
+  int walls = 0;  // wall variant of the members when the batch was made (walls_variant)
   std::map<std::tuple<int, int, int, int>, cudaGraphExec_t> graphs;  // (n, eta, parity, shape)
 };
 
@@ -344,7 +312,8 @@ void free_batch(lbm_batch* b) {
   for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
   for (int s = 0; s < kNumShapes; ++s)
     if (b->tiles[s]) cudaFree(b->tiles[s]);
-  void* ptrs[] = {b->args[0], b->args[1], b->maps, b->dargs, b->rlinks, b->bmap, b->nblk};
+  void* ptrs[] = {b->args[0], b->args[1], b->maps, b->dargs, b->rlinks,
+                  b->bmap,    b->nblk,    b->otask};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete b;
@@ -368,8 +337,16 @@ lbm_status upload_args(lbm_batch* b) {
   return LBM_OK;
 }
 
+template <bool kFinal, int kWalls>
+lbm_status set_tma_smem() {
+  BCK(cudaFuncSetAttribute(lbm_step_tma_batch<kFinal, kWalls>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, kBTmaSmem));
+  return LBM_OK;
+}
+
 // Tensor maps of every member for the pipelined kernel (FP32 members that
-// all carry maps); otherwise that shape stays unavailable.
+// all carry maps), and its boundary-warp tasks; otherwise that shape stays
+// unavailable.
 lbm_status upload_maps(lbm_batch* b) {
   if (b->esize != 4) return LBM_OK;
   for (lbm_ctx* c : b->m)
@@ -386,67 +363,98 @@ lbm_status upload_maps(lbm_batch* b) {
   }
   BCK(cudaMalloc((void**)&b->maps, n * sizeof(MemberMaps)));
   BCK(cudaMemcpy(b->maps, h.data(), n * sizeof(MemberMaps), cudaMemcpyHostToDevice));
-  BCK(cudaFuncSetAttribute(lbm_step_tma_batch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           kBTmaSmem));
-  BCK(cudaFuncSetAttribute(lbm_step_tma_batch<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           kBTmaSmem));
-  BCK(cudaFuncSetAttribute(lbm_step_tma_batch<true, true>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, kBTmaSmem));
-  BCK(cudaFuncSetAttribute(lbm_step_tma_batch<false, true>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, kBTmaSmem));
+  lbm_status st = LBM_OK;
+  if (st == LBM_OK) st = set_tma_smem<true, 0>();
+  if (st == LBM_OK) st = set_tma_smem<false, 0>();
+  if (st == LBM_OK) st = set_tma_smem<true, 1>();
+  if (st == LBM_OK) st = set_tma_smem<false, 1>();
+  if (st == LBM_OK) st = set_tma_smem<true, 2>();
+  if (st == LBM_OK) st = set_tma_smem<false, 2>();
+  if (st != LBM_OK) return st;
+  // boundary tasks: each member's open nodes (device list of its context)
+  // in chunks of 32, padded with -1; chunk c of member i owns partial slot
+  // member_tiles[kTmaShape][i] + c (the tile list is built before this)
+  std::vector<int4> tasks;
+  b->member_chunks.assign(n, 0);
+  for (int i = 0; i < n; ++i) {
+    lbm_ctx* c = b->m[i];
+    if (c->n_open == 0) continue;
+    std::vector<int> nodes(c->n_open);
+    BCK(cudaMemcpy(nodes.data(), c->open_nodes, nodes.size() * sizeof(int),
+                   cudaMemcpyDeviceToHost));
+    const int chunks = (c->n_open + 31) / 32;
+    for (int ch = 0; ch < chunks; ++ch) {
+      const int slot = b->member_tiles[kTmaShape][i] + ch;
+      if (slot >= c->partial_cap)
+        return fail(LBM_ERR_STATE, "lbm_batch_create: member %d has too few partial slots", i);
+      for (int l = 0; l < 32; ++l) {
+        const int e = 32 * ch + l;
+        tasks.push_back(make_int4(i, e < c->n_open ? nodes[e] : -1, slot, 0));
+      }
+    }
+    b->member_chunks[i] = chunks;
+  }
+  b->nchunks = (int)(tasks.size() / 32);
+  if (!tasks.empty()) {
+    BCK(cudaMalloc((void**)&b->otask, tasks.size() * sizeof(int4)));
+    BCK(cudaMemcpy(b->otask, tasks.data(), tasks.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  }
   return LBM_OK;
 }
 
-template <typename Real, bool kFinal, bool kWalls>
+template <typename Real, bool kFinal, int kWalls>
 void launch_step_shape(lbm_batch* b, int shape, int par, double frac) {
   if (shape == kTmaShape) {  // FP32 only (set_shape checks)
-    const int grid = b->ntiles[shape] < b->num_sms ? b->ntiles[shape] : b->num_sms;
-    lbm_step_tma_batch<kFinal, kWalls><<<grid, lbm::kTmaBlock, kBTmaSmem, b->stream>>>(
-        (const ArgSlot<float>*)b->args[par], b->maps, par, b->tiles[shape], b->ntiles[shape],
-        frac);
+    if constexpr (sizeof(Real) == 4) {
+      const int grid = b->ntiles[shape] < b->num_sms ? b->ntiles[shape] : b->num_sms;
+      lbm_step_tma_batch<kFinal, kWalls><<<grid, lbm::kTmaBlock, kBTmaSmem, b->stream>>>(
+          (const ArgSlot<float>*)b->args[par], b->maps, par, b->tiles[shape], b->ntiles[shape],
+          b->otask, b->nchunks, frac);
+    }
     return;
   }
-  const Shape sh = kShapes[shape];
   const int grid = b->ntiles[shape] < 8 * b->num_sms ? b->ntiles[shape] : 8 * b->num_sms;
-  const auto* a = (const ArgSlot<Real>*)b->args[par];
-  const dim3 block(32, sh.by);
-  const int4* tl = b->tiles[shape];
-  const int nt = b->ntiles[shape];
-  if (sh.by == 8 && sh.r == 1)
-    lbm_step_batch<Real, kFinal, 8, 1, kWalls><<<grid, block, 0, b->stream>>>(a, tl, nt, frac);
-  else if (sh.by == 16 && sh.r == 1)
-    lbm_step_batch<Real, kFinal, 16, 1, kWalls><<<grid, block, 0, b->stream>>>(a, tl, nt, frac);
-  else if (sh.by == 8 && sh.r == 2)
-    lbm_step_batch<Real, kFinal, 8, 2, kWalls><<<grid, block, 0, b->stream>>>(a, tl, nt, frac);
-  else if (sh.by == 4 && sh.r == 2)
-    lbm_step_batch<Real, kFinal, 4, 2, kWalls><<<grid, block, 0, b->stream>>>(a, tl, nt, frac);
-  else if (sh.by == 8 && sh.r == 4)
-    lbm_step_batch<Real, kFinal, 8, 4, kWalls><<<grid, block, 0, b->stream>>>(a, tl, nt, frac);
-  else
-    lbm_step_batch<Real, kFinal, 4, 4, kWalls><<<grid, block, 0, b->stream>>>(a, tl, nt, frac);
+  lbm::launch_batch_plain<Real, kFinal, kWalls>(shape, grid, b->stream,
+                                                (const ArgSlot<Real>*)b->args[par],
+                                                b->tiles[shape], b->ntiles[shape], frac);
+}
+
+template <typename Real, int kWalls>
+void launch_step_walls(lbm_batch* b, bool final_step, int shape, int par, double frac) {
+  if (final_step) launch_step_shape<Real, true, kWalls>(b, shape, par, frac);
+  else launch_step_shape<Real, false, kWalls>(b, shape, par, frac);
 }
 
 // Enqueue n steps starting at buffer parity par (no capture logic here).
 template <typename Real>
 void enqueue_steps(lbm_batch* b, int n, int eta, int par, int shape) {
+  using Share = typename std::conditional<sizeof(Real) == 8, double, lbm::ShareF32>::type;
   for (int j = 1; j <= n; ++j) {
     const double frac = (double)j / (double)eta;
-    if (b->walls) {  // some member has maximum-entropy pore walls
-      if (j == n) launch_step_shape<Real, true, true>(b, shape, par, frac);
-      else launch_step_shape<Real, false, true>(b, shape, par, frac);
+    if (b->walls == 0) {
+      launch_step_walls<Real, 0>(b, j == n, shape, par, frac);
+    } else if constexpr (sizeof(Real) == 8) {
+      launch_step_walls<Real, 1>(b, j == n, shape, par, frac);
     } else {
-      if (j == n) launch_step_shape<Real, true, false>(b, shape, par, frac);
-      else launch_step_shape<Real, false, false>(b, shape, par, frac);
+      if (b->walls == 1) launch_step_walls<Real, 1>(b, j == n, shape, par, frac);
+      else launch_step_walls<Real, 2>(b, j == n, shape, par, frac);
     }
     par ^= 1;
     if (b->dblocks > 0)
-      lbm_dissolve_batch<Real><<<b->dblocks, lbm::kDThreads, 0, b->stream>>>(
-          b->dargs, (const Real* const*)b->rlinks, b->bmap, b->nblk);
+      lbm_dissolve_batch<Share><<<b->dblocks, lbm::kDThreads, 0, b->stream>>>(
+          b->dargs, (const void* const*)b->rlinks, b->bmap, b->nblk);
   }
 }
 
 lbm_status run_batch(lbm_batch* b, int n, int eta) {
   const int par = b->m[0]->cur;
+  // the recorded graphs fix every member's buffer parity: a member stepped on
+  // its own by an odd number of steps would read the wrong buffer
+  for (size_t i = 1; i < b->m.size(); ++i)
+    if (b->m[i]->cur != par)
+      return fail(LBM_ERR_STATE,
+                  "lbm_batch: member %d was stepped outside the batch (its buffer parity "
+                  "differs from member 0's)", (int)i);
   const auto key = std::make_tuple(n, eta, par, b->shape);
   auto it = b->graphs.find(key);
   if (it == b->graphs.end()) {
@@ -472,7 +480,7 @@ lbm_status run_batch(lbm_batch* b, int n, int eta) {
     lbm_ctx* c = b->m[i];
     c->cur ^= (n & 1);
     c->steps += n;
-    c->nparts = b->member_tiles[b->shape][i];
+    c->nparts = b->member_tiles[b->shape][i] + (b->shape == kTmaShape ? b->member_chunks[i] : 0);
   }
   return LBM_OK;
 }
@@ -506,18 +514,29 @@ lbm_status lbm_batch_create(lbm_batch** out, int n, lbm_ctx* const* members) {
   b->esize = (int)members[0]->esize;
   b->stream = members[0]->stream;
   b->num_sms = members[0]->num_sms;
-  for (int i = 0; i < n; ++i) b->walls = b->walls || members[i]->wall_mode != LBM_WALL_BOUNCE;
+  for (int i = 0; i < n; ++i) {
+    const int v = walls_variant(members[i]);
+    if (v != 0 && b->walls != 0 && v != b->walls) {
+      free_batch(b);
+      return fail(LBM_ERR_ARG,
+                  "lbm_batch_create: members solve maximum-entropy walls in different "
+                  "precisions (member %d)", i);
+    }
+    if (v != 0) b->walls = v;
+  }
   lbm_status st = b->esize == 8 ? upload_args<double>(b) : upload_args<float>(b);
-  if (st == LBM_OK) st = upload_maps(b);
   if (st != LBM_OK) {
     free_batch(b);
     return st;
   }
+  bool tma_ok = b->esize == 4;
+  for (int i = 0; i < n; ++i) tma_ok = tma_ok && members[i]->tma_ready;
   // tile lists, one per shape
   for (int s = 0; s < kNumShapes; ++s) {
-    if (s == kTmaShape && !b->maps) continue;
+    if (s == kTmaShape && !tma_ok) continue;
     const int tw = s == kTmaShape ? lbm::kTW : 32;
-    const int th = s == kTmaShape ? lbm::kTH : kShapes[s].by * kShapes[s].r;
+    const int th = s == kTmaShape ? lbm::kTH
+                                  : lbm::kBatchShapes[s].by * lbm::kBatchShapes[s].r;
     std::vector<int4> h;
     b->member_tiles[s].assign(n, 0);
     for (int i = 0; i < n; ++i) {
@@ -537,6 +556,10 @@ lbm_status lbm_batch_create(lbm_batch** out, int n, lbm_ctx* const* members) {
       free_batch(b);
       return fail(LBM_ERR_CUDA, "lbm_batch_create: %s", cudaGetErrorString(e));
     }
+  }
+  if (tma_ok && (st = upload_maps(b)) != LBM_OK) {
+    free_batch(b);
+    return st;
   }
   // dissolution tables for members that dissolve: blocks in proportion to
   // their current surface-list length
@@ -589,8 +612,6 @@ lbm_status lbm_batch_substeps(lbm_batch* b, int n, int eta, const double* const*
       if (src[k]) BCK(cudaMemcpyAsync(c->edge + k * c->nedge, src[k], eb, cudaMemcpyDefault, b->stream));
       else BCK(cudaMemsetAsync(c->edge + k * c->nedge, 0, eb, b->stream));
     }
-    const lbm_status st = ctx_edges_changed(c);
-    if (st != LBM_OK) return st;
   }
   BCK(cudaStreamSynchronize(b->stream));  // host edge data may be reused after return
   return run_batch(b, n, eta);
@@ -618,8 +639,8 @@ lbm_status lbm_batch_shape_info(int shape, int* tile_w, int* tile_h, int* thread
   if (shape < 0 || shape >= kNumShapes) return fail(LBM_ERR_ARG, "lbm_batch_shape_info: shape %d", shape);
   const bool tma = shape == kTmaShape;
   if (tile_w) *tile_w = tma ? lbm::kTW : 32;
-  if (tile_h) *tile_h = tma ? lbm::kTH : kShapes[shape].by * kShapes[shape].r;
-  if (threads) *threads = tma ? lbm::kTmaBlock : 32 * kShapes[shape].by;
+  if (tile_h) *tile_h = tma ? lbm::kTH : lbm::kBatchShapes[shape].by * lbm::kBatchShapes[shape].r;
+  if (threads) *threads = tma ? lbm::kTmaBlock : 32 * lbm::kBatchShapes[shape].by;
   if (pipelined) *pipelined = tma ? 1 : 0;
   return LBM_OK;
 }

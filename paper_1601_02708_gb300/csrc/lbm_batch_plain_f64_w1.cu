@@ -1,0 +1,12 @@
+// lbm_batch_plain_f64_w1.cu -- plain batch step kernels, double lattices,
+// wall variant 1 (see lbm_batch_plain.cuh).
+#include "lbm_batch_plain_impl.cuh"
+
+namespace lbm {
+template void launch_batch_plain<double, true, 1>(int, int, cudaStream_t,
+                                                   const ArgSlot<double>*, const int4*, int,
+                                                   double);
+template void launch_batch_plain<double, false, 1>(int, int, cudaStream_t,
+                                                    const ArgSlot<double>*, const int4*, int,
+                                                    double);
+}  // namespace lbm

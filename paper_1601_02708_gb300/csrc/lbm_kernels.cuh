@@ -32,20 +32,28 @@ struct StepArgs {
   const Real* __restrict__ vel;  // [2][rows][pitch]
   const Real* __restrict__ kf;   // [rows][pitch] or null
   Real* __restrict__ u_out;      // [rows][pitch], written on the final substep
-  Real* __restrict__ ureact;     // [rows][pitch], k u / W_s at reactive nodes
+  Real* __restrict__ u_hist;     // [rows][pitch], written every step if not null
+                                 // (the adjoint's recomputation)
+  void* __restrict__ ureact;     // [rows][pitch] reaction shares at near-solid nodes
+                                 // (dissolution): FP64 lattice r = k u / W_s (double);
+                                 // FP32 lattice {u, 36 W_s} (ShareF32), r formed in FP64
   const double* __restrict__ ua;  // edge data, start of the coarse step
   const double* __restrict__ ub;  // edge data, end of the coarse step
   const double* __restrict__ q;   // Neumann data
-  const float* __restrict__ ua32;  // FP32 copies of the edge data (FP32 lattice)
-  const float* __restrict__ ub32;
-  const float* __restrict__ q32;
   long long* __restrict__ infeasible;  // per edge slot
   double* __restrict__ jnode;          // per east-edge row: sum_t u
+  double* __restrict__ jflux;          // per east-edge row: first moment sum_i f_i e_ix
+                                       // at x = nx - 1 of the last step (or null)
   double* __restrict__ partial;        // per block: sum u (final substep)
   int* __restrict__ status;            // device error word (0 = fine)
   unsigned char* __restrict__ bc_root;  // per edge slot: 1 where the Neumann root
                                         // set the unknowns this step (or null)
   long long* __restrict__ wall_infeasible;  // count of wall solves without a root
+  long long* __restrict__ newton_fail;      // count of wall solves short of the tolerance
+  const int* __restrict__ open_nodes;  // padded indices of the nodes on non-periodic
+                                       // sides (boundary warp of the tile pipeline)
+  int n_open;
+  int open_mask;    // bit s: side s (W, E, S, N) is a Dirichlet or Neumann side
   int wall_maxent;  // pore walls of the maximum-entropy kind (else bounce-back)
   long long plane;  // pitch * rows
   int nx, ny, pitch;
@@ -57,6 +65,24 @@ struct StepArgs {
   Real k_scalar;
   double frac;  // j / eta of this substep
 };
+
+// Reaction share of a near-solid node of the FP32 lattice: its concentration
+// as stored by the lattice and 36 W_s = 4 (axis links to solid) + (diagonal
+// links to solid), an integer in 1 .. 20.  The dissolution pass forms
+// k u / W_s from it in FP64.
+struct alignas(8) ShareF32 {
+  float u;
+  uint32_t w36;
+};
+
+// Whether interior node (x, y) lies on a Dirichlet or Neumann side (bit s of
+// open_mask for side W, E, S, N): its populations pulled from outside the
+// lattice are set by a boundary solve.  Periodic sides and the sides a slab
+// shares with its neighbours (exchange sides) are not open.
+__device__ __forceinline__ bool on_open_side(int x, int y, int nx, int ny, int open_mask) {
+  return ((open_mask & 1) && x == 0) || ((open_mask & 2) && x == nx - 1) ||
+         ((open_mask & 4) && y == 0) || ((open_mask & 8) && y == ny - 1);
+}
 
 // Warp + block sum of a double into one value per block (thread 0 holds it).
 __device__ __forceinline__ double block_sum(double v, double* smem) {
@@ -124,14 +150,9 @@ __device__ __forceinline__ void collide(Real (&f)[9], Real u, Real vx, Real vy,
   f[0] = rest;
 }
 
-// a / b for the reaction split: exact in FP64; the fast reciprocal-based
-// quotient in FP32 (the value only feeds the FP64 mineral sum).
-__device__ __forceinline__ double share(double a, double b) { return a / b; }
-__device__ __forceinline__ float share(float a, float b) { return __fdividef(a, b); }
-
 // Store a node value and, at nodes on a periodic side, its ghost images.
-template <typename Real>
-__device__ __forceinline__ void store_node(Real* __restrict__ base, long long n, Real v,
+template <typename T>
+__device__ __forceinline__ void store_node(T* __restrict__ base, long long n, T v,
                                            bool ghosts, int x, int y, int nx, int ny,
                                            int pitch, int per_x, int per_y,
                                            long long limit = 1ll << 62, int* flag = nullptr) {
@@ -167,15 +188,45 @@ struct GlobalSrc {
   __device__ __forceinline__ Real kf() const { return a.kf[nd()]; }
 };
 
+// Reaction share of a near-solid node, stored for the dissolution pass:
+// r = k u / W_s on the FP64 lattice; the concentration and 36 W_s on the FP32
+// lattice (the pass forms r in FP64).  `post` holds the node's links to solid
+// neighbours after this step's flips; post = 0 stores a zero share.
+template <typename Real>
+__device__ __forceinline__ void store_share(const StepArgs<Real>& a, long long n, Real kr,
+                                            Real u, uint32_t post, bool ghosts, int x, int y) {
+  const int na = __popc(post & 0x0Fu), nd = __popc(post & 0xF0u);
+  if constexpr (sizeof(Real) == 8) {
+    const double wsolid = (double)na * w_of(1) + (double)nd * w_of(5);
+    store_node((double*)a.ureact, n, post ? (double)kr * (double)u / wsolid : 0.0, ghosts, x, y,
+               a.nx, a.ny, a.pitch, a.per_x, a.per_y, a.plane, a.status);
+  } else {
+    ShareF32 v;
+    v.u = (float)u;
+    v.w36 = (uint32_t)(4 * na + nd);
+    store_node((ShareF32*)a.ureact, n, v, ghosts, x, y, a.nx, a.ny, a.pitch, a.per_x, a.per_y,
+               a.plane, a.status);
+  }
+}
+
 // One node's step.  (x, y) interior coordinates, n its padded index.  Writes
-// f* (and ghost images), ureact, jnode, u_out; returns u (0 at solid nodes)
-// for the mass reduction.
+// f* (and ghost images), ureact, jnode, jflux, u_out; returns u (0 at solid
+// nodes) for the mass reduction.
 // kEdge false: the caller guarantees the node is at least one node away
 // from every side, so no pull leaves the lattice, no ghost image exists and
 // the node is not on the outlet; the boundary code is then compiled out.
-// kWalls: the kernel may meet maximum-entropy pore walls (a.wall_maxent);
-// kernels built without it carry no wall code.
-template <typename Real, bool kFinal, bool kEdge, bool kWalls = false, class Src>
+// kSolve: the node may lie on a non-periodic side, whose populations pulled
+// from outside are set by the maximum-entropy conditions (in FP64 on either
+// lattice); callers that route those nodes elsewhere compile the solves out.
+// kWalls: 0, the kernel carries no wall code; 1, maximum-entropy pore walls
+// (when a.wall_maxent) solved in the lattice's precision; 2, solved in FP64.
+// kLight: the node's inputs are cheap to read (a shared-memory tile), so a
+// solid lane runs the fluid lanes' arithmetic on its (finite) inputs and
+// discards it: the warp takes one path and issues one set of stores, where
+// mixed solid and fluid lanes would otherwise split it in two.  Results are
+// the same either way.
+template <typename Real, bool kFinal, bool kEdge, bool kSolve, int kWalls, bool kLight = false,
+          class Src>
 __device__ __forceinline__ double step_node(const StepArgs<Real>& a, const Src& src,
                                             int x, int y, long long n, double frac) {
   const uint32_t w = src.word();
@@ -186,22 +237,23 @@ __device__ __forceinline__ double step_node(const StepArgs<Real>& a, const Src& 
   // (8 FP32 nodes, aligned since kXO = 8) holds fluid nodes writes zeros, so
   // every sector the warp touches is written whole.  A node that turns
   // fluid before this step collides (pending) gets zero populations anyway.
-  const bool solid = (w & kOwnSolid) && !(w & kOwnPending);
+  const bool own_solid = (w & kOwnSolid) != 0u;
+  const bool pending = (w & kOwnPending) != 0u;
+  const bool solid = own_solid && !pending;
   const unsigned active = __activemask();
   const unsigned fluid_lanes = __ballot_sync(active, !solid);
   const unsigned lane = threadIdx.x & 31u;
   const bool fill = ((fluid_lanes >> (lane & 24u)) & 0xFFu) != 0u;
-  if (w & kOwnSolid) {
-    if ((w & kOwnPending) || (sizeof(Real) == 4 && fill)) {
+  if (!kLight && own_solid) {
+    if (pending || (sizeof(Real) == 4 && fill)) {
 #pragma unroll
       for (int i = 0; i < 9; ++i)
         store_node(a.fout + i * a.plane, n, (Real)0, ghosts, x, y, a.nx, a.ny, a.pitch,
                    a.per_x, a.per_y, a.plane, a.status);
-      if (a.dissolution && (w & kOwnPending))
-        store_node(a.ureact, n, (Real)0, ghosts, x, y, a.nx, a.ny, a.pitch, a.per_x,
-                   a.per_y, a.plane, a.status);
+      if (a.dissolution && pending) store_share(a, n, (Real)0, (Real)0, 0u, ghosts, x, y);
     }
     if (kFinal) a.u_out[dbg_idx(n, a.plane, a.status, kSiteNode)] = (Real)0;
+    if (a.u_hist) a.u_hist[dbg_idx(n, a.plane, a.status, kSiteNode)] = (Real)0;
     return 0.0;
   }
   Real f[9];
@@ -210,39 +262,36 @@ __device__ __forceinline__ double step_node(const StepArgs<Real>& a, const Src& 
   for (int i = 1; i < 9; ++i) f[i] = src.pull_or_bounce(i, w & up_bit(kUpSolidShift, i));
   // pore walls of the maximum-entropy kind, at nodes off the open lattice
   // sides (those keep bounce-back at their solid links)
-  if (kWalls && a.wall_maxent && (w & 0xFFu) && !(w & (0xFFu << kUpOutShift)))
-    if (maxent_wall(f, (w & 0xFFu) << 1))
+  if (kWalls != 0 && a.wall_maxent && !own_solid && (w & 0xFFu) &&
+      !(w & (0xFFu << kUpOutShift))) {
+    const int r = kWalls == 2 ? maxent_wall<double>(f, (w & 0xFFu) << 1)
+                              : maxent_wall<Real>(f, (w & 0xFFu) << 1);
+    if (r == kWallNoRoot)
       atomicAdd(reinterpret_cast<unsigned long long*>(a.wall_infeasible), 1ull);
-  if (kEdge) {
+    else if (r == kWallNoConv)
+      atomicAdd(reinterpret_cast<unsigned long long*>(a.newton_fail), 1ull);
+  }
+  if (kEdge && kSolve && !own_solid) {
     const unsigned unknown = ((w >> kUpOutShift) & 0xFFu) << 1;  // bit i: direction i
     if (unknown) {
-      // Boundary node: Dirichlet wins at corners, else Neumann.
+      // Boundary node: Dirichlet wins at corners, else Neumann.  The solves
+      // run in FP64 from the FP64 edge data on either lattice; only their
+      // results are rounded to the lattice's precision.
       int dside, nside, sx, sy;
       edge_kind(a.edge, x, y, a.nx, a.ny, &dside, &nside, &sx, &sy);
       bool bad;
       int slot;
       if (dside >= 0) {
         slot = edge_slot(dside, x, y, a.nx, a.ny);
-        if constexpr (sizeof(Real) == 4) {
-          const float fr = (float)frac;
-          bad = maxent_dirichlet_f32(f, unknown, (1.f - fr) * a.ua32[slot] + fr * a.ub32[slot]);
-        } else {
-          const double up = (1.0 - frac) * a.ua[slot] + frac * a.ub[slot];
-          bad = maxent_dirichlet(f, unknown, up);
-        }
+        const double up = (1.0 - frac) * a.ua[slot] + frac * a.ub[slot];
+        bad = maxent_dirichlet(f, unknown, up);
       } else {
         slot = edge_slot(nside, x, y, a.nx, a.ny);
-        int how = -1;
-        if constexpr (sizeof(Real) == 4) {
-          if (sx == 0 || sy == 0) how = maxent_neumann_side_f32(f, unknown, sx, sy, a.q32[slot]);
-        }
-        if (how < 0) {  // FP64 lattice, or the corner of two Neumann sides
-          Real fbb[9];
+        Real fbb[9];
 #pragma unroll
-          for (int i = 0; i < 9; ++i)
-            fbb[i] = (unknown & (1u << opp_of(i))) ? src.own(i) : (Real)0;
-          how = maxent_neumann(f, unknown, sx, sy, a.q[slot], fbb);
-        }
+        for (int i = 0; i < 9; ++i)
+          fbb[i] = (unknown & (1u << opp_of(i))) ? src.own(i) : (Real)0;
+        const int how = maxent_neumann(f, unknown, sx, sy, a.q[slot], fbb);
         bad = how == kNeuInfeasible;
         if (a.bc_root) a.bc_root[slot] = how == kNeuRoot;
       }
@@ -252,6 +301,10 @@ __device__ __forceinline__ double step_node(const StepArgs<Real>& a, const Src& 
   Real u = f[0];
 #pragma unroll
   for (int i = 1; i < 9; ++i) u += f[i];
+  // the first moment through the east column (outlet flux of lbm_diagnostics)
+  if (kEdge && x == a.nx - 1 && a.jflux && !own_solid)
+    a.jflux[y] = ((double)f[1] + (double)f[5] + (double)f[8]) -
+                 ((double)f[3] + (double)f[6] + (double)f[7]);
   // links to solid neighbours after this step's flips: axis links weigh 1/9,
   // diagonal links 1/36
   const uint32_t post = (w >> kUpPostShift) & 0xFFu;
@@ -260,20 +313,27 @@ __device__ __forceinline__ double step_node(const StepArgs<Real>& a, const Src& 
   if (a.react_mode == kReactBulk || (a.react_mode == kReactSurface && near_solid))
     kr = a.kf ? src.kf() : a.k_scalar;
   collide(f, u, src.vx(), src.vy(), a.omega, kr);
+  if (kLight && own_solid) {  // a solid lane: zeros (pending), or nothing to keep
 #pragma unroll
-  for (int i = 0; i < 9; ++i)
-    store_node(a.fout + i * a.plane, n, f[i], ghosts, x, y, a.nx, a.ny, a.pitch,
-               a.per_x, a.per_y, a.plane, a.status);
-  // mass this node takes from each solid neighbour per unit link weight
-  if (a.dissolution && near_solid) {
-    const Real wsolid = (Real)__popc(post & 0x0Fu) * (Real)w_of(1) +
-                        (Real)__popc(post & 0xF0u) * (Real)w_of(5);
-    store_node(a.ureact, n, share(kr * u, wsolid), ghosts, x, y, a.nx, a.ny, a.pitch,
-               a.per_x, a.per_y, a.plane, a.status);
+    for (int i = 0; i < 9; ++i) f[i] = (Real)0;
+    u = (Real)0;
+  }
+  if (!kLight || !own_solid || pending || (sizeof(Real) == 4 && fill)) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+      store_node(a.fout + i * a.plane, n, f[i], ghosts, x, y, a.nx, a.ny, a.pitch,
+                 a.per_x, a.per_y, a.plane, a.status);
+  }
+  // what this node takes from its solid neighbours (dissolution pass); a
+  // pending node's share is zero
+  if (a.dissolution) {
+    if (kLight && pending) store_share(a, n, (Real)0, (Real)0, 0u, ghosts, x, y);
+    else if (!own_solid && near_solid) store_share(a, n, kr, u, post, ghosts, x, y);
   }
   // one node per row adds to its row's sum: a reduction without a read-back
-  if (kEdge && x == a.nx - 1) atomicAdd(a.jnode + y, (double)u);
+  if (kEdge && x == a.nx - 1 && !own_solid) atomicAdd(a.jnode + y, (double)u);
   if (kFinal) a.u_out[dbg_idx(n, a.plane, a.status, kSiteNode)] = u;
+  if (a.u_hist) a.u_hist[dbg_idx(n, a.plane, a.status, kSiteNode)] = u;
   return (double)u;
 }
 
@@ -286,9 +346,8 @@ __device__ __forceinline__ bool group_is_interior(int xs, int y, int nx, int ny)
 
 // Generic step: one thread per node, inputs from global memory.  Used in
 // FP64 mode; the FP32 path runs the TMA kernel instead.
-template <typename Real, bool kFinal, bool kWalls = false>
-__global__ void __launch_bounds__(kBX * kBY, sizeof(Real) == 4 ? 4 : 4)
-    lbm_step(const StepArgs<Real> a) {
+template <typename Real, bool kFinal, int kWalls = 0>
+__global__ void __launch_bounds__(kBX * kBY, 4) lbm_step(const StepArgs<Real> a) {
   __shared__ double red[kBX * kBY / 32];
   const int x = blockIdx.x * kBX + threadIdx.x;
   const int y = blockIdx.y * kBY + threadIdx.y;
@@ -297,9 +356,9 @@ __global__ void __launch_bounds__(kBX * kBY, sizeof(Real) == 4 ? 4 : 4)
     const long long n = (long long)(y + kYO) * a.pitch + (x + kXO);
     GlobalSrc<Real> src{a, n};
     if (group_is_interior(blockIdx.x * kBX, y, a.nx, a.ny))
-      my_u = step_node<Real, kFinal, false, kWalls>(a, src, x, y, n, a.frac);
+      my_u = step_node<Real, kFinal, false, false, kWalls>(a, src, x, y, n, a.frac);
     else
-      my_u = step_node<Real, kFinal, true, kWalls>(a, src, x, y, n, a.frac);
+      my_u = step_node<Real, kFinal, true, true, kWalls>(a, src, x, y, n, a.frac);
   }
   if (kFinal) {
     const double s = block_sum(my_u, red);
@@ -332,8 +391,6 @@ __global__ void __launch_bounds__(kBX * kBY)
       equilibrium(f, u, vx, vy);
       const uint32_t post = (w >> kUpPostShift) & 0xFFu;
       const bool near_solid = post != 0u;
-      const Real wsolid = (Real)__popc(post & 0x0Fu) * (Real)w_of(1) +
-                          (Real)__popc(post & 0xF0u) * (Real)w_of(5);
       Real kr = (Real)0;
       if (a.react_mode == kReactBulk || (a.react_mode == kReactSurface && near_solid))
         kr = a.kf ? a.kf[n] : a.k_scalar;
@@ -342,9 +399,7 @@ __global__ void __launch_bounds__(kBX * kBY)
       for (int i = 0; i < 9; ++i)
         store_node(a.fout + i * a.plane, n, f[i], ghosts, x, y, a.nx, a.ny, a.pitch,
                    a.per_x, a.per_y, a.plane, a.status);
-      if (a.dissolution && near_solid)
-        store_node(a.ureact, n, kr * u / wsolid, ghosts, x, y, a.nx, a.ny, a.pitch,
-                   a.per_x, a.per_y, a.plane, a.status);
+      if (a.dissolution && near_solid) store_share(a, n, kr, u, post, ghosts, x, y);
       a.u_out[n] = u;
       my_u = (double)u;
     }
@@ -363,8 +418,12 @@ struct DissolveArgs {
   int* flip_list;        // padded indices of nodes found exhausted this pass
   int* flip_count;
   unsigned* done;
+  int* pass;             // passes run so far (the first, after initialisation, is 0)
+  int* flip_step;        // [rows][pitch]: pass that turned the node fluid, -1 if none
   long long* flips_total;
   int* status;    // the context's status word (index checks of the debug build)
+  const float* kf32;  // FP32 lattice with a rate field: k per node (else null)
+  double k_scalar;    // FP32 lattice without a rate field: k
   int nx, ny, pitch, per_x, per_y;
   int check_all;  // also flip untouched solid nodes whose mineral is <= 0
 };
@@ -400,29 +459,104 @@ __device__ __forceinline__ void clear_in_neighbours(const DissolveArgs& d, int x
   }
 }
 
-// Mineral lost by solid node n this step (word w): sum over its fluid
-// (after this step's flips) in-lattice neighbours s = y - e_j of w_j r(s),
-// r(s) = k(s) u(s) / W_s(s) stored by the step.  Summed in the working
-// precision in a fixed order; FP64 throughput is scarce and the result only
-// enters the FP64 mineral.
-template <typename Real>
-__device__ __forceinline__ Real mineral_take(const Real* __restrict__ rlink, long long n,
-                                             const DissolveArgs& d, uint32_t fluid) {
+// A pending node (found exhausted by the previous pass, fluid since this
+// step's collision) becomes plain fluid: it stops being solid upstream for
+// its neighbours, and the pass that turned it fluid is recorded.
+__device__ __forceinline__ void finish_flip(const DissolveArgs& d, int n, int pass) {
+  int x, y;
+  node_xy(d, n, x, y);
+  atomicAnd(d.link + n, ~(kOwnSolid | kOwnPending | kListed));
+  clear_in_neighbours(d, x, y, kUpSolidShift);
+  if (d.flip_step) d.flip_step[n] = pass;
+}
+
+// Mineral lost by solid node n this step (word w): sum over its fluid (after
+// this step's flips) in-lattice neighbours s = y - e_j of w_j r(s),
+// r(s) = k(s) u(s) / W_s(s), in FP64 and a fixed order.
+// FP64 lattice: r(s) was stored by the step.
+__device__ __forceinline__ double mineral_take(const double* __restrict__ r, long long n,
+                                               const DissolveArgs& d, uint32_t fluid,
+                                               const double*) {
   const long long plane = (long long)d.pitch * padded_rows(d.ny);
-  Real take = (Real)0;
+  double take = 0.0;
 #pragma unroll
   for (int j = 1; j < 9; ++j)
     if (fluid & (1u << (j - 1)))
-      take += (Real)w_of(j) *
-              rlink[dbg_idx(n - cx_of(j) - (long long)cy_of(j) * d.pitch, plane, d.status,
-                            kSiteShare)];
+      take += w_of(j) * r[dbg_idx(n - cx_of(j) - (long long)cy_of(j) * d.pitch, plane,
+                                  d.status, kSiteShare)];
   return take;
+}
+// FP32 lattice: the step stored u(s) and c = 36 W_s(s); with T[t][c] = 36 w_t / c
+// (t = 0 axis, 1 diagonal direction) w_j r(s) = k(s) u(s) T[t_j][c].  GB300
+// runs FP64 at 1/64 of the FP32 rate, so the terms and their sum are formed
+// in double-float arithmetic on the FP32 pipe -- T as an unevaluated float
+// pair, each product by Dekker's splitting with a fused multiply-add, the
+// sum by Knuth's two-sum -- carrying about 48 significant bits (relative
+// error near 1e-14), and only the final sum is converted and scaled by k in
+// FP64.  With a rate field each term is scaled in FP64.
+struct F2 {
+  float hi, lo;
+};
+__device__ __forceinline__ void two_sum_add(float& s, float& e, float a) {
+  const float t = s + a;
+  const float bp = t - s;
+  e += (s - (t - bp)) + (a - bp);
+  s = t;
+}
+__device__ __forceinline__ double mineral_take(const ShareF32* __restrict__ sh, long long n,
+                                               const DissolveArgs& d, uint32_t fluid,
+                                               const double* tab) {
+  const long long plane = (long long)d.pitch * padded_rows(d.ny);
+  const F2* tf = reinterpret_cast<const F2*>(tab + 42);  // the float pairs of T
+  if (d.kf32) {
+    double take = 0.0;
+#pragma unroll
+    for (int j = 1; j < 9; ++j)
+      if (fluid & (1u << (j - 1))) {
+        const long long s = dbg_idx(n - cx_of(j) - (long long)cy_of(j) * d.pitch, plane,
+                                    d.status, kSiteShare);
+        const ShareF32 v = sh[s];
+        take += (double)v.u * tab[(j >= 5 ? 21 : 0) + (int)dbg_idx(v.w36, 21, d.status, kSiteShare)] *
+                (double)d.kf32[s];
+      }
+    return take;
+  }
+  float S = 0.f, E = 0.f;
+#pragma unroll
+  for (int j = 1; j < 9; ++j)
+    if (fluid & (1u << (j - 1))) {
+      const long long s = dbg_idx(n - cx_of(j) - (long long)cy_of(j) * d.pitch, plane,
+                                  d.status, kSiteShare);
+      const ShareF32 v = sh[s];
+      const F2 t = tf[(j >= 5 ? 21 : 0) + (int)dbg_idx(v.w36, 21, d.status, kSiteShare)];
+      const float p = v.u * t.hi;
+      const float err = fmaf(v.u, t.hi, -p) + v.u * t.lo;  // u T - p, to ~2^-48 of u T
+      two_sum_add(S, E, p);
+      E += err;
+    }
+  return ((double)S + (double)E) * d.k_scalar;
+}
+
+// The tables of mineral_take for the FP32 lattice, in shared memory:
+// tab[t][c] = 36 w_t / c in FP64 (36 w_t = 4 axis, 1 diagonal; tab[t][0] = 0),
+// then the same 42 values as float pairs hi + lo (hi the float nearest, lo
+// the float nearest the remainder).  84 doubles of storage.
+__device__ __forceinline__ void share_table(double* tab) {
+  F2* tf = reinterpret_cast<F2*>(tab + 42);
+  for (int i = threadIdx.x; i < 42; i += blockDim.x) {
+    const int c = i % 21;
+    const double v = c == 0 ? 0.0 : (i < 21 ? 4.0 : 1.0) / (double)c;
+    tab[i] = v;
+    const float hi = (float)v;
+    tf[i] = F2{hi, (float)(v - (double)hi)};
+  }
+  __syncthreads();
 }
 
 // Mark every node of the flip list pending (solid for the next streaming,
 // fluid for its collision), tell its neighbours through their post-flip bits,
 // and put solid neighbours it exposes on the surface list.  Run by one block
-// after every node has been examined.
+// after every node has been examined; it closes the pass.
 __device__ inline void apply_flips(const DissolveArgs& d, int tid, int nthreads) {
   __threadfence();
   const int cnt = *((volatile int*)d.flip_count);
@@ -450,6 +584,7 @@ __device__ inline void apply_flips(const DissolveArgs& d, int tid, int nthreads)
     *d.flips_total += cnt;
     *d.flip_count = 0;
     *d.done = 0u;
+    *d.pass += 1;
   }
 }
 
@@ -460,12 +595,16 @@ __device__ inline void apply_flips(const DissolveArgs& d, int tid, int nthreads)
 // collected and, by the last block to finish, marked pending (apply_flips).
 // Link-word edits are atomic bit operations on bits no concurrent reader of
 // the same word depends on, so the result is independent of timing.
+// Share is double (FP64 lattice) or ShareF32 (FP32 lattice).
 constexpr int kDThreads = 256;
 
-template <typename Real>
+template <typename Share>
 __global__ void __launch_bounds__(kDThreads)
-    lbm_dissolve_list(const DissolveArgs d, const Real* __restrict__ rlink) {
+    lbm_dissolve_list(const DissolveArgs d, const Share* __restrict__ rlink) {
+  __shared__ double tab[84];
+  share_table(tab);
   const int tid = threadIdx.x;
+  const int pass = *(volatile int*)d.pass;
   bool flipped = false;
   const int count = *d.scount;
   for (int e = blockIdx.x * kDThreads + tid; e < count; e += gridDim.x * kDThreads) {
@@ -473,15 +612,12 @@ __global__ void __launch_bounds__(kDThreads)
     const uint32_t w = d.link[n];
     if (!(w & kOwnSolid)) continue;  // dissolved earlier
     if (w & kOwnPending) {
-      int x, y;
-      node_xy(d, n, x, y);
-      atomicAnd(d.link + n, ~(kOwnSolid | kOwnPending | kListed));
-      clear_in_neighbours(d, x, y, kUpSolidShift);
+      finish_flip(d, n, pass);
       continue;
     }
     const uint32_t fluid = ~((w >> kUpPostShift) | (w >> kUpOutShift)) & 0xFFu;
     if (!fluid) continue;
-    const double m = d.smin[e] - (double)mineral_take(rlink, n, d, fluid);
+    const double m = d.smin[e] - mineral_take(rlink, n, d, fluid, tab);
     d.smin[e] = m;
     if (m <= 0.0) {
       d.flip_list[dbg_idx(atomicAdd(d.flip_count, 1), (long long)d.nx * d.ny, d.status, kSiteList)] = n;
@@ -502,10 +638,13 @@ __global__ void __launch_bounds__(kDThreads)
 // Dissolution pass over every node (used once, after initialisation): the
 // same update as lbm_dissolve_list for surface nodes, and with check_all set
 // it also flips solid nodes given no mineral.  The mineral is the dense array.
-template <typename Real>
+template <typename Share>
 __global__ void __launch_bounds__(kDThreads)
-    lbm_dissolve_dense(const DissolveArgs d, const Real* __restrict__ rlink) {
+    lbm_dissolve_dense(const DissolveArgs d, const Share* __restrict__ rlink) {
+  __shared__ double tab[84];
+  share_table(tab);
   const int tid = threadIdx.x;
+  const int pass = *(volatile int*)d.pass;
   bool flipped = false;
   const long long total = (long long)d.nx * d.ny;
   for (long long id = blockIdx.x * (long long)kDThreads + tid; id < total;
@@ -515,13 +654,12 @@ __global__ void __launch_bounds__(kDThreads)
     const uint32_t w = d.link[n];
     if (!(w & kOwnSolid)) continue;
     if (w & kOwnPending) {
-      atomicAnd(d.link + n, ~(kOwnSolid | kOwnPending | kListed));
-      clear_in_neighbours(d, x, y, kUpSolidShift);
+      finish_flip(d, n, pass);
       continue;
     }
     const uint32_t fluid = ~((w >> kUpPostShift) | (w >> kUpOutShift)) & 0xFFu;
     if (!fluid && !d.check_all) continue;
-    const double m = d.mineral[n] - (double)mineral_take(rlink, n, d, fluid);
+    const double m = d.mineral[n] - mineral_take(rlink, n, d, fluid, tab);
     if (fluid) d.mineral[n] = m;
     if (m <= 0.0) {
       d.flip_list[dbg_idx(atomicAdd(d.flip_count, 1), (long long)d.nx * d.ny, d.status, kSiteList)] = n;

@@ -103,7 +103,9 @@ __device__ __forceinline__ void for_each_ghost(int x, int y, int nx, int ny, int
     }
 }
 
-enum { kPeriodic = 0, kDirichlet = 1, kNeumann = 2 };
+// Side kinds (lbm_edge_kind); kExchange: a side a slab shares with its
+// neighbour in a split lattice (its ghost row is filled by the halo exchange).
+enum { kPeriodic = 0, kDirichlet = 1, kNeumann = 2, kExchange = 3 };
 enum { kReactNone = 0, kReactSurface = 1, kReactBulk = 2 };
 
 
@@ -194,60 +196,15 @@ __device__ int maxent_neumann(Real (&f)[9], unsigned unknown, int sx, int sy,
   return kNeuRoot;
 }
 
-// 1 / W_U for an unknown set of na axis and nd diagonal directions:
-// W_U = na / 9 + nd / 36 = (4 na + nd) / 36, so 1 / W_U = 36 / (4 na + nd).
-static __constant__ float kInvWeight36[21] = {
-    0.f,        36.f,        18.f,        12.f,        9.f,         36.f / 5.f,  6.f,
-    36.f / 7.f, 36.f / 8.f,  4.f,         36.f / 10.f, 36.f / 11.f, 3.f,         36.f / 13.f,
-    36.f / 14.f, 36.f / 15.f, 36.f / 16.f, 36.f / 17.f, 2.f,         36.f / 19.f, 36.f / 20.f};
-__device__ __forceinline__ float inv_weight_sum(unsigned unknown) {
-  return kInvWeight36[4 * __popc(unknown & 0x1Eu) + __popc(unknown & 0x1E0u)];
-}
-
-// FP32 forms of the two side solutions, for the FP32 lattice: the same closed
-// forms (f proportional to w over the unknowns, Sec. 4.1.1 (a) and, on a
-// straight side, (b)) evaluated in the lattice's own precision.
-__device__ __forceinline__ bool maxent_dirichlet_f32(float (&f)[9], unsigned unknown, float up) {
-  float known = 0.f;
-#pragma unroll
-  for (int i = 0; i < 9; ++i)
-    if (!(unknown & (1u << i))) known += f[i];
-  const float rest = up - known;
-  const float scale = rest * inv_weight_sum(unknown);
-#pragma unroll
-  for (int i = 0; i < 9; ++i)
-    if (unknown & (1u << i)) f[i] = (float)w_of(i) * scale;
-  return rest < 0.f;
-}
-// Straight side with outward normal (sx, sy), one of them zero: every unknown
-// has e.n = -1 and S = sum_{e.n = 1} f - q.
-__device__ __forceinline__ int maxent_neumann_side_f32(float (&f)[9], unsigned unknown, int sx,
-                                                       int sy, float q) {
-  float S = -q;
-#pragma unroll
-  for (int i = 1; i < 9; ++i)
-    if (!(unknown & (1u << i)) && cx_of(i) * sx + cy_of(i) * sy == 1) S += f[i];
-  if (!(S > 0.f)) {
-#pragma unroll
-    for (int i = 1; i < 9; ++i)
-      if (unknown & (1u << i)) f[i] = 0.f;
-    return S < 0.f ? kNeuInfeasible : kNeuZero;
-  }
-  const float scale = S * inv_weight_sum(unknown);
-#pragma unroll
-  for (int i = 1; i < 9; ++i)
-    if (unknown & (1u << i)) f[i] = (float)w_of(i) * scale;
-  return kNeuRoot;
-}
-
 // Boundary kind of an edge node (x, y) whose unknown set is not empty:
 // Dirichlet wins at corners (*dside >= 0, the first Dirichlet side), else
 // Neumann (*nside, the first Neumann side, with the outward normal (sx, sy)
 // summed over the node's Neumann sides).
 __device__ __forceinline__ void edge_kind(const int (&edge)[4], int x, int y, int nx, int ny,
                                           int* dside, int* nside, int* sx, int* sy) {
-  const bool on[4] = {x == 0 && edge[0] != kPeriodic, x == nx - 1 && edge[1] != kPeriodic,
-                      y == 0 && edge[2] != kPeriodic, y == ny - 1 && edge[3] != kPeriodic};
+  auto bc = [&](int s) { return edge[s] == kDirichlet || edge[s] == kNeumann; };
+  const bool on[4] = {x == 0 && bc(0), x == nx - 1 && bc(1), y == 0 && bc(2),
+                      y == ny - 1 && bc(3)};
   *dside = -1;
   *nside = -1;
   *sx = 0;
@@ -270,7 +227,7 @@ __device__ __forceinline__ void edge_kind(const int (&edge)[4], int x, int y, in
 // in those directions.  The outward normal is the lattice-weighted direction
 // to the solid neighbours, n = -sum_{i in solid} w_i e_i, normalised (where it
 // cancels, as in a one-node channel, bounce-back stays throughout; which
-// unknowns are tangent is decided on 36 n, an integer vector).  Unknowns
+// unknowns are tangent to it is decided on 36 n, an integer vector).  Unknowns
 // with e_i.n >= 0 keep bounce-back; the others become
 // w_i exp(-1 - gamma e_i.n) with gamma making sum_i f_i e_i.n zero.  With
 // a_i = e_i.n < 0 the flux of those unknowns is -L(gamma),
@@ -278,10 +235,16 @@ __device__ __forceinline__ void edge_kind(const int (&edge)[4], int x, int y, in
 // log L(gamma) = log(-R), R = -sum_{others} a_j f_j; log L is convex and
 // increasing with slope between the smallest and largest |a_i|, so Newton's
 // method converges from any start (in one step when every |a_i| is equal, as
-// on a flat wall).  Returns true if R > 0 (no root: those unknowns are set to
-// zero, the gamma -> -infinity limit).
-template <typename Real>
-__device__ bool maxent_wall(Real (&f)[9], unsigned solid) {
+// on a flat wall).
+// S is the precision of the solve (the Lagrange multiplier, the normal, the
+// fluxes and the exponentials); the lattice's populations f are read and
+// written in their own precision Real.  Returns kWallSet, kWallNoRoot if
+// R > 0 (no root: those unknowns are set to zero, the gamma -> -infinity
+// limit) or kWallNoConv if Newton's method stopped short of its tolerance
+// (the last iterate is used).
+enum { kWallSet = 0, kWallNoRoot = 1, kWallNoConv = 2 };
+template <typename S, typename Real>
+__device__ int maxent_wall(Real (&f)[9], unsigned solid) {
   // the normal scaled by 36 (the weights are 4/36 and 1/36): integers, so
   // which unknowns are tangent to it, and whether it cancels, is exact
   int mx = 0, my = 0;
@@ -292,61 +255,71 @@ __device__ bool maxent_wall(Real (&f)[9], unsigned solid) {
       mx -= w36 * cx_of(i);
       my -= w36 * cy_of(i);
     }
-  if (mx == 0 && my == 0) return false;
-  const Real inv = (Real)1 / sqrt((Real)(mx * mx + my * my));
-  const Real nx = (Real)mx * inv, ny = (Real)my * inv;
-  Real a[9], R = (Real)0, s1 = (Real)0, s2 = (Real)0;
+  if (mx == 0 && my == 0) return kWallSet;
+  const S inv = (S)1 / sqrt((S)(mx * mx + my * my));
+  const S nx = (S)mx * inv, ny = (S)my * inv;
+  S a[9], R = (S)0, s1 = (S)0, s2 = (S)0;
   unsigned neg = 0u;
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
-    a[i] = (Real)cx_of(i) * nx + (Real)cy_of(i) * ny;
+    a[i] = (S)cx_of(i) * nx + (S)cy_of(i) * ny;
     if (((solid >> i) & 1u) && cx_of(i) * mx + cy_of(i) * my < 0) {
       neg |= 1u << i;
-      s1 -= (Real)w_of(i) * a[i];
-      s2 += (Real)w_of(i) * a[i] * a[i];
+      s1 -= (S)w_of(i) * a[i];
+      s2 += (S)w_of(i) * a[i] * a[i];
     } else {
-      R -= a[i] * f[i];
+      R -= a[i] * (S)f[i];
     }
   }
-  if (!neg) return false;
-  if (!(R < (Real)0)) {
+  if (!neg) return kWallSet;
+  if (!(R < (S)0)) {
 #pragma unroll
     for (int i = 0; i < 9; ++i)
       if (neg & (1u << i)) f[i] = (Real)0;
-    return R > (Real)0;
+    return R > (S)0 ? kWallNoRoot : kWallSet;
   }
-  if (sizeof(Real) == 4 && -R < (Real)1e-30) {
+  if (sizeof(S) == 4 && -R < (S)1e-30) {
     // far below FP32's normal range the exponentials would underflow: the
     // flux-conserving split w_i (-R) / sum w |a| meets the constraint exactly
     // and differs from the maximum-entropy values by less than 1e-30
 #pragma unroll
     for (int i = 0; i < 9; ++i)
-      if (neg & (1u << i)) f[i] = (Real)w_of(i) * (-R / s1);
-    return false;
+      if (neg & (1u << i)) f[i] = (Real)((S)w_of(i) * (-R / s1));
+    return kWallSet;
   }
-  constexpr int kIters = sizeof(Real) == 8 ? 60 : 24;
-  const Real tol = sizeof(Real) == 8 ? (Real)1e-15 : (Real)1e-7;
-  const Real logR = log(-R);
+  // tolerance on the relative Newton step: a few units of the solve's
+  // rounding (FP64 2.2e-16, FP32 1.2e-7)
+  constexpr int kIters = sizeof(S) == 8 ? 60 : 24;
+  const S tol = sizeof(S) == 8 ? (S)1e-15 : (S)5e-7;
+  const S logR = log(-R);
   // start: the root if every |a_i| were their weighted mean s2 / s1
-  Real g = (logR - log(s1) + (Real)1) * (s1 / s2);
+  S g = (logR - log(s1) + (S)1) * (s1 / s2);
+  bool conv = false;
+  S last = (S)0;
   for (int it = 0; it < kIters; ++it) {
-    Real L = (Real)0, dL = (Real)0;
+    S L = (S)0, dL = (S)0;
 #pragma unroll
     for (int i = 0; i < 9; ++i)
       if (neg & (1u << i)) {
-        const Real e = (Real)w_of(i) * exp(g * -a[i] - (Real)1);
+        const S e = (S)w_of(i) * exp(g * -a[i] - (S)1);
         L -= a[i] * e;
         dL += a[i] * a[i] * e;
       }
-    if (!(dL > (Real)0)) break;
-    const Real step = (log(L) - logR) * (L / dL);
+    if (!(dL > (S)0)) break;
+    const S step = (log(L) - logR) * (L / dL);
     g -= step;
-    if (fabs(step) <= tol * ((Real)1 + fabs(g))) break;
+    last = step;
+    if (fabs(step) <= tol * ((S)1 + fabs(g))) {
+      conv = true;
+      break;
+    }
   }
+  // an iteration that ended oscillating at its rounding level has converged
+  if (!conv && fabs(last) <= (S)16 * tol * ((S)1 + fabs(g))) conv = true;
 #pragma unroll
   for (int i = 0; i < 9; ++i)
-    if (neg & (1u << i)) f[i] = (Real)w_of(i) * exp(g * -a[i] - (Real)1);
-  return false;
+    if (neg & (1u << i)) f[i] = (Real)((S)w_of(i) * exp(g * -a[i] - (S)1));
+  return conv ? kWallSet : kWallNoConv;
 }
 
 }  // namespace lbm

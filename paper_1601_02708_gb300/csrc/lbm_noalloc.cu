@@ -3,11 +3,12 @@
 //
 // The library's own mass sum (lbm_diagnostics) folds per-block partials that
 // live in memory the library allocated for the context.  Some callers cannot
-// allocate at the time they need the sum: code recording a CUDA graph (an
-// allocation is not a capturable operation), code that works inside a
-// memory budget fixed at start-up, or a host framework that owns every
-// device allocation itself.  This entry point takes the concentration field
-// from the caller and keeps its partials in a fixed file-scope device array.
+// allocate at the time they need the sum: code that works inside a device
+// memory budget fixed at start-up (every byte is spoken for, so a new
+// allocation can fail at any later point), or a host framework that owns
+// every device allocation itself and forbids libraries to call cudaMalloc.
+// This entry point takes the concentration field from the caller and keeps
+// its partials in a fixed file-scope device array.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -126,12 +127,24 @@ lbm_status lbm_mass_noalloc(const void* u, int precision, long long n, double* m
   const lbm_status st = scratch_for(dev, &scratch);
   if (st != LBM_OK) return st;
   const cudaStream_t s = (cudaStream_t)stream;
+  const bool out_dev = is_device(mass_out);
+  if (!out_dev) {
+    // a host result needs a copy back and a wait for the stream; a stream in
+    // capture mode allows no wait, so the call refuses instead of failing in
+    // the middle
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cap);
+    if (e != cudaSuccess) return fail(LBM_ERR_CUDA, "lbm_mass_noalloc: cudaStreamIsCapturing failed");
+    if (cap != cudaStreamCaptureStatusNone)
+      return fail(LBM_ERR_ARG,
+                  "lbm_mass_noalloc: mass_out must be device memory while the stream is "
+                  "being captured");
+  }
   const int nblocks = (int)((n + kChunk - 1) / kChunk);
   if (precision == 64)
     mass_partials<double><<<nblocks, kThreads, 0, s>>>((const double*)u, n, scratch);
   else
     mass_partials<float><<<nblocks, kThreads, 0, s>>>((const float*)u, n, scratch);
-  const bool out_dev = is_device(mass_out);
   double* dst = out_dev ? mass_out : scratch + kMaxBlocks;
   mass_fold<<<1, kThreads, 0, s>>>(scratch, nblocks, dst);
   e = cudaGetLastError();

@@ -9,9 +9,12 @@
 // fourth from shared memory with step_node(), which is shared with the
 // generic kernel, and store f* with coalesced row writes.  (The update is
 // bound by the consumers' instruction latency, so the tile is sized for as
-// many consumer warps as the register file holds.)  Every wait on an
-// mbarrier has an iteration limit: on expiry the CTA records a status,
-// drains its copies in flight (again with a limit) and returns.
+// many consumer warps as the register file holds.)  The nodes on
+// non-periodic sides, whose boundary solves run in FP64 (slow on this part),
+// are left to one boundary warp per CTA that reads them from global memory
+// beside the pipeline, so no consumer warp waits on the FP64 pipe.  Every
+// wait on an mbarrier has an iteration limit: on expiry the CTA records a
+// status, drains its copies in flight (again with a limit) and returns.
 #pragma once
 #include <cuda.h>
 
@@ -24,13 +27,19 @@ constexpr int kTH = 8;             // tile height (rows)
 constexpr int kBoxW = kTW + 8;     // halo box width: 4 columns each side (16 B aligned)
 constexpr int kBoxH = kTH + 2;     // halo box height: one row each side
 constexpr int kStages = 4;
-constexpr int kTmaThreads = 768;   // consumer threads: 24 warps (plus one producer warp)
-constexpr int kTmaBlock = kTmaThreads + 32;
+constexpr int kTmaThreads = 768;   // consumer threads: 24 warps
+constexpr int kTmaBlock = kTmaThreads + 64;  // plus one producer and one boundary warp
+constexpr int kBoundaryWarp = kTmaThreads / 32 + 1;
 constexpr int kWarpsPerRow = (kTmaThreads / 32) / kTH;    // consumer warps sharing a tile row
 constexpr int kNodesPerLane = kTW / (32 * kWarpsPerRow);  // nodes of a row per lane
 static_assert((kTmaThreads / 32) % kTH == 0 && kNodesPerLane * 32 * kWarpsPerRow == kTW,
               "tile mapping");
-constexpr long long kSpinLimit = 1ll << 24;
+// Bounded waits: a wait on an mbarrier gives up after kWaitLimitNs of
+// wall-clock time (the kernel then records a status and returns); each poll
+// lets the hardware suspend the warp for up to kSuspendNs until the phase
+// completes, so a waiting warp issues a handful of instructions, not a spin.
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
+constexpr unsigned kSuspendNs = 100000u;                     // 100 us per poll
 
 constexpr int round128(int b) { return (b + 127) / 128 * 128; }
 constexpr int kPopBytes = 9 * kBoxH * kBoxW * 4;
@@ -60,18 +69,25 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
+      : "r"(smem_addr(bar)), "r"(parity), "r"(kSuspendNs)
       : "memory");
   return ok != 0;
 }
-// Bounded wait; false if the phase did not complete within kSpinLimit polls.
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait; false if the phase did not complete within kWaitLimitNs.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (long long i = 0; i < kSpinLimit; ++i)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (global_ns() - t0 > kWaitLimitNs) return false;
+  return true;
 }
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0,
                                             int c1, int c2, uint64_t* bar) {
@@ -146,15 +162,17 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // Warp-specialised pipeline: warp 0 is the producer (one lane issues the TMA
 // boxes of tile k into stage k % kStages once all consumer warps have
 // released that stage), warps 1..24 are consumers (each updates a third of
-// one tile row and releases the stage with one arrival).  No CTA-wide
-// barrier sits inside the tile loop.
-template <bool kFinal, bool kWalls = false>
+// one tile row and releases the stage with one arrival), warp 25 steps the
+// CTA's share of the nodes on non-periodic sides from global memory.  No
+// CTA-wide barrier sits inside the tile loop.
+template <bool kFinal, int kWalls = 0>
 __global__ void __launch_bounds__(kTmaBlock, 1)
     lbm_step_tma(const StepArgs<float> a, const __grid_constant__ TmaMaps maps, int ntx,
                  int nty) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[kStages];
   __shared__ __align__(8) uint64_t empty[kStages];
+  __shared__ int2 origin[kStages];  // tile origin of each stage, set by the producer
   __shared__ double red[kTmaBlock / 32];
   __shared__ int abort_flag;
   const int tid = threadIdx.x;
@@ -187,6 +205,7 @@ __global__ void __launch_bounds__(kTmaBlock, 1)
         if (*(volatile int*)&abort_flag) break;
         unsigned char* st = smem + s * kStageBytes;
         const int x0 = (t % ntx) * kTW, y0 = (t / ntx) * kTH;
+        origin[s] = make_int2(x0, y0);  // published by the arrival below
         mbar_expect_tx(&full[s], bytes);
         tma_load_3d(st, &maps.pop, x0 + kXO - 4, y0, 0, &full[s]);
         tma_load_3d(st + kOffVel, &maps.vel, x0 + kXO, y0 + kYO, 0, &full[s]);
@@ -197,6 +216,18 @@ __global__ void __launch_bounds__(kTmaBlock, 1)
         // drain: every issued box must land before shared memory goes away
         for (int kk = (k >= kStages ? k - kStages : 0); kk < k; ++kk)
           (void)mbar_wait(&full[kk % kStages], (uint32_t)((kk / kStages) & 1));
+      }
+    }
+  } else if (warp == kBoundaryWarp) {
+    // ---- boundary nodes: FP64 maximum-entropy solves beside the pipeline --
+    // (every lane runs the same trip count; lanes past the list idle)
+    for (int e0 = blockIdx.x * 32; e0 < a.n_open; e0 += gridDim.x * 32) {
+      const int e = e0 + lane;
+      if (e < a.n_open) {
+        const int n = a.open_nodes[dbg_idx(e, a.n_open, a.status, kSiteNode)];
+        const int y = n / a.pitch - kYO, x = n - (y + kYO) * a.pitch - kXO;
+        GlobalSrc<float> src{a, n};
+        my_u += step_node<float, kFinal, true, true, kWalls>(a, src, x, y, n, a.frac);
       }
     }
   } else {
@@ -215,7 +246,8 @@ __global__ void __launch_bounds__(kTmaBlock, 1)
       const unsigned char* st = smem + s * kStageBytes;
       SmemSrc src{(const float*)st, (const float*)(st + kOffVel), (const float*)(st + kOffK),
                   (const uint32_t*)(st + kOffWord), r, 0, a.status};
-      const int x0 = (t % ntx) * kTW, y = (t / ntx) * kTH + r;
+      const int2 o = origin[s];
+      const int x0 = o.x, y = o.y + r;
 #pragma unroll 1
       for (int j = 0; j < kNodesPerLane; ++j) {
         const int xl = cbase + 32 * j;
@@ -223,9 +255,9 @@ __global__ void __launch_bounds__(kTmaBlock, 1)
         src.c = xl + 4;
         const long long n = (long long)(y + kYO) * a.pitch + (x + kXO);
         if (group_is_interior(x - lane, y, a.nx, a.ny))
-          my_u += step_node<float, kFinal, false, kWalls>(a, src, x, y, n, a.frac);
-        else if (x < a.nx && y < a.ny)
-          my_u += step_node<float, kFinal, true, kWalls>(a, src, x, y, n, a.frac);
+          my_u += step_node<float, kFinal, false, false, kWalls, true>(a, src, x, y, n, a.frac);
+        else if (x < a.nx && y < a.ny && !on_open_side(x, y, a.nx, a.ny, a.open_mask))
+          my_u += step_node<float, kFinal, true, false, kWalls, true>(a, src, x, y, n, a.frac);
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[s]);

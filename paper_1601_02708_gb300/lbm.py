@@ -16,7 +16,10 @@ from ._lib import Diag, LBMError, Params, check
 
 PERIODIC, DIRICHLET, NEUMANN = 0, 1, 2
 REACT_NONE, REACT_SURFACE, REACT_BULK = 0, 1, 2
-WALLS = {"bounce": 0, "maxent": 1}  # lbm_wall_mode: halfway bounce-back, zero-flux max-entropy
+# lbm_wall_mode: halfway bounce-back; zero-flux maximum entropy with the
+# Newton solve in FP64 ("maxent") or in the lattice's own precision
+# ("maxent_lattice", FP32 on an FP32 lattice)
+WALLS = {"bounce": 0, "maxent": 1, "maxent_lattice": 2}
 
 
 def _torch():
@@ -92,7 +95,9 @@ class LBM:
     ``precision`` 32 runs FP32 populations with FP64 boundary solves and
     sums; 64 runs FP64 throughout.  ``walls`` treats the pore walls by
     halfway bounce-back ("bounce") or as zero-flux boundaries of the
-    maximum-entropy kind (Sec. 4.1.1 (b), "maxent").
+    maximum-entropy kind (Sec. 4.1.1 (b)) with the Lagrange multiplier's
+    Newton solve in FP64 ("maxent") or in the lattice's precision
+    ("maxent_lattice").
     """
 
     def __init__(self, nx, ny, tau, edges=(PERIODIC,) * 4, precision=32,
@@ -100,6 +105,7 @@ class LBM:
                  k_field=None, dissolution=False, mineral=None, stream=None, walls="bounce"):
         self._lib = _lib.load()
         self.nx, self.ny = int(nx), int(ny)
+        self.ny_whole = self.ny  # rows of the inputs (a slab's lattice has more)
         self.precision = int(precision)
         p = Params()
         p.nx, p.ny, p.precision = self.nx, self.ny, self.precision
@@ -111,7 +117,7 @@ class LBM:
         p.dissolution = int(bool(dissolution))
         self.params = p
         self.edges = tuple(int(e) for e in edges)
-        N = self.nx * self.ny
+        N = self.nx * self.ny_whole
         keep = []
         args = (_in_ptr(solid, "u8", N, keep), _in_ptr(vel, "f64", 2 * N, keep),
                 _in_ptr(k_field, "f64", N, keep), _in_ptr(mineral, "f64", N, keep),
@@ -119,14 +125,18 @@ class LBM:
         if stream is None:
             stream = current_stream_handle()
         self._stream = stream
-        h = ctypes.c_void_p()
-        check(self._lib.lbm_init(ctypes.byref(h), ctypes.byref(p), *args, stream))
-        self._h = h
+        self._h = self._create(p, args, stream)
         self.set_walls(walls)
 
+    def _create(self, p, args, stream):
+        h = ctypes.c_void_p()
+        check(self._lib.lbm_init(ctypes.byref(h), ctypes.byref(p), *args, stream))
+        return h
+
     def set_walls(self, walls):
-        """Pore walls from the next step on: "bounce" (halfway bounce-back) or
-        "maxent" (zero-flux maximum-entropy condition, lbm_set_wall_mode)."""
+        """Pore walls from the next step on: "bounce" (halfway bounce-back),
+        "maxent" or "maxent_lattice" (zero-flux maximum-entropy condition,
+        lbm_set_wall_mode)."""
         if walls not in WALLS:
             raise ValueError(f"walls must be one of {sorted(WALLS)}")
         check(self._lib.lbm_set_wall_mode(self.handle, WALLS[walls]))
@@ -154,7 +164,7 @@ class LBM:
     @property
     def handle(self):
         if self._h is None:
-            raise LBMError(-4, "context is closed")
+            raise LBMError(-5, "context is closed")
         return self._h
 
     @property
@@ -187,7 +197,8 @@ class LBM:
         the east edge) with its gradients, computed by the library's reverse
         sweep with sqrt(n) checkpoints: dict(J, k [ny, nx] = dJ/dk(x),
         ua / ub [n_edge] = dJ/d(Dirichlet data at the start / end),
-        q [n_edge] = dJ/d(Neumann data)).  Fixed mask only."""
+        q [n_edge] = dJ/d(Neumann data), side [4] = dJ/d(one Dirichlet
+        value held on the whole W, E, S, N side)).  Fixed mask only."""
         keep = []
         m = self.n_edge
         a = _in_ptr(u_dir_t0, "f64", m, keep)
@@ -196,10 +207,11 @@ class LBM:
         J = ctypes.c_double()
         gk = np.empty((self.ny, self.nx))
         ga, gb, gq = (np.empty(m) for _ in range(3))
+        gs = np.empty(4)
         check(self._lib.lbm_adjoint(self.handle, int(n), int(eta), int(stride), a, b, q,
                                     ctypes.byref(J), gk.ctypes.data, ga.ctypes.data,
-                                    gb.ctypes.data, gq.ctypes.data))
-        return dict(J=J.value, k=gk, ua=ga, ub=gb, q=gq)
+                                    gb.ctypes.data, gq.ctypes.data, gs.ctypes.data))
+        return dict(J=J.value, k=gk, ua=ga, ub=gb, q=gq, side=gs)
 
     KERNELS = {"auto": 0, "generic": 1, "tma": 2}
 
@@ -221,7 +233,10 @@ class LBM:
         return a.value, b.value, c.value, d.value
 
     def synchronize(self):
-        check(self._lib.lbm_synchronize(self.handle))
+        """Wait for the context's stream; returns 1 (LBM_WARN_BC_INFEASIBLE)
+        when boundary solves since the last report met data with no
+        non-negative solution, else 0."""
+        return check(self._lib.lbm_synchronize(self.handle))
 
     # -- read-out --------------------------------------------------------------
     def concentration(self, out=None, precision=64):
@@ -253,6 +268,18 @@ class LBM:
         check(self._lib.lbm_get_solid(self.handle, _out_ptr(out, "u8", self.nx * self.ny)))
         return out
 
+    def flip_steps(self, out=None):
+        """Dissolution record [ny, nx] (int32): the number of steps after
+        which each node was first fluid, -1 for nodes never turned fluid."""
+        if out is None:
+            out = np.empty((self.ny, self.nx), dtype=np.int32)
+        if not (isinstance(out, np.ndarray) and out.dtype == np.int32 and out.size == self.nx * self.ny) \
+                and not _is_tensor(out):
+            raise ValueError("output must be an int32 array of ny * nx elements")
+        ptr = out.data_ptr() if _is_tensor(out) else out.ctypes.data
+        check(self._lib.lbm_get_flip_steps(self.handle, ptr))
+        return out
+
     def mineral(self, out=None):
         if out is None:
             out = np.empty((self.ny, self.nx))
@@ -260,8 +287,13 @@ class LBM:
         return out
 
     def diagnostics(self):
+        """FP64 reductions and counters (lbm_diag).  The counts of boundary
+        solves without a non-negative solution and of wall solves short of
+        the Newton tolerance are reported here, not raised."""
         d = Diag()
-        check(self._lib.lbm_diagnostics(self.handle, ctypes.byref(d)))
+        st = self._lib.lbm_diagnostics(self.handle, ctypes.byref(d))
+        if st != _lib.LBM_ERR_NEWTON:
+            check(st)
         return {k: getattr(d, k) for k, _ in Diag._fields_}
 
     def trace(self, xy, out=None):
@@ -330,7 +362,7 @@ def _breakthrough_class():
             r = lbm.adjoint(n, 1, ud, ud, None, stride)
             dev = k_field.device if torch.is_tensor(k_field) else "cpu"
             gk = torch.as_tensor(r["k"], device=dev).to(k_field.dtype).reshape(k_field.shape)
-            gc = float(r["ua"][:lbm.ny].sum() + r["ub"][:lbm.ny].sum())
+            gc = float(r["side"][0])  # dJ/dc_in of the west side, from the library
             ctx.save_for_backward(gk)
             ctx.gc = gc
             ctx.cin_like = c_in if torch.is_tensor(c_in) else None

@@ -110,7 +110,7 @@ def test_shapes_agree_and_autotune_restores_state(env):
     cases = inputs.batch_cases(n_inst=5, seed=5, smin=64, smax=300)
     ud = [c["u_dir"] for c in cases]
     shapes = pkg.LBMBatch.shapes()
-    assert shapes[-1] == (96, 8, 800, True)
+    assert shapes[-1] == (96, 8, 832, True)
     results = []
     for shape in range(len(shapes)):
         members = _members(pkg, s.cuda_stream, 32, cases)

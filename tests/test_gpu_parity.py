@@ -89,11 +89,14 @@ def test_porous_dissolution_parity(gb, oracle_mod, prec, kernel, shape):
     lat.substeps(steps, 1, ud, ud, q)
     d_ref = ref.diag()
     u_ref, solid_ref, fpost_ref = ref.u(), ref.solid(), ref.fpost()
+    flips_ref = ref.flip_steps()
     ref.substeps(1, 1, ud, ud, q)           # mineral one reaction step ahead
     m_next = ref.mineral()
     u = lat.concentration()
     assert _relerr(u, u_ref) <= TOL[prec]
     assert np.array_equal(lat.solid(), solid_ref)
+    # the step after which every dissolved node turned fluid, node by node
+    assert np.array_equal(lat.flip_steps(), flips_ref)
     assert _relerr(lat.populations(), fpost_ref) <= TOL[prec]
     s = solid_ref != 0
     mtol = 1e-12 if prec == 64 else 1e-5
@@ -339,8 +342,8 @@ def test_fp32_bound_over_ten_thousand_steps(gb, oracle_mod, dissolution):
     """The FP32 bound after the 10,000-step run length of the large workload,
     on a 128 x 128 lattice of the same generator that the oracle can finish:
     max|u32 - u_oracle| <= 1e-5 max|u|; with dissolution (over a thousand
-    flips) the FP32 mask also matches the oracle's, and FP64 mode matches to
-    1e-12 with an identical mask."""
+    flips) the final FP32 mask matches the oracle's, and FP64 mode matches to
+    1e-12 with an identical mask and identical flip steps."""
     n, steps = 128, 10000
     case = inputs.porous_case(n, n, seed=2)
     case["solid"] = inputs.disk_packing(n, n, 0.6, 2, rmin=3, rmax=8)
@@ -356,6 +359,15 @@ def test_fp32_bound_over_ten_thousand_steps(gb, oracle_mod, dissolution):
         lat.substeps(steps, 1, ud, ud, q)
         assert _relerr(lat.concentration(), ref.u()) <= TOL[prec]
         assert np.array_equal(lat.solid(), ref.solid())
+        if dissolution:
+            shifted = int((lat.flip_steps() != ref.flip_steps()).sum())
+            if prec == 64:
+                assert shifted == 0
+            else:  # a flip may come a step apart where the mineral crosses
+                # zero within the FP32 margin (reading c16); the final masks agree
+                print(f"PRECISION fp32 128^2 x 1e4: {shifted} of "
+                      f"{int(ref.diag()['flips'])} flips shifted")
+                assert shifted <= 0.01 * ref.diag()["flips"]
     if dissolution:
         assert ref.diag()["flips"] > 1000
 

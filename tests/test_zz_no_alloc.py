@@ -1,8 +1,9 @@
 """lbm_mass_noalloc: the FP64 mass sum that allocates nothing, for callers
-that cannot allocate device memory when they need the sum (CUDA-graph
-recording, a fixed memory budget, a host framework owning all allocations).
-Called through the C ABI and checked against the mass of lbm_diagnostics on
-the same state, twice in a row.  Collected last on purpose."""
+that cannot allocate device memory when they need the sum (code inside a
+device-memory budget fixed at start-up, a host framework that owns every
+allocation).  Called through the C ABI and checked against the mass of
+lbm_diagnostics on the same state, twice in a row.  Collected last on
+purpose."""
 import ctypes
 
 import numpy as np
