@@ -503,17 +503,23 @@ def main():
         uA0 = np.zeros((n, n))
         uB0 = np.where(fluid, 0.5, 0.0)  # B resident; A enters at the inlet
         coeffs = (1.0, 2.0, 1.0)
-        bm = Bimolecular(n, n, case["tau"], coeffs, uA0, uB0, precision=32,
-                         edges=kw["edges"], solid=kw["solid"], vel=kw["vel"])
         a_in = ud  # alpha = u_A + u_C at the inlet: the inlet value of A
         b_in = torch.zeros_like(ud)
-        bm.substeps(3, 1, (a_in, a_in), (b_in, b_in))
-        barrier()
-        ev0.record(stream)
-        bm.substeps(args.bimolecular_steps, 1, (a_in, a_in), (b_in, b_in))
-        ev1.record(stream)
-        ev1.synchronize()
-        msb = max_over_ranks(ev0.elapsed_time(ev1))
+        msb = {}
+        for fused in (False, True):  # two launches a substep, then the fused pair kernel
+            if fused:
+                bm.close()
+                del bm
+                torch.cuda.empty_cache()
+            bm = Bimolecular(n, n, case["tau"], coeffs, uA0, uB0, precision=32, fused=fused,
+                             edges=kw["edges"], solid=kw["solid"], vel=kw["vel"])
+            bm.substeps(3, 1, (a_in, a_in), (b_in, b_in))
+            barrier()
+            ev0.record(stream)
+            bm.substeps(args.bimolecular_steps, 1, (a_in, a_in), (b_in, b_in))
+            ev1.record(stream)
+            ev1.synchronize()
+            msb[fused] = max_over_ranks(ev0.elapsed_time(ev1))
         al = torch.empty((n, n), dtype=torch.float64, device="cuda")
         be = torch.empty_like(al)
         bm.alpha.concentration(out=al)
@@ -533,9 +539,18 @@ def main():
         bm.close()
         del bm, al, be, uA, uB, uC
         torch.cuda.empty_cache()
-        bimol = {"value": world * 2 * nodes * args.bimolecular_steps / (msb / 1e3) / 1e9,
+        ms_f = msb[True] / args.bimolecular_steps
+        n_sol = int((kw["solid"] != 0).sum())
+        # fused pair: two fields' populations, one velocity and one mask read per node
+        bp = (2 * 9 * 4 * 2 + 2 * 4 + 1) * (nodes - n_sol) + BYTES_SOLID * n_sol
+        ap_ = bp / (ms_f / 1e3) / 1e9
+        bimol = {"value": world * 2 * nodes * args.bimolecular_steps / (msb[True] / 1e3) / 1e9,
                  "unit": "GLUPS (both invariants)", "steps": args.bimolecular_steps,
-                 "ms_per_step": msb / args.bimolecular_steps,
+                 "fused": True, "ms_per_step": ms_f,
+                 "unfused_ms_per_step": msb[False] / args.bimolecular_steps,
+                 "roofline": {"bound": "hbm", "achieved": ap_, "peak": peak, "unit": "GB/s",
+                              "frac": ap_ / peak, "bytes_per_fluid_node": 2 * 9 * 4 * 2 + 2 * 4 + 1,
+                              "timing": "whole substep calls (launch gaps included)"},
                  "species_ms": epi_ms, "species_gbs": 5 * 8 * nodes / (epi_ms / 1e3) / 1e9,
                  "sum_uC": produced,
                  "reaction": "A + 2B -> C, instantaneous; A enters at the inlet, B resident"}

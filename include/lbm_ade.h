@@ -231,6 +231,52 @@ lbm_status lbm_invariants_from_species(long long n, double nA, double nB, double
                                        const double* uA, const double* uB, const double* uC,
                                        double* alpha, double* beta, void* stream);
 
+/* Calcite at equilibrium, CaCO3 <-> Ca2+ + CO3^2- (Sec. 7.4): with u1, u2, u3
+ * the concentrations of CaCO3, Ca2+, CO3^2-, K_sp = u2 u3 / u1 (Eq.
+ * "Hybrid_Ksp"), and the invariants psi1 = u1 + u2, psi2 = u3 - u2 (Eq.
+ * "Carbonate_uncoupled"; the printed u1 - u2 is not conserved by the
+ * reaction, u1 + u2 is and leads to the printed root), which two lattices
+ * transport without a reaction term.  lbm_calcite_species returns
+ *   u2 = (-(psi2 + K_sp) + sqrt((psi2 + K_sp)^2 + 4 K_sp psi1)) / 2,
+ *   u1 = psi1 - u2,  u3 = psi2 + u2,
+ * evaluating the root as 2 K_sp psi1 / ((psi2 + K_sp) + sqrt(...)) where
+ * psi2 + K_sp > 0 (the same root, without the cancellation of the printed
+ * form when K_sp psi1 is small).  Invariants of non-negative species
+ * (psi1 >= 0, psi1 + psi2 >= 0) give non-negative species; elsewhere the
+ * discriminant may be negative and the node's outputs NaN.
+ * lbm_calcite_invariants is the inverse map.
+ * Arrays of n FP64 values, host or device, as lbm_species_from_invariants.
+ * Errors: LBM_ERR_ARG (n < 0, K_sp not finite and positive, a NULL array),
+ * LBM_ERR_NOMEM, LBM_ERR_CUDA. */
+lbm_status lbm_calcite_species(long long n, double ksp, const double* psi1, const double* psi2,
+                               double* u1, double* u2, double* u3, void* stream);
+lbm_status lbm_calcite_invariants(long long n, const double* u1, const double* u2,
+                                  const double* u3, double* psi1, double* psi2, void* stream);
+
+/* Two fields on one geometry (the invariants alpha, beta of Sec. 7.2 or
+ * psi1, psi2 of Sec. 7.4: two concentrations carried by one flow through one
+ * pore space).  lbm_pair_create binds two existing contexts that have the
+ * same size, sides, solid mask and velocity field, FP32 populations, the
+ * same stream and step parity, bounce-back walls and no dissolution (their
+ * relaxation time, rate field, edge data and initial data may differ; the
+ * masks and velocities are compared on the device, a call that waits for
+ * the stream).  lbm_pair_substeps then advances both by n substeps of eta
+ * with one kernel launch a substep: each lattice computes exactly what
+ * lbm_substeps on it alone computes (the same Eq. "MTS" edge data, the same
+ * mass partials), while the velocity and link words are read once for both.
+ * Edge arguments as lbm_substeps, one set per lattice (a_* for the first).
+ * The contexts stay usable on their own (lbm_get_u, lbm_mass, lbm_save ...);
+ * a pair whose lattices were stepped apart since is refused
+ * (LBM_ERR_STATE).  The pair holds no device memory; destroy it before its
+ * contexts.  Errors: LBM_ERR_ARG (the lattices do not qualify, n < 0,
+ * eta < 1), LBM_ERR_STATE, LBM_ERR_NOMEM, LBM_ERR_CUDA. */
+typedef struct lbm_pair lbm_pair;
+lbm_status lbm_pair_create(lbm_pair** out, lbm_ctx* a, lbm_ctx* b);
+lbm_status lbm_pair_substeps(lbm_pair* p, int n, int eta, const double* a_dir_t0,
+                             const double* a_dir_t1, const double* a_q, const double* b_dir_t0,
+                             const double* b_dir_t1, const double* b_q);
+void lbm_pair_destroy(lbm_pair* p);
+
 /* Schwarz rollback (Algorithm 1 restarts every sub-iteration from the state
  * at the start of the coarse step): lbm_state_bytes gives the size of a
  * state blob; lbm_save writes the full state into a caller-owned buffer of

@@ -83,6 +83,8 @@ def load():
             "lbm_min_population": [P, ctypes.POINTER(D)],
             "lbm_species_from_invariants": [ctypes.c_longlong, D, D, D, P, P, P, P, P, P],
             "lbm_invariants_from_species": [ctypes.c_longlong, D, D, D, P, P, P, P, P, P],
+            "lbm_calcite_species": [ctypes.c_longlong, D, P, P, P, P, P, P],
+            "lbm_calcite_invariants": [ctypes.c_longlong, P, P, P, P, P, P],
             "lbm_state_bytes": [P, ctypes.POINTER(S)],
             "lbm_save": [P, P, S],
             "lbm_restore": [P, P, S],
@@ -107,6 +109,8 @@ def load():
             "lbm_stage_edges": [P, P, P, P],
             "lbm_step_stream": [P, I, I, I],
             "lbm_step_dissolve": [P],
+            "lbm_pair_create": [ctypes.POINTER(P), P, P],
+            "lbm_pair_substeps": [P, I, I, P, P, P, P, P, P],
             "lbm1d_init": [ctypes.POINTER(P), I, D, D, I, I, P, P],
             "lbm1d_substeps": [P, I, I, P, P, P],
             "lbm1d_get": [P, P],
@@ -138,6 +142,8 @@ def load():
         lib.lbm_fem_destroy.restype = None
         lib.lbm_destroy.argtypes = [P]
         lib.lbm_destroy.restype = None
+        lib.lbm_pair_destroy.argtypes = [P]
+        lib.lbm_pair_destroy.restype = None
         lib.lbm1d_destroy.argtypes = [P]
         lib.lbm1d_destroy.restype = None
         lib.lbm_last_error.argtypes = []

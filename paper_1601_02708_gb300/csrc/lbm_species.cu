@@ -42,6 +42,40 @@ __global__ void k_invariants(const double* __restrict__ ua, const double* __rest
   }
 }
 
+// Calcite at equilibrium (Sec. 7.4, Eq. "Hybrid_Ksp" K_sp = u2 u3 / u1) from
+// the invariants psi1 = u1 + u2 and psi2 = u3 - u2 (Eq. "Carbonate_uncoupled";
+// the printed u1 - u2 is not conserved by the reaction, u1 + u2 is and gives
+// the printed root): u2 is the non-negative root of
+// u2^2 + (psi2 + K_sp) u2 - K_sp psi1 = 0.  Written as printed,
+// (-(psi2 + K_sp) + sqrt(...)) / 2 cancels catastrophically when
+// psi2 + K_sp > 0 and K_sp psi1 is small (K_sp = 3.36e-9: u2 ~ 1e-8 from two
+// O(0.1) terms); the same root as 2 K_sp psi1 / ((psi2 + K_sp) + sqrt(...))
+// does not, so that form is used there.  u1 = psi1 - u2, u3 = psi2 + u2.
+__global__ void k_calcite(const double* __restrict__ p1, const double* __restrict__ p2,
+                          long long n, double ksp, double* __restrict__ u1,
+                          double* __restrict__ u2, double* __restrict__ u3) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double a = p1[i], b = p2[i];
+    const double s = b + ksp;
+    const double r = sqrt(s * s + 4.0 * ksp * a);
+    const double c = s > 0.0 ? 2.0 * ksp * a / (s + r) : 0.5 * (r - s);
+    u1[i] = a - c;
+    u2[i] = c;
+    u3[i] = b + c;
+  }
+}
+
+__global__ void k_calcite_inv(const double* __restrict__ u1, const double* __restrict__ u2,
+                              const double* __restrict__ u3, long long n,
+                              double* __restrict__ p1, double* __restrict__ p2) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    p1[i] = u1[i] + u2[i];
+    p2[i] = u3[i] - u2[i];
+  }
+}
+
 bool ratios_ok(double nA, double nB, double nC) {
   return std::isfinite(nA) && std::isfinite(nB) && std::isfinite(nC) && nA > 0 && nB > 0 &&
          nC > 0;
@@ -128,6 +162,35 @@ lbm_status lbm_invariants_from_species(long long n, double nA, double nB, double
   double* out[2] = {alpha, beta};
   return with_device_arrays(n, s, in, 3, out, 2, who, [&](const double* const* d, double* const* o) {
     k_invariants<<<grid_for(n), 256, 0, s>>>(d[0], d[1], d[2], n, rAC, rBC, o[0], o[1]);
+  });
+}
+
+lbm_status lbm_calcite_species(long long n, double ksp, const double* psi1, const double* psi2,
+                               double* u1, double* u2, double* u3, void* stream) {
+  const char* who = "lbm_calcite_species";
+  if (n < 0 || !(std::isfinite(ksp) && ksp > 0.0) ||
+      (n > 0 && (!psi1 || !psi2 || !u1 || !u2 || !u3)))
+    return ctx_fail(LBM_ERR_ARG, "%s: bad arguments", who);
+  if (n == 0) return LBM_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const double* in[2] = {psi1, psi2};
+  double* out[3] = {u1, u2, u3};
+  return with_device_arrays(n, s, in, 2, out, 3, who, [&](const double* const* d, double* const* o) {
+    k_calcite<<<grid_for(n), 256, 0, s>>>(d[0], d[1], n, ksp, o[0], o[1], o[2]);
+  });
+}
+
+lbm_status lbm_calcite_invariants(long long n, const double* u1, const double* u2,
+                                  const double* u3, double* psi1, double* psi2, void* stream) {
+  const char* who = "lbm_calcite_invariants";
+  if (n < 0 || (n > 0 && (!u1 || !u2 || !u3 || !psi1 || !psi2)))
+    return ctx_fail(LBM_ERR_ARG, "%s: bad arguments", who);
+  if (n == 0) return LBM_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const double* in[3] = {u1, u2, u3};
+  double* out[2] = {psi1, psi2};
+  return with_device_arrays(n, s, in, 3, out, 2, who, [&](const double* const* d, double* const* o) {
+    k_calcite_inv<<<grid_for(n), 256, 0, s>>>(d[0], d[1], d[2], n, o[0], o[1]);
   });
 }
 

@@ -117,36 +117,40 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
       : "memory");
 }
 
-// Inputs of one node read from the shared-memory tile of its stage.
-struct SmemSrc {
-  const float* pop;      // [9][kBoxH][kBoxW]
-  const float* vel;      // [2][kTH][kTW]
-  const float* kfield;   // [kTH][kTW]
-  const uint32_t* words; // [kTH][kTW] link words
+// Inputs of one node read from the shared-memory tile of its stage: tiles of
+// kTW x TH nodes, the population box one node wider on every side.
+template <int TH>
+struct SmemSrcT {
+  static constexpr int kBH = TH + 2;  // box rows
+  const float* pop;      // [9][kBH][kBoxW]
+  const float* vel;      // [2][TH][kTW]
+  const float* kfield;   // [TH][kTW]
+  const uint32_t* words; // [TH][kTW] link words
   int r, c;              // node's row in the tile, column in the halo box (xl + 4)
   int* flag;             // status word (index checks of the debug build)
   __device__ __forceinline__ int at(int i) const {  // box offset of x - e_i
     return (r + 1 - cy_of(i)) * kBoxW + (c - cx_of(i));
   }
   __device__ __forceinline__ long long pb(long long i) const {
-    return dbg_idx(i, 9 * kBoxH * kBoxW, flag, kSiteSmemPop);
+    return dbg_idx(i, 9 * kBH * kBoxW, flag, kSiteSmemPop);
   }
   __device__ __forceinline__ long long nb(long long i, int planes = 1) const {
-    return dbg_idx(i, planes * kTH * kTW, flag, kSiteSmemNode);
+    return dbg_idx(i, planes * TH * kTW, flag, kSiteSmemNode);
   }
   __device__ __forceinline__ uint32_t word() const { return words[nb(r * kTW + (c - 4))]; }
-  __device__ __forceinline__ float pull(int i) const { return pop[pb(i * kBoxH * kBoxW + at(i))]; }
+  __device__ __forceinline__ float pull(int i) const { return pop[pb(i * kBH * kBoxW + at(i))]; }
   __device__ __forceinline__ float own(int i) const {
-    return pop[pb(i * kBoxH * kBoxW + (r + 1) * kBoxW + c)];
+    return pop[pb(i * kBH * kBoxW + (r + 1) * kBoxW + c)];
   }
   __device__ __forceinline__ float pull_or_bounce(int i, bool bounce) const {
-    return pop[pb(bounce ? opp_of(i) * kBoxH * kBoxW + (r + 1) * kBoxW + c
-                         : i * kBoxH * kBoxW + at(i))];
+    return pop[pb(bounce ? opp_of(i) * kBH * kBoxW + (r + 1) * kBoxW + c
+                         : i * kBH * kBoxW + at(i))];
   }
   __device__ __forceinline__ float vx() const { return vel[nb(r * kTW + (c - 4), 2)]; }
-  __device__ __forceinline__ float vy() const { return vel[nb((kTH + r) * kTW + (c - 4), 2)]; }
+  __device__ __forceinline__ float vy() const { return vel[nb((TH + r) * kTW + (c - 4), 2)]; }
   __device__ __forceinline__ float kf() const { return kfield[nb(r * kTW + (c - 4))]; }
 };
+using SmemSrc = SmemSrcT<kTH>;
 
 struct TmaMaps {
   CUtensorMap pop;   // fin: [9][rows][pitch] float, box {kBoxW, kBoxH, 9}

@@ -335,6 +335,47 @@ class LBM:
         check(self._lib.lbm_restore(self.handle, ptr, nb))
 
 
+class LBMPair:
+    """Two lattices of one geometry stepped together (lbm_pair_*): one kernel
+    launch a substep reads the shared velocity and link words once and
+    updates both fields, each exactly as its own ``substeps`` would.  Both
+    must be FP32, of one size, sides, mask, velocity, stream and step count,
+    with bounce-back walls and no dissolution; ``LBMError`` otherwise.  The
+    lattices stay usable on their own for read-outs; close the pair first."""
+
+    def __init__(self, a, b):
+        self._lib = _lib.load()
+        self.a, self.b = a, b
+        h = ctypes.c_void_p()
+        check(self._lib.lbm_pair_create(ctypes.byref(h), a.handle, b.handle))
+        self._h = h
+
+    def substeps(self, n, eta=1, a_dir=(None, None), b_dir=(None, None), a_q=None, b_q=None):
+        """n substeps of both; Dirichlet data per lattice as (at the start,
+        at the end of the coarse step), Neumann data likewise, each in the
+        edge layout of ``LBM.substeps``."""
+        if self._h is None:
+            raise LBMError(-5, "pair is closed")
+        keep = []
+        m = self.a.n_edge
+        ptrs = [_in_ptr(x, "f64", m, keep) for x in (a_dir[0], a_dir[1], a_q,
+                                                     b_dir[0], b_dir[1], b_q)]
+        check(self._lib.lbm_pair_substeps(self._h, int(n), int(eta), *ptrs))
+        self._keep = keep
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._lib.lbm_pair_destroy(h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def outlet_breakthrough(lbm, k_field, c_in, n, start_state, stride=0):
     """J(k, c_in): the outlet breakthrough of ``lbm`` over n substeps from
     ``start_state`` (a blob of ``lbm.save()``), with the rate field
