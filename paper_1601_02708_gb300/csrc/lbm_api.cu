@@ -542,15 +542,21 @@ lbm_status init_impl(lbm_ctx* c, const uint8_t* solid, const double* vel,
     CK(cudaMalloc((void**)&c->smin, nxy * sizeof(double)));
   }
   {
-    // the nodes on non-periodic sides, each once (W, E, S, N order)
+    // the nodes on Dirichlet / Neumann sides, each once (W, E, S, N order);
+    // periodic sides and the sides a slab shares with a neighbour are not open
     std::vector<int> open;
     auto add = [&](int x, int y) { open.push_back((y + kYO) * c->pitch + (x + kXO)); };
-    if (!per_x)
-      for (int x : {0, p.nx - 1})
-        for (int y = 0; y < p.ny; ++y) add(x, y);
-    if (!per_y)
-      for (int y : {0, p.ny - 1})
-        for (int x = per_x ? 0 : 1; x < (per_x ? p.nx : p.nx - 1); ++x) add(x, y);
+    auto is_open = [&](int s) {
+      return p.edge[s] == LBM_EDGE_DIRICHLET || p.edge[s] == LBM_EDGE_NEUMANN;
+    };
+    if (is_open(0))
+      for (int y = 0; y < p.ny; ++y) add(0, y);
+    if (is_open(1))
+      for (int y = 0; y < p.ny; ++y) add(p.nx - 1, y);
+    const int xa = is_open(0) ? 1 : 0, xb = is_open(1) ? p.nx - 1 : p.nx;
+    for (int s : {2, 3})
+      if (is_open(s))
+        for (int x = xa; x < xb; ++x) add(x, s == 2 ? 0 : p.ny - 1);
     c->n_open = (int)open.size();
     if (!open.empty()) {
       CK(cudaMalloc((void**)&c->open_nodes, open.size() * sizeof(int)));

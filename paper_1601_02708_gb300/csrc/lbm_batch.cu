@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(lbm::kTmaBlock, 1)
         src.c = xl + 4;
         const long long n = (long long)(y + kYO) * a.pitch + (x + kXO);
         if (group_is_interior(x - lane, y, a.nx, a.ny))
-          tile_u += step_node<float, kFinal, false, false, kWalls, true>(a, src, x, y, n, frac);
+          tile_u += step_interior_group<kFinal, kWalls>(a, src, x, y, n, frac);
         else if (x < a.nx && y < a.ny && !on_open_side(x, y, a.nx, a.ny, a.open_mask))
           tile_u += step_node<float, kFinal, true, false, kWalls, true>(a, src, x, y, n, frac);
       }

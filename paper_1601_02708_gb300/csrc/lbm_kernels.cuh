@@ -225,11 +225,16 @@ __device__ __forceinline__ void store_share(const StepArgs<Real>& a, long long n
 // discards it: the warp takes one path and issues one set of stores, where
 // mixed solid and fluid lanes would otherwise split it in two.  Results are
 // the same either way.
+// kClear (with !kEdge): the caller has checked that the node is fluid with
+// no solid neighbour before or after this step's flips (its link word is
+// zero in kClearMask), so the bounce-back, wall, share and solid-lane code is
+// compiled out.  Results are the same as without it.
 template <typename Real, bool kFinal, bool kEdge, bool kSolve, int kWalls, bool kLight = false,
-          class Src>
+          bool kClear = false, class Src>
 __device__ __forceinline__ double step_node(const StepArgs<Real>& a, const Src& src,
                                             int x, int y, long long n, double frac) {
-  const uint32_t w = src.word();
+  static_assert(!(kClear && kEdge), "the clear path is for interior nodes");
+  const uint32_t w = kClear ? 0u : src.word();
   const bool ghosts =
       kEdge && ((x == 0) | (x == a.nx - 1) | (y == 0) | (y == a.ny - 1)) &&
       (a.per_x | a.per_y);
@@ -240,8 +245,7 @@ __device__ __forceinline__ double step_node(const StepArgs<Real>& a, const Src& 
   const bool own_solid = (w & kOwnSolid) != 0u;
   const bool pending = (w & kOwnPending) != 0u;
   const bool solid = own_solid && !pending;
-  const unsigned active = __activemask();
-  const unsigned fluid_lanes = __ballot_sync(active, !solid);
+  const unsigned fluid_lanes = kClear ? 0xFFFFFFFFu : __ballot_sync(__activemask(), !solid);
   const unsigned lane = threadIdx.x & 31u;
   const bool fill = ((fluid_lanes >> (lane & 24u)) & 0xFFu) != 0u;
   if (!kLight && own_solid) {

@@ -38,6 +38,10 @@ constexpr int kUpSolidShift = 0;
 constexpr int kUpPostShift = 8;
 constexpr int kUpOutShift = 16;
 __host__ __device__ constexpr uint32_t up_bit(int shift, int i) { return 1u << (shift + i - 1); }
+// A fluid node without a solid neighbour before or after this step's flips
+// has a link word that is zero in these bits.
+constexpr uint32_t kClearMask =
+    kOwnSolid | kOwnPending | (0xFFu << kUpSolidShift) | (0xFFu << kUpPostShift);
 
 // Index checks of the debug-bounds build (compiled with LBM_DEBUG_BOUNDS, in
 // place of a memory checker): an index outside [0, limit) records its check

@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(kTmaBlock, 1)
       const long long n = (long long)(y + kYO) * a.pitch + (x + kXO);
       double v = 0.0;
       if (group_is_interior(x - lane, y, a.nx, a.ny))
-        v = step_node<float, kFinal, false, false, 0, true>(a, src, x, y, n, a.frac);
+        v = step_interior_group<kFinal, 0>(a, src, x, y, n, a.frac);
       else if (x < a.nx && y < a.ny && !on_open_side(x, y, a.nx, a.ny, a.open_mask))
         v = step_node<float, kFinal, true, false, 0, true>(a, src, x, y, n, a.frac);
       if (f) u1 += v;

@@ -152,6 +152,24 @@ struct SmemSrcT {
 };
 using SmemSrc = SmemSrcT<kTH>;
 
+// Step of a warp's 32 interior nodes from a shared-memory tile, by the
+// warp's class (a warp-uniform choice on the link words): every lane clear
+// of solids takes the clear path; every lane solid (and not turning fluid)
+// has nothing to update but its u; other warps take the general path.
+template <bool kFinal, int kWalls, class Src>
+__device__ __forceinline__ double step_interior_group(const StepArgs<float>& a, const Src& src,
+                                                      int x, int y, long long n, double frac) {
+  const uint32_t w = src.word();
+  if (__all_sync(0xFFFFFFFFu, (w & kClearMask) == 0u))
+    return step_node<float, kFinal, false, false, kWalls, true, true>(a, src, x, y, n, frac);
+  if (__all_sync(0xFFFFFFFFu, (w & (kOwnSolid | kOwnPending)) == kOwnSolid)) {
+    if (kFinal) a.u_out[dbg_idx(n, a.plane, a.status, kSiteNode)] = 0.0f;
+    if (a.u_hist) a.u_hist[dbg_idx(n, a.plane, a.status, kSiteNode)] = 0.0f;
+    return 0.0;
+  }
+  return step_node<float, kFinal, false, false, kWalls, true>(a, src, x, y, n, frac);
+}
+
 struct TmaMaps {
   CUtensorMap pop;   // fin: [9][rows][pitch] float, box {kBoxW, kBoxH, 9}
   CUtensorMap vel;   // [2][rows][pitch] float, box {kTW, kTH, 2}
@@ -259,7 +277,7 @@ __global__ void __launch_bounds__(kTmaBlock, 1)
         src.c = xl + 4;
         const long long n = (long long)(y + kYO) * a.pitch + (x + kXO);
         if (group_is_interior(x - lane, y, a.nx, a.ny))
-          my_u += step_node<float, kFinal, false, false, kWalls, true>(a, src, x, y, n, a.frac);
+          my_u += step_interior_group<kFinal, kWalls>(a, src, x, y, n, a.frac);
         else if (x < a.nx && y < a.ny && !on_open_side(x, y, a.nx, a.ny, a.open_mask))
           my_u += step_node<float, kFinal, true, false, kWalls, true>(a, src, x, y, n, a.frac);
       }

@@ -27,7 +27,7 @@ def gb():
 def _case(nx, ny, seed, edges, walls="bounce"):
     solid = inputs.disk_packing(nx, ny, 0.6, seed, rmin=3, rmax=9)
     vel = inputs.streamfunction_velocity(nx, ny, seed + 1, solid=solid)
-    return dict(edges=edges, solid=solid, vel=vel, u0=np.zeros((ny, nx)), react_mode=1,
+    return dict(edges=edges, solid=solid, vel=vel, u0=np.where(solid != 0, 0.0, 0.3), react_mode=1,
                 k=0.05, dissolution=True, mineral=np.full((ny, nx), 0.03), walls=walls)
 
 
@@ -51,7 +51,11 @@ def _run_both(gb, nx, ny, parts, prec, kw, calls, eta):
                                          (4, (1, 2, 1, 2)), (3, (0, 0, 1, 1))])
 def test_split_lattice_is_bit_identical(gb, prec, parts, edges):
     nx, ny = 211, 157  # ragged: several tiles, slab heights that differ
+    from paper_1601_02708_gb300.partition import slab_bounds
     kw = _case(nx, ny, 17 * parts + edges[2], edges)
+    for y0, _ in slab_bounds(ny, parts):  # little mineral on both sides of every cut
+        for y in (y0 - 2, y0 - 1, y0, y0 + 1):
+            kw["mineral"][y % ny] = 0.002
     whole, split = _run_both(gb, nx, ny, parts, prec, kw, calls=6, eta=25)
     assert np.array_equal(split.concentration(), whole.concentration())
     assert np.array_equal(split.populations(), whole.populations())
