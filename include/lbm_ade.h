@@ -339,11 +339,15 @@ lbm_status lbm_set_rate_field(lbm_ctx* c, const double* k_field);
  * J and every gradient are FP64; any
  * output may be NULL; outputs may be host or device memory and are complete
  * when the call returns.
- * Work and memory: the state is kept every `stride` steps (stride <= 0:
- * ceil(sqrt(n))), each segment is recomputed once during the reverse sweep
- * storing u and the Neumann branches of its steps, and one adjoint step runs
- * per step: about three forward passes, with ceil(n / stride) + 3 population
- * sets and `stride` concentration planes of device memory, kept in the
+ * Work and memory: with stride >= n the forward run stores u and the
+ * Neumann branches of every step (n concentration planes of device memory)
+ * and the reverse sweep runs one adjoint step per step: about two forward
+ * passes.  With 0 < stride < n the state is kept every `stride` steps, each
+ * segment is recomputed once during the reverse sweep storing u and the
+ * branches of its steps: about three forward passes, with ceil(n / stride)
+ * + 3 population sets and `stride` concentration planes.  stride <= 0
+ * chooses the whole history when it takes at most a quarter of the free
+ * device memory, else stride = ceil(sqrt(n)).  The buffers stay in the
  * context for the next call.
  * Errors: LBM_ERR_STATE if dissolution is on (a flip is not differentiable)
  * or the pore walls are of the maximum-entropy kind (not affine in f);

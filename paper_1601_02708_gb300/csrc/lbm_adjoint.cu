@@ -30,6 +30,8 @@
 // sqrt(N) checkpointing: the forward run keeps F every L steps; the reverse
 // sweep restores each segment's checkpoint, recomputes its L steps storing
 // u^n and the Neumann branches, then runs its L adjoint steps backwards.
+// With one segment (L >= N) the forward run stores u^n and the branches of
+// every step itself and nothing is recomputed.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -308,15 +310,24 @@ lbm_status adjoint_impl(lbm_ctx* c, int n, int eta, int L) {
   cudaStream_t st = c->stream;
   const dim3 grid = c->grid, block = c->block;
 
-  // forward, keeping a checkpoint every L steps
+  // forward, keeping a checkpoint every L steps; with one segment (K = 1)
+  // the forward run records u and the Neumann branches of every step itself
+  // and nothing is recomputed
+  const bool whole = K == 1;
   ACK(cudaMemcpyAsync(w->u0, c->u, pb, cudaMemcpyDeviceToDevice, st));
   ACK(cudaMemcpyAsync(w->jn0, c->jnode, (size_t)c->p.ny * sizeof(double),
                       cudaMemcpyDeviceToDevice, st));
+  if (whole) ACK(cudaMemsetAsync(w->roots, 0, (size_t)L * ne, st));
   for (int j = 1; j <= n; ++j) {
-    if ((j - 1) % L == 0)
+    if (!whole && (j - 1) % L == 0)
       ACK(cudaMemcpyAsync(w->ck + (size_t)((j - 1) / L) * fb, c->f[c->cur], fb,
                           cudaMemcpyDeviceToDevice, st));
-    ATRY(ctx_launch_step<Real>(c, step_args<Real>(c, (double)j / eta), j == n));
+    lbm::StepArgs<Real> a = step_args<Real>(c, (double)j / eta);
+    if (whole) {
+      a.u_hist = (Real*)(w->uh + (size_t)(j - 1) * pb);
+      a.bc_root = w->roots + (size_t)(j - 1) * ne;
+    }
+    ATRY(ctx_launch_step<Real>(c, a, j == n));
     c->cur ^= 1;
     c->steps += 1;
   }
@@ -330,15 +341,17 @@ lbm_status adjoint_impl(lbm_ctx* c, int n, int eta, int L) {
   ACK(cudaMemsetAsync(w->gk, 0, (size_t)c->plane * sizeof(double), st));
   ACK(cudaMemsetAsync(w->gk32, 0, (size_t)c->plane * sizeof(float), st));
   ACK(cudaMemsetAsync(w->ge, 0, 3 * ne * sizeof(double), st));
-  ACK(cudaMemsetAsync(w->roots, 0, (size_t)L * ne, st));
+  if (!whole) ACK(cudaMemsetAsync(w->roots, 0, (size_t)L * ne, st));
   int mc = 0;
   const long long fb_blocks = (c->plane + 255) / 256;
   const int fold_grid = (int)(fb_blocks < 4LL * c->num_sms ? fb_blocks : 4LL * c->num_sms);
   for (int s = K - 1; s >= 0; --s) {
     const int n0 = s * L, n1 = n0 + L < n ? n0 + L : n;
-    ACK(cudaMemcpyAsync(c->f[0], w->ck + (size_t)s * fb, fb, cudaMemcpyDeviceToDevice, st));
-    c->cur = 0;
-    for (int j = n0 + 1; j <= n1; ++j) {
+    if (!whole) {
+      ACK(cudaMemcpyAsync(c->f[0], w->ck + (size_t)s * fb, fb, cudaMemcpyDeviceToDevice, st));
+      c->cur = 0;
+    }
+    for (int j = n0 + 1; !whole && j <= n1; ++j) {
       // recompute: u of every step into the history (no mass sums: not a
       // final substep), the Neumann branches into their record
       lbm::StepArgs<Real> a = step_args<Real>(c, (double)j / eta);
@@ -351,12 +364,19 @@ lbm_status adjoint_impl(lbm_ctx* c, int n, int eta, int L) {
       ATRY(ctx_launch_step<Real>(c, a, false));
       c->cur ^= 1;
     }
+    // the FP32 lattice's dJ/dk is folded into the FP64 total after every
+    // segment, and every ceil(sqrt(n)) steps of a whole-history sweep
+    const int fold_every = whole ? (int)std::ceil(std::sqrt((double)n)) : 0;
     for (int j = n1; j > n0; --j) {
       const auto a = adj_args<Real>(c, w, mc, (const Real*)(w->uh + (size_t)(j - n0 - 1) * pb),
                                     w->roots + (size_t)(j - n0 - 1) * ne, (double)j / eta);
       lbm_adjoint_step<Real, false><<<grid, block, 0, st>>>(a);
       ACK(cudaGetLastError());
       mc ^= 1;
+      if (sizeof(Real) == 4 && fold_every > 0 && j > n0 + 1 && (n1 - j + 1) % fold_every == 0) {
+        k_fold_gk<<<fold_grid, 256, 0, st>>>(w->gk, w->gk32, c->plane);
+        ACK(cudaGetLastError());
+      }
     }
     if (sizeof(Real) == 4) {
       k_fold_gk<<<fold_grid, 256, 0, st>>>(w->gk, w->gk32, c->plane);
@@ -425,7 +445,17 @@ lbm_status lbm_adjoint(lbm_ctx* c, int n, int eta, int stride, const double* u_d
   ATRY(ctx_check(c));
   if (n < 1 || eta < 1) return ctx_fail(LBM_ERR_ARG, "lbm_adjoint: need n >= 1 and eta >= 1");
   ATRY(check_adjoint(c));
-  int L = stride > 0 ? stride : (int)std::ceil(std::sqrt((double)n));
+  int L = stride;
+  if (stride <= 0) {
+    // the whole history when it takes at most a quarter of the free device
+    // memory (no recompute), else sqrt(n) checkpoints
+    size_t free_b = 0, total_b = 0;
+    ACK(cudaMemGetInfo(&free_b, &total_b));
+    const size_t whole_b = (size_t)n * ((size_t)c->plane * c->esize + (size_t)c->nedge) +
+                           (size_t)c->plane * c->esize * 9;
+    const size_t held = c->adj ? (size_t)c->adj->cap_l * c->adj->plane_b : 0;
+    L = whole_b <= (free_b + held) / 4 ? n : (int)std::ceil(std::sqrt((double)n));
+  }
   if (L > n) L = n;
   ATRY(ctx_stage_edges(c, u_dir_t0, u_dir_t1, q_neu));
   ATRY(ensure_work(c, (n + L - 1) / L, L));

@@ -89,10 +89,12 @@ def test_adjoint_neumann_zero_limit(pkg, oracle_mod):
 
 @pytest.mark.parametrize("prec", [64, 32])
 def test_stride_independence_and_final_state(pkg, prec):
-    """Every checkpoint stride recomputes the same steps, so the gradients
-    are bitwise equal -- except dJ/dk of the FP32 lattice, which sums each
-    segment in FP32 before adding it to the FP64 total, so its rounding
-    follows the segment boundaries; the context ends as after lbm_substeps."""
+    """Every checkpoint stride recomputes the same steps, and a stride of n
+    or more (77, 500; 0 chooses it here) has the forward run record them, so
+    the gradients are bitwise equal -- except dJ/dk of the FP32 lattice,
+    which sums each segment in FP32 before adding it to the FP64 total, so
+    its rounding follows the segment boundaries; the context ends as after
+    lbm_substeps."""
     case, ua, ub, q = _case(4, 100, 30)
     n, eta = 77, 3
     results = []
