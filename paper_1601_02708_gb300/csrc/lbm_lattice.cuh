@@ -298,6 +298,38 @@ __device__ int maxent_wall(Real (&f)[9], unsigned solid) {
   const S logR = log(-R);
   // start: the root if every |a_i| were their weighted mean s2 / s1
   S g = (logR - log(s1) + (S)1) * (s1 / s2);
+  if constexpr (sizeof(S) == 8) {
+    // FP32 iterations (64 times the FP64 rate on this part) bring g to FP32
+    // rounding of the root; the FP64 iterations below then need two or three
+    // steps to the FP64 tolerance instead of a full solve.  Outside FP32's
+    // range, or without FP32 convergence, the FP64 solve starts as above.
+    if (-R > 1e-30 && -R < 1e30) {
+      float af[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) af[i] = (float)a[i];
+      const float logRf = logf((float)-R);
+      float gf = (float)g;
+      bool okf = false;
+      for (int it = 0; it < 24; ++it) {
+        float L = 0.f, dL = 0.f;
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+          if (neg & (1u << i)) {
+            const float e = (float)w_of(i) * expf(gf * -af[i] - 1.f);
+            L -= af[i] * e;
+            dL += af[i] * af[i] * e;
+          }
+        if (!(dL > 0.f) || !(L > 0.f)) break;
+        const float step = (logf(L) - logRf) * (L / dL);
+        gf -= step;
+        if (fabsf(step) <= 5e-7f * (1.f + fabsf(gf))) {
+          okf = true;
+          break;
+        }
+      }
+      if (okf && isfinite(gf)) g = (S)gf;
+    }
+  }
   bool conv = false;
   S last = (S)0;
   for (int it = 0; it < kIters; ++it) {
