@@ -348,6 +348,45 @@ __device__ __forceinline__ bool group_is_interior(int xs, int y, int nx, int ny)
   return xs >= 1 && xs + 32 <= nx - 1 && y >= 1 && y <= ny - 2;
 }
 
+// Inputs of an interior node fetched from global memory in one round: the
+// link word, both candidates of every streamed population (the one pulled
+// from x - e_i and the node's own opposite one, for bounce-back) and the
+// velocity and rate, none of the loads waiting for the link word, which
+// then picks between the candidates.
+template <typename Real>
+struct PreSrc {
+  uint32_t w;
+  Real f[9];
+  Real vx_, vy_, kf_;
+  __device__ __forceinline__ uint32_t word() const { return w; }
+  __device__ __forceinline__ Real own(int i) const { return f[i]; }  // i = 0 only
+  __device__ __forceinline__ Real pull_or_bounce(int i, bool) const { return f[i]; }
+  __device__ __forceinline__ Real vx() const { return vx_; }
+  __device__ __forceinline__ Real vy() const { return vy_; }
+  __device__ __forceinline__ Real kf() const { return kf_; }
+  __device__ __forceinline__ ShareF32* keep_ptr() const { return nullptr; }
+};
+template <typename Real>
+__device__ __forceinline__ PreSrc<Real> preload(const StepArgs<Real>& a, long long n) {
+  const long long lim = 9 * a.plane;
+  PreSrc<Real> p;
+  Real own[9], pul[9];
+  p.w = a.link[dbg_idx(n, a.plane, a.status, kSiteNode)];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) own[i] = a.fin[dbg_idx(i * a.plane + n, lim, a.status, kSitePull)];
+#pragma unroll
+  for (int i = 1; i < 9; ++i)
+    pul[i] = a.fin[dbg_idx(i * a.plane + n - cx_of(i) - (long long)cy_of(i) * a.pitch, lim,
+                           a.status, kSitePull)];
+  p.vx_ = a.vel[dbg_idx(n, a.plane, a.status, kSiteNode)];
+  p.vy_ = a.vel[dbg_idx(a.plane + n, 2 * a.plane, a.status, kSiteNode)];
+  p.kf_ = a.kf ? a.kf[dbg_idx(n, a.plane, a.status, kSiteNode)] : (Real)0;
+  p.f[0] = own[0];
+#pragma unroll
+  for (int i = 1; i < 9; ++i) p.f[i] = (p.w & up_bit(kUpSolidShift, i)) ? own[opp_of(i)] : pul[i];
+  return p;
+}
+
 // Generic step: one thread per node, inputs from global memory.  Used in
 // FP64 mode; the FP32 path runs the TMA kernel instead.
 template <typename Real, bool kFinal, int kWalls = 0>
@@ -358,11 +397,13 @@ __global__ void __launch_bounds__(kBX * kBY, 4) lbm_step(const StepArgs<Real> a)
   double my_u = 0.0;
   if (x < a.nx && y < a.ny) {
     const long long n = (long long)(y + kYO) * a.pitch + (x + kXO);
-    GlobalSrc<Real> src{a, n};
-    if (group_is_interior(blockIdx.x * kBX, y, a.nx, a.ny))
+    if (group_is_interior(blockIdx.x * kBX, y, a.nx, a.ny)) {
+      const PreSrc<Real> src = preload(a, n);
       my_u = step_node<Real, kFinal, false, false, kWalls>(a, src, x, y, n, a.frac);
-    else
+    } else {
+      GlobalSrc<Real> src{a, n};
       my_u = step_node<Real, kFinal, true, true, kWalls>(a, src, x, y, n, a.frac);
+    }
   }
   if (kFinal) {
     const double s = block_sum(my_u, red);
