@@ -74,11 +74,36 @@ __device__ __forceinline__ double spmv_row(const double* __restrict__ A, const d
   return acc;
 }
 
+// Row (i, j) of A y where y_m = g(m) * invd[m] is formed on the fly from
+// vectors complete behind the last grid barrier (read through L2).
+template <class G>
+__device__ __forceinline__ double spmv_row_of(const double* __restrict__ A,
+                                              const double* __restrict__ invd, G g, int i, int j,
+                                              int nxn, int nyn, long long n) {
+  const long long row = (long long)j * nxn + i;
+  double acc = 0.0;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const int di = k % 3 - 1, dj = k / 3 - 1;
+    const int ii = i + di, jj = j + dj;
+    if (ii < 0 || ii >= nxn || jj < 0 || jj >= nyn) continue;
+    const long long m = (long long)jj * nxn + ii;
+    acc += A[k * n + row] * (g(m) * invd[m]);
+  }
+  return acc;
+}
+// The search direction's update r + beta (p - omega v), one expression for
+// the owner's stored value and for the neighbours' on-the-fly values.
+__device__ __forceinline__ double next_dir(double r, double p, double v, double beta,
+                                           double omega) {
+  return r + beta * (p - omega * v);
+}
+
 // ---- the linear solve as one cooperative launch -----------------------------
 // Every block runs the same BiCGSTAB iteration over a grid-stride share of the
-// nodes; the five points per iteration where a vector must be complete (a
-// sparse product reads neighbours) or a dot product summed are grid-wide
-// barriers.  Partial dots are written per block and folded by every block in
+// nodes; the three points per iteration where a dot product must be summed
+// (the vectors the sparse products read are complete there too) are
+// grid-wide barriers.  Partial dots are written per block and folded by every block in
 // the same fixed order, so all blocks take the same decisions.  Each barrier
 // wait is bounded: on expiry the status word is set and the blocks return.
 
@@ -246,24 +271,39 @@ __global__ void __launch_bounds__(kThreads) k_bicgstab(const Solve S) {
     w.r[p] = r;
     w.rhat[p] = r;
     w.p[p] = r;
+    w.v[p] = 0.0;  // the first direction update r + 0 (p - 0 v) reads it
     rr += r * r;
   }
   block_dot2(rr, 0.0, P1, nullptr);
   if (!grid_sync(S.bar, S.status)) return;
   double bnorm2, rnorm2;
   grid_fold2(P0, P1, bnorm2, rnorm2);
-  double rho = rnorm2, alpha = 0.0, omega = 0.0;
+  double rho = rnorm2, alpha = 0.0, omega = 0.0, beta = 0.0;
   const double tol2 = S.tol * S.tol * bnorm2;
   bool done = rnorm2 <= tol2, breakdown = false;
   int it = 0;
+  // Three grid barriers an iteration: each sparse product forms its input
+  // vector on the fly from vectors that are complete behind the last barrier
+  // (the new search direction p = r + beta (p - omega v) with the
+  // preconditioner, then s = r - alpha v with it), so neither needs a
+  // barrier of its own.  p and v alternate between two buffers, because the
+  // products read the previous ones while the owners write the new ones.
+  double* pc = w.p;     // search direction of the last iteration
+  double* pn = w.phat;  // this iteration's
+  double* vc = w.v;     // A (p invd) of the last iteration
+  double* vn = w.shat;  // this iteration's
   while (!done && it < S.max_iter) {
-    for (long long p = p0; p < n; p += stride) w.phat[p] = w.p[p] * S.invd[p];
-    if (!grid_sync(S.bar, S.status)) return;
     double d0 = 0.0;
     for (long long p = p0; p < n; p += stride) {
       const int i = (int)(p % nxn), j = (int)(p / nxn);
-      const double v = spmv_row(A, w.phat, i, j, nxn, nyn, n);
-      w.v[p] = v;
+      pn[p] = next_dir(w.r[p], pc[p], vc[p], beta, omega);
+      const double v = spmv_row_of(
+          A, S.invd,
+          [&](long long m) {
+            return next_dir(__ldcg(w.r + m), __ldcg(pc + m), __ldcg(vc + m), beta, omega);
+          },
+          i, j, nxn, nyn, n);
+      vn[p] = v;
       d0 += w.rhat[p] * v;
     }
     block_dot2(d0, 0.0, P0, nullptr);
@@ -274,18 +314,16 @@ __global__ void __launch_bounds__(kThreads) k_bicgstab(const Solve S) {
       break;
     }
     alpha = rho / rv;
-    for (long long p = p0; p < n; p += stride) {
-      const double sv = w.r[p] - alpha * w.v[p];
-      w.s[p] = sv;
-      w.shat[p] = sv * S.invd[p];
-    }
-    if (!grid_sync(S.bar, S.status)) return;
     double ts = 0.0, tt = 0.0;
     for (long long p = p0; p < n; p += stride) {
       const int i = (int)(p % nxn), j = (int)(p / nxn);
-      const double t = spmv_row(A, w.shat, i, j, nxn, nyn, n);
+      const double sv = w.r[p] - alpha * vn[p];
+      w.s[p] = sv;
+      const double t = spmv_row_of(
+          A, S.invd, [&](long long m) { return __ldcg(w.r + m) - alpha * __ldcg(vn + m); }, i, j,
+          nxn, nyn, n);
       w.t[p] = t;
-      ts += t * w.s[p];
+      ts += t * sv;
       tt += t * t;
     }
     block_dot2(ts, tt, P0, P1);
@@ -296,8 +334,9 @@ __global__ void __launch_bounds__(kThreads) k_bicgstab(const Solve S) {
     double rh = 0.0;
     rr = 0.0;
     for (long long p = p0; p < n; p += stride) {
-      w.x[p] += alpha * w.phat[p] + omega * w.shat[p];
-      const double r = w.s[p] - omega * w.t[p];
+      const double sv = w.s[p];
+      w.x[p] += alpha * (pn[p] * S.invd[p]) + omega * (sv * S.invd[p]);
+      const double r = sv - omega * w.t[p];
       w.r[p] = r;
       rh += w.rhat[p] * r;
       rr += r * r;
@@ -315,9 +354,14 @@ __global__ void __launch_bounds__(kThreads) k_bicgstab(const Solve S) {
       breakdown = true;
       break;
     }
-    const double beta = (rho_new / rho) * (alpha / omega);
+    beta = (rho_new / rho) * (alpha / omega);
     rho = rho_new;
-    for (long long p = p0; p < n; p += stride) w.p[p] = w.r[p] + beta * (w.p[p] - omega * w.v[p]);
+    double* tp = pc;
+    pc = pn;
+    pn = tp;
+    double* tv = vc;
+    vc = vn;
+    vn = tv;
   }
   // every block copies its own share of x: no barrier needed
   for (long long p = p0; p < n; p += stride) S.d[p] = w.x[p];
