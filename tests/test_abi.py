@@ -64,3 +64,43 @@ def test_bimolecular_refuses_reaction_arguments():
     for kw in ({"k": 1e-3}, {"dissolution": True}, {"react_mode": 1}, {"u0": z}):
         with pytest.raises(ValueError):
             Bimolecular(5, 4, 0.8, (1, 2, 1), z, z, **kw)
+
+
+def test_calcite_refuses_reaction_arguments():
+    """Calcite's invariants carry no sink either: refused before any lattice
+    is made (host logic, no GPU needed)."""
+    import numpy as np
+    import pytest
+    from paper_1601_02708_gb300 import Calcite
+    z = np.zeros((4, 5))
+    for kw in ({"k": 1e-3}, {"dissolution": True}, {"react_mode": 1}, {"k_field": z},
+               {"mineral": z}):
+        with pytest.raises(ValueError):
+            Calcite(5, 4, 0.8, 3.36e-9, z, z, z, **kw)
+
+
+def test_chemistry_pairs_only_when_asked_or_possible():
+    """fused=False never makes a pair; fused=None falls back to two
+    separate lattices when the pair is refused; fused=True passes the
+    refusal on (a stand-in pair constructor, no GPU)."""
+    import pytest
+    from paper_1601_02708_gb300 import chemistry
+
+    class Refused(Exception):
+        pass
+
+    calls = []
+
+    def refuse(a, b):
+        calls.append((a, b))
+        raise Refused()
+
+    orig = chemistry.LBMPair
+    chemistry.LBMPair = refuse
+    try:
+        assert chemistry._pair("a", "b", False) is None and not calls
+        assert chemistry._pair("a", "b", None) is None and len(calls) == 1
+        with pytest.raises(Refused):
+            chemistry._pair("a", "b", True)
+    finally:
+        chemistry.LBMPair = orig
