@@ -134,15 +134,19 @@ __device__ __forceinline__ void collide(Real (&f)[9], Real u, Real vx, Real vy,
                                         Real omega, Real kr) {
   const Real base = (Real)1 - (Real)1.5 * (vx * vx + vy * vy);
   const Real om1 = (Real)1 - omega;
+  // the factors that do not depend on the direction, formed once
+  const Real sym0 = omega * base - kr;
+  const Real c45 = (Real)4.5 * omega;
+  const Real c3 = (Real)3 * omega;
+  const Real ev[4] = {vx, vy, vx + vy, vy - vx};  // e.v of directions 1, 2, 5, 6
   Real rest = u - kr * u;
 #pragma unroll
   for (int p = 0; p < 4; ++p) {
     const int i = p < 2 ? p + 1 : p + 3;  // 1, 2, 5, 6; opposites 3, 4, 7, 8
     const int o = opp_of(i);
     const Real wu = (Real)w_of(i) * u;
-    const Real ev = (Real)cx_of(i) * vx + (Real)cy_of(i) * vy;
-    const Real sym = wu * (omega * ((Real)4.5 * ev * ev + base) - kr);
-    const Real anti = wu * omega * (Real)3 * ev;
+    const Real sym = wu * (c45 * (ev[p] * ev[p]) + sym0);
+    const Real anti = (wu * c3) * ev[p];
     f[i] = om1 * f[i] + (sym + anti);
     f[o] = om1 * f[o] + (sym - anti);
     rest -= f[i] + f[o];
