@@ -399,7 +399,41 @@ __global__ void __launch_bounds__(kBX * kBY, 4) lbm_step(const StepArgs<Real> a)
   const int x = blockIdx.x * kBX + threadIdx.x;
   const int y = blockIdx.y * kBY + threadIdx.y;
   double my_u = 0.0;
-  if (x < a.nx && y < a.ny) {
+  const int x0 = blockIdx.x * kBX, y0 = blockIdx.y * kBY;
+  if (sizeof(Real) == 8 && x0 >= 1 && x0 + kBX <= a.nx - 1 && y0 >= 1 && y0 + kBY <= a.ny - 1) {
+    // FP64 lattice, a block one node inside every side: the FP64 pipe (1/64
+    // of the FP32 rate on this part) bounds the update, so the block's nodes
+    // that update (fluid, or turning fluid) are packed into the first lanes
+    // and solid lanes do not occupy it
+    __shared__ unsigned short list[kBX * kBY];
+    __shared__ int wcount[kBX * kBY / 32];
+    const int tid = threadIdx.y * kBX + threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const long long n = (long long)(y + kYO) * a.pitch + (x + kXO);
+    const uint32_t w = a.link[dbg_idx(n, a.plane, a.status, kSiteNode)];
+    const bool active = !(w & kOwnSolid) || (w & kOwnPending);
+    if (!active) {
+      if (kFinal) a.u_out[dbg_idx(n, a.plane, a.status, kSiteNode)] = (Real)0;
+      if (a.u_hist) a.u_hist[dbg_idx(n, a.plane, a.status, kSiteNode)] = (Real)0;
+    }
+    const unsigned bal = __ballot_sync(0xFFFFFFFFu, active);
+    if (lane == 0) wcount[wid] = __popc(bal);
+    __syncthreads();
+    int off = 0, total = 0;
+#pragma unroll
+    for (int k = 0; k < kBX * kBY / 32; ++k) {
+      off += k < wid ? wcount[k] : 0;
+      total += wcount[k];
+    }
+    if (active) list[off + __popc(bal & ((1u << lane) - 1u))] = (unsigned short)tid;
+    __syncthreads();
+    if (tid < total) {
+      const int t = list[tid];
+      const int xx = x0 + (t % kBX), yy = y0 + (t / kBX);
+      const long long nn = (long long)(yy + kYO) * a.pitch + (xx + kXO);
+      const PreSrc<Real> src = preload(a, nn);
+      my_u = step_node<Real, kFinal, false, false, kWalls>(a, src, xx, yy, nn, a.frac);
+    }
+  } else if (x < a.nx && y < a.ny) {
     const long long n = (long long)(y + kYO) * a.pitch + (x + kXO);
     if (group_is_interior(blockIdx.x * kBX, y, a.nx, a.ny)) {
       const PreSrc<Real> src = preload(a, n);
