@@ -724,6 +724,7 @@ def main():
         del lat4
         torch.cuda.empty_cache()
         adjoint = {"ratio": adj_ms / fwd_ms, "forward_ms": fwd_ms, "adjoint_ms": adj_ms,
+                   "forward_us_per_step_graph_replay": fwd_ms * 1e3 / na,
                    "reverse_only_ratio": (adj_ms - fwd_ms) / fwd_ms, "steps": na,
                    "stride": na, "history": "whole (u and Neumann branches of every step "
                                             "stored by the forward run; no recompute)",
@@ -772,6 +773,22 @@ def main():
                 "lattice_glups": world * node_steps / (hms / 1e3) / 1e9,
                 "fem_solver_iterations_mean": float(np.mean(its)),
                 "wall_s": wall}
+            if name == "plain":
+                # the lattice's eta substeps alone, replayed from their recorded
+                # graph: the small lattice is launch-bound, so time per substep
+                lat, eta = run.lbm, layout["eta"]
+                snap = lat.save()
+                for _ in range(3):
+                    lat.substeps(eta, eta, run.ua[0], run.ub[0], run.q)
+                reps = 200
+                ev0.record(stream)
+                for _ in range(reps):
+                    lat.substeps(eta, eta, run.ua[0], run.ub[0], run.q)
+                ev1.record(stream)
+                ev1.synchronize()
+                hybrid[name]["lattice_us_per_substep_graph_replay"] = \
+                    ev0.elapsed_time(ev1) * 1e3 / (reps * eta)
+                lat.restore(snap)
             run.close()
             del run
             torch.cuda.empty_cache()
