@@ -387,6 +387,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-instances", type=int, default=256)
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--kernel", default="auto", choices=["auto", "generic", "tma"],
+                    help="FP32 step kernel of the headline lattice (auto: the library's choice)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -436,13 +438,20 @@ def main():
         lat = SlabLattice(n, n * world, whole["tau"], rank=rank, world=world, precision=32,
                           **lattice_kwargs(whole))
         ud_w, q_w = dev(whole["u_dir"]), dev(whole["q_neu"])
+        if args.kernel != "auto":
+            for sl in lat.slabs:
+                sl.set_kernel(args.kernel)
         lat.substeps(args.warmup, 1, ud_w, ud_w, q_w)
         ud, q = ud_w, q_w
         timed = lat.slabs[0]
     else:
         lat = LBM(n, n, case["tau"], precision=32, **kw)
+        if args.kernel != "auto":
+            lat.set_kernel(args.kernel)
         lat.substeps(args.warmup, 1, ud, ud, q)
         timed = lat
+    variant = timed.kernel()
+    kernel_name = {"tma": "lbm_step_tma<false>", "generic": "lbm_step<float, false>"}[variant]
     barrier()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -475,7 +484,8 @@ def main():
     per_launch_ms = step_ms / max(step_n, 1)
     achieved = bytes_step / (per_launch_ms / 1e3) / 1e9
     traffic = None
-    tpath = os.path.join(ROOT, "profiles", "lbm_step_traffic.json")
+    tpath = os.path.join(ROOT, "profiles", {"tma": "lbm_step_traffic.json",
+                                            "generic": "lbm_step_generic_traffic.json"}[variant])
     try:
         from paper_1601_02708_gb300 import build as _b
         import hashlib
@@ -566,8 +576,13 @@ def main():
         coeffs = (1.0, 2.0, 1.0)
         a_in = ud  # alpha = u_A + u_C at the inlet: the inlet value of A
         b_in = torch.zeros_like(ud)
+        probe = Bimolecular(n, n, case["tau"], coeffs, uA0, uB0, precision=32,
+                            edges=kw["edges"], solid=kw["solid"], vel=kw["vel"])
+        default_pair = probe.pair is not None  # the library's default for this size
+        probe.close()
+        del probe
         msb = {}
-        for fused in (False, True):  # two launches a substep, then the fused pair kernel
+        for fused in (False, True):  # two lattices a substep, then the fused pair kernel
             if fused:
                 bm.close()
                 del bm
@@ -601,14 +616,19 @@ def main():
         del bm, al, be, uA, uB, uC
         torch.cuda.empty_cache()
         ms_f = msb[True] / args.bimolecular_steps
+        ms_u = msb[False] / args.bimolecular_steps
+        default_fused = bool(default_pair)  # what Bimolecular(fused=None) chose
+        ms_d = ms_f if default_fused else ms_u
         n_sol = int((kw["solid"] != 0).sum())
-        # fused pair: two fields' populations, one velocity and one mask read per node
+        # two fields' populations and one velocity and mask read per node (the
+        # fused pair's algorithmic bytes; two separate lattices move these too
+        # plus a second velocity and mask)
         bp = (2 * 9 * 4 * 2 + 2 * 4 + 1) * (nodes - n_sol) + BYTES_SOLID * n_sol
-        ap_ = bp / (ms_f / 1e3) / 1e9
-        bimol = {"value": world * 2 * nodes * args.bimolecular_steps / (msb[True] / 1e3) / 1e9,
+        ap_ = bp / (ms_d / 1e3) / 1e9
+        bimol = {"value": world * 2 * nodes / (ms_d / 1e3) / 1e9,
                  "unit": "GLUPS (both invariants)", "steps": args.bimolecular_steps,
-                 "fused": True, "ms_per_step": ms_f,
-                 "unfused_ms_per_step": msb[False] / args.bimolecular_steps,
+                 "default": "fused pair" if default_fused else "two lattices",
+                 "ms_per_step": ms_d, "fused_ms_per_step": ms_f, "unfused_ms_per_step": ms_u,
                  "roofline": {"bound": "hbm", "achieved": ap_, "peak": peak, "unit": "GB/s",
                               "frac": ap_ / peak, "bytes_per_fluid_node": 2 * 9 * 4 * 2 + 2 * 4 + 1,
                               "timing": "whole substep calls (launch gaps included)"},
@@ -824,7 +844,7 @@ def main():
                                       if world > 1 else "single GPU",
                        "l2": "inputs larger than L2 (2 x 604 MB populations), no flush"},
             "fluid_glups": world * n_fluid * args.steps / (ms / 1e3) / 1e9,
-            "roofline": {"bound": "hbm", "kernel": "lbm_step_tma<false>",
+            "roofline": {"bound": "hbm", "kernel": kernel_name,
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,
                          "traffic": traffic, "algorithmic_bytes_per_launch": bytes_step,

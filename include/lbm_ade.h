@@ -296,14 +296,18 @@ lbm_status lbm_kernel_timing(lbm_ctx* c, int enable);
 lbm_status lbm_kernel_times_read(lbm_ctx* c, double* step_ms, long long* step_launches,
                                  double* dissolve_ms, long long* dissolve_launches);
 
-/* Kernel variant of the step: LBM_KERNEL_AUTO (default: the tile pipeline
- * in FP32 mode, the generic kernel in FP64 mode), LBM_KERNEL_GENERIC (one
- * thread per node reading global memory) or LBM_KERNEL_TMA (persistent
- * TMA-fed tile pipeline, FP32 only).  All variants compute the same update;
+/* Kernel variant of the step: LBM_KERNEL_AUTO (default: in FP32 mode the
+ * tile pipeline below 8 M nodes or with maximum-entropy pore walls, the
+ * generic kernel for larger lattices with bounce-back walls -- the faster of
+ * the two on GB300 in each case; the generic kernel in FP64 mode), LBM_KERNEL_GENERIC (one thread per node reading global memory) or
+ * LBM_KERNEL_TMA (persistent TMA-fed tile pipeline, FP32 only).  All variants compute the same update;
  * the choice only changes speed.  LBM_ERR_ARG for an unknown or unsupported
  * variant. */
 enum { LBM_KERNEL_AUTO = 0, LBM_KERNEL_GENERIC = 1, LBM_KERNEL_TMA = 2 };
 lbm_status lbm_set_kernel(lbm_ctx* c, int variant);
+/* The variant the context's steps run now (LBM_KERNEL_GENERIC or
+ * LBM_KERNEL_TMA) into *variant. */
+lbm_status lbm_get_kernel(lbm_ctx* c, int* variant);
 
 /* Change the stream the context launches on; wait for its work. */
 lbm_status lbm_set_stream(lbm_ctx* c, void* stream);

@@ -92,6 +92,7 @@ def load():
             "lbm_synchronize": [P],
             "lbm_kernel_timing": [P, I],
             "lbm_set_kernel": [P, I],
+            "lbm_get_kernel": [P, ctypes.POINTER(I)],
             "lbm_set_rate_field": [P, P],
             "lbm_fem_init": [ctypes.POINTER(P), ctypes.POINTER(FemParams), P, I, P, P, P],
             "lbm_fem_step": [P, P],

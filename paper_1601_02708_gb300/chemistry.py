@@ -90,8 +90,12 @@ def calcite_invariants(u1, u2, u3, stream=None):
 
 def _pair(a, b, fused):
     """The fused stepper of two lattices, or None for two separate calls
-    (fused False, or None and the lattices do not qualify)."""
+    (fused False; or None and the lattices do not qualify, or run the
+    one-thread-per-node kernel, which on the large lattices it is chosen for
+    steps two fields faster than the fused tile pipeline)."""
     if fused is False:
+        return None
+    if fused is None and a.kernel() != "tma":
         return None
     try:
         return LBMPair(a, b)
@@ -139,7 +143,7 @@ class Calcite(_TwoFields):
     ``u10``, ``u20``, ``u30`` the initial CaCO3, Ca2+, CO3^2- [ny, nx];
     ``fused`` True steps both lattices with one kernel (lbm_pair_*; an error
     where they do not qualify), False with two, None (default) fused where
-    they qualify; the other keyword arguments are those of ``LBM`` except
+    they qualify and run the tile pipeline; the other keyword arguments are those of ``LBM`` except
     the reaction ones."""
 
     def __init__(self, nx, ny, tau, ksp, u10, u20, u30, fused=None, **lattice):

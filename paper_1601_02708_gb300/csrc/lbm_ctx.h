@@ -67,6 +67,7 @@ struct lbm_ctx {
   dim3 grid, block;
   int dgrid = 0;  // persistent blocks of the dissolution pass
   bool use_tma = false;  // the FP32 step runs the tile pipeline
+  bool kernel_auto = true;  // the library chooses the FP32 step kernel
   bool tma_ready = false;
   int tma_grid = 0, ntx = 0, nty = 0;
   lbm::TmaMaps maps[2];  // pop map of f[0] / f[1]; other maps identical

@@ -391,10 +391,13 @@ __device__ __forceinline__ PreSrc<Real> preload(const StepArgs<Real>& a, long lo
   return p;
 }
 
-// Generic step: one thread per node, inputs from global memory.  Used in
-// FP64 mode; the FP32 path runs the TMA kernel instead.
+// Generic step: one thread per node, inputs from global memory.  The FP64
+// lattice's step, and the FP32 one on large lattices (lbm_set_kernel).
 template <typename Real, bool kFinal, int kWalls = 0>
-__global__ void __launch_bounds__(kBX * kBY, 4) lbm_step(const StepArgs<Real> a) {
+// FP32: six blocks of 256 per SM (40 registers) keep more loads in flight
+// than four; FP64 keeps four (64 registers) for its arithmetic.
+__global__ void __launch_bounds__(kBX * kBY, sizeof(Real) == 4 ? 6 : 4)
+    lbm_step(const StepArgs<Real> a) {
   __shared__ double red[kBX * kBY / 32];
   const int x = blockIdx.x * kBX + threadIdx.x;
   const int y = blockIdx.y * kBY + threadIdx.y;
@@ -436,8 +439,21 @@ __global__ void __launch_bounds__(kBX * kBY, 4) lbm_step(const StepArgs<Real> a)
   } else if (x < a.nx && y < a.ny) {
     const long long n = (long long)(y + kYO) * a.pitch + (x + kXO);
     if (group_is_interior(blockIdx.x * kBX, y, a.nx, a.ny)) {
+      // the warp's class by its link words: all clear of solids, all solid
+      // (u only), or general (solid lanes compute on their finite inputs and
+      // discard the result, so the warp takes one path)
+      // (FP32 only: the FP64 lattice's interior blocks are packed above, and
+      // its other nodes keep the one path that the batch's FP64 kernels share)
       const PreSrc<Real> src = preload(a, n);
-      my_u = step_node<Real, kFinal, false, false, kWalls>(a, src, x, y, n, a.frac);
+      if (sizeof(Real) == 8)
+        my_u = step_node<Real, kFinal, false, false, kWalls>(a, src, x, y, n, a.frac);
+      else if (__all_sync(0xFFFFFFFFu, (src.w & kClearMask) == 0u))
+        my_u = step_node<Real, kFinal, false, false, kWalls, true, true>(a, src, x, y, n, a.frac);
+      else if (__all_sync(0xFFFFFFFFu, (src.w & (kOwnSolid | kOwnPending)) == kOwnSolid)) {
+        if (kFinal) a.u_out[dbg_idx(n, a.plane, a.status, kSiteNode)] = (Real)0;
+        if (a.u_hist) a.u_hist[dbg_idx(n, a.plane, a.status, kSiteNode)] = (Real)0;
+      } else
+        my_u = step_node<Real, kFinal, false, false, kWalls, true>(a, src, x, y, n, a.frac);
     } else {
       GlobalSrc<Real> src{a, n};
       my_u = step_node<Real, kFinal, true, true, kWalls>(a, src, x, y, n, a.frac);

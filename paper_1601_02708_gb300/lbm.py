@@ -220,6 +220,12 @@ class LBM:
         tile pipeline); every variant computes the same update."""
         check(self._lib.lbm_set_kernel(self.handle, self.KERNELS[variant]))
 
+    def kernel(self):
+        """The step kernel the lattice runs now: "generic" or "tma"."""
+        v = ctypes.c_int()
+        check(self._lib.lbm_get_kernel(self.handle, ctypes.byref(v)))
+        return {1: "generic", 2: "tma"}[v.value]
+
     def kernel_timing(self, enable=True):
         """Record CUDA events around every step and dissolution launch."""
         check(self._lib.lbm_kernel_timing(self.handle, int(bool(enable))))

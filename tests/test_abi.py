@@ -80,14 +80,22 @@ def test_calcite_refuses_reaction_arguments():
 
 
 def test_chemistry_pairs_only_when_asked_or_possible():
-    """fused=False never makes a pair; fused=None falls back to two
-    separate lattices when the pair is refused; fused=True passes the
-    refusal on (a stand-in pair constructor, no GPU)."""
+    """fused=False never makes a pair; fused=None makes none for lattices
+    on the one-thread-per-node kernel and falls back to two separate
+    lattices when the pair is refused; fused=True passes the refusal on
+    (stand-in lattices and pair constructor, no GPU)."""
     import pytest
     from paper_1601_02708_gb300 import chemistry
 
     class Refused(Exception):
         pass
+
+    class Lat:
+        def __init__(self, kernel):
+            self._k = kernel
+
+        def kernel(self):
+            return self._k
 
     calls = []
 
@@ -95,12 +103,14 @@ def test_chemistry_pairs_only_when_asked_or_possible():
         calls.append((a, b))
         raise Refused()
 
+    tma, plain = Lat("tma"), Lat("generic")
     orig = chemistry.LBMPair
     chemistry.LBMPair = refuse
     try:
-        assert chemistry._pair("a", "b", False) is None and not calls
-        assert chemistry._pair("a", "b", None) is None and len(calls) == 1
+        assert chemistry._pair(tma, tma, False) is None and not calls
+        assert chemistry._pair(plain, plain, None) is None and not calls
+        assert chemistry._pair(tma, tma, None) is None and len(calls) == 1
         with pytest.raises(Refused):
-            chemistry._pair("a", "b", True)
+            chemistry._pair(plain, plain, True)
     finally:
         chemistry.LBMPair = orig
