@@ -518,7 +518,7 @@ lbm_status init_impl(lbm_ctx* c, const uint8_t* solid, const double* vel,
   c->block = dim3(lbm::kBX, lbm::kBY);
   c->grid = dim3((p.nx + lbm::kBX - 1) / lbm::kBX, (p.ny + lbm::kBY - 1) / lbm::kBY);
   const size_t plane_b = (size_t)c->plane * c->esize;
-  const int per_x = p.edge[0] == LBM_EDGE_PERIODIC, per_y = p.edge[2] == LBM_EDGE_PERIODIC;
+  const int per_x = p.edge[0] == LBM_EDGE_PERIODIC;
   CK(cudaGetDevice(&c->device));
   CK(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
   {
@@ -840,6 +840,12 @@ void ctx_drop_recorded(lbm_ctx* c, int kind) {
   }
   for (auto it = c->seen.begin(); it != c->seen.end();)
     it = std::get<0>(*it) == kind ? c->seen.erase(it) : std::next(it);
+}
+
+lbm_status ctx_make_map(const char* what, CUtensorMap* m, CUtensorMapDataType dt, int rank,
+                        void* base, const cuuint64_t* dims, const cuuint64_t* strides,
+                        const cuuint32_t* box) {
+  return make_map(what, m, dt, rank, base, dims, strides, box);
 }
 
 template <typename Real>

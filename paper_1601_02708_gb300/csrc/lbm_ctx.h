@@ -109,6 +109,11 @@ void ctx_drop_recorded(lbm_ctx* c, int kind);
 
 // Services of lbm_api.cu for the other translation units of the library.
 lbm_status ctx_fail(lbm_status s, const char* fmt, ...);  // message of lbm_last_error
+// A tiled tensor map (no swizzle, no interleave, L2 promotion 128 B) of a
+// rank-2 or rank-3 array; LBM_ERR_CUDA naming `what` if it cannot be made.
+lbm_status ctx_make_map(const char* what, CUtensorMap* m, CUtensorMapDataType dt, int rank,
+                        void* base, const cuuint64_t* dims, const cuuint64_t* strides,
+                        const cuuint32_t* box);
 lbm_status ctx_check(const lbm_ctx* c);                    // null context
 lbm_status ctx_status(lbm_ctx* c);   // waits for the stream, reads the device error word
 bool ctx_on_device(const void* p);

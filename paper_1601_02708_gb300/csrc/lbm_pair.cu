@@ -176,33 +176,6 @@ __global__ void k_same_geometry(const uint32_t* __restrict__ la, const uint32_t*
     if (la[i] != lb[i] || va[i] != vb[i] || va[plane + i] != vb[plane + i]) *differ = 1;
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 encode() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                         &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-    else
-      cudaGetLastError();
-  }
-  return fn;
-}
-
-lbm_status map(CUtensorMap* m, CUtensorMapDataType dt, int rank, void* base,
-               const cuuint64_t* dims, const cuuint64_t* strides, const cuuint32_t* box) {
-  auto enc = encode();
-  if (!enc) return ctx_fail(LBM_ERR_CUDA, "lbm_pair_create: cuTensorMapEncodeTiled unavailable");
-  const cuuint32_t es[3] = {1, 1, 1};
-  if (enc(m, dt, (cuuint32_t)rank, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-    return ctx_fail(LBM_ERR_CUDA, "lbm_pair_create: cuTensorMapEncodeTiled failed");
-  return LBM_OK;
-}
-
 }  // namespace
 
 struct lbm_pair {
@@ -258,13 +231,20 @@ lbm_status lbm_pair_create(lbm_pair** out, lbm_ctx* a, lbm_ctx* b) {
     PairMaps& m = pr->maps[par];
     for (int f = 0; f < 2 && st == LBM_OK; ++f) {
       lbm_ctx* c = pr->c[f];
-      st = map(&m.pop[f], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, c->f[par], dpop, spop, bpop);
+      st = ctx_make_map("pair population", &m.pop[f], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                        c->f[par], dpop, spop, bpop);
       if (st == LBM_OK)
-        st = c->kf ? map(&m.kf[f], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, c->kf, d2, s2, b2)
-                   : map(&m.kf[f], CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, a->link, d2, s2, b2);
+        st = c->kf ? ctx_make_map("pair rate", &m.kf[f], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                                  c->kf, d2, s2, b2)
+                   : ctx_make_map("pair rate", &m.kf[f], CU_TENSOR_MAP_DATA_TYPE_UINT32, 2,
+                                  a->link, d2, s2, b2);
     }
-    if (st == LBM_OK) st = map(&m.vel, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, a->vel, dvel, spop, bvel);
-    if (st == LBM_OK) st = map(&m.link, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, a->link, d2, s2, b2);
+    if (st == LBM_OK)
+      st = ctx_make_map("pair velocity", &m.vel, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, a->vel, dvel,
+                        spop, bvel);
+    if (st == LBM_OK)
+      st = ctx_make_map("pair link", &m.link, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, a->link, d2, s2,
+                        b2);
   }
   if (st == LBM_OK &&
       (cudaFuncSetAttribute(lbm_step_tma_pair<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,

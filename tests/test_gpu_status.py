@@ -124,3 +124,27 @@ def test_status_numbering(gb):
     with pytest.raises(gb.LBMError) as e:
         gb.LBM(8, 8, 0.8, precision=32).flip_steps()  # no dissolution
     assert e.value.status == -5
+
+
+def test_kernel_choice(gb):
+    """LBM_KERNEL_AUTO: the tile pipeline below 8 M nodes or with
+    maximum-entropy walls, the plain kernel for larger bounce-back lattices;
+    an explicit choice survives a change of wall treatment; FP64 runs the
+    plain kernel."""
+    small = gb.LBM(64, 64, 0.8)
+    assert small.kernel() == "tma"
+    big = gb.LBM(2900, 2900, 0.8)  # 8.4 M nodes
+    assert big.kernel() == "generic"
+    big.set_walls("maxent_lattice")
+    assert big.kernel() == "tma"
+    big.set_walls("bounce")
+    assert big.kernel() == "generic"
+    big.set_kernel("tma")
+    big.set_walls("maxent")
+    big.set_walls("bounce")
+    assert big.kernel() == "tma"
+    big.set_kernel("auto")
+    assert big.kernel() == "generic"
+    assert gb.LBM(64, 64, 0.8, precision=64).kernel() == "generic"
+    small.close()
+    big.close()
