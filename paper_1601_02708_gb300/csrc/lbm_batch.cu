@@ -241,11 +241,11 @@ __global__ void __launch_bounds__(lbm::kDThreads)
                        const int* __restrict__ nblk) {
   __shared__ lbm::DissolveArgs d;
   __shared__ bool last;
-  __shared__ double tab[84];
+  const double* const tab = lbm::share_table();
   const int tid = threadIdx.x;
   const int2 bm = bmap[blockIdx.x];
   if (tid == 0) d = dargs[bm.x];
-  lbm::share_table(tab);  // synchronises the block
+  __syncthreads();
   const Share* rlink = (const Share*)rlinks[bm.x];
   const int nb = nblk[bm.x];
   const int pass = *(volatile int*)d.pass;

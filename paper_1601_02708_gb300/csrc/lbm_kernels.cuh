@@ -636,20 +636,31 @@ __device__ __forceinline__ double mineral_take(const ShareF32* __restrict__ sh, 
   return ((double)S + (double)E) * d.k_scalar;
 }
 
-// The tables of mineral_take for the FP32 lattice, in shared memory:
-// tab[t][c] = 36 w_t / c in FP64 (36 w_t = 4 axis, 1 diagonal; tab[t][0] = 0),
-// then the same 42 values as float pairs hi + lo (hi the float nearest, lo
-// the float nearest the remainder).  84 doubles of storage.
-__device__ __forceinline__ void share_table(double* tab) {
-  F2* tf = reinterpret_cast<F2*>(tab + 42);
-  for (int i = threadIdx.x; i < 42; i += blockDim.x) {
+// The tables of mineral_take for the FP32 lattice: tab[t][c] = 36 w_t / c
+// in FP64 (36 w_t = 4 axis, 1 diagonal; tab[t][0] = 0), then the same 42
+// values as float pairs hi + lo (hi the float nearest, lo the float nearest
+// the remainder).  Computed by the compiler (IEEE division and conversions,
+// as on the device) into device memory, so no block spends time building
+// them; share_table() returns them as 84 doubles of storage.
+struct ShareTab {
+  double d[42];
+  F2 f[42];
+};
+constexpr ShareTab make_share_tab() {
+  ShareTab t{};
+  for (int i = 0; i < 42; ++i) {
     const int c = i % 21;
     const double v = c == 0 ? 0.0 : (i < 21 ? 4.0 : 1.0) / (double)c;
-    tab[i] = v;
+    t.d[i] = v;
     const float hi = (float)v;
-    tf[i] = F2{hi, (float)(v - (double)hi)};
+    t.f[i] = F2{hi, (float)(v - (double)hi)};
   }
-  __syncthreads();
+  return t;
+}
+__device__ const ShareTab kShareTab = make_share_tab();
+static_assert(sizeof(ShareTab) == 84 * sizeof(double), "tables of 84 doubles");
+__device__ __forceinline__ const double* share_table() {
+  return reinterpret_cast<const double*>(&kShareTab);
 }
 
 // Mark every node of the flip list pending (solid for the next streaming,
@@ -700,8 +711,7 @@ constexpr int kDThreads = 256;
 template <typename Share>
 __global__ void __launch_bounds__(kDThreads)
     lbm_dissolve_list(const DissolveArgs d, const Share* __restrict__ rlink) {
-  __shared__ double tab[84];
-  share_table(tab);
+  const double* const tab = share_table();
   const int tid = threadIdx.x;
   const int pass = *(volatile int*)d.pass;
   bool flipped = false;
@@ -740,8 +750,7 @@ __global__ void __launch_bounds__(kDThreads)
 template <typename Share>
 __global__ void __launch_bounds__(kDThreads)
     lbm_dissolve_dense(const DissolveArgs d, const Share* __restrict__ rlink) {
-  __shared__ double tab[84];
-  share_table(tab);
+  const double* const tab = share_table();
   const int tid = threadIdx.x;
   const int pass = *(volatile int*)d.pass;
   bool flipped = false;
