@@ -153,7 +153,9 @@ lbm_status lbm_substeps(lbm_ctx* c, int n, int eta, const double* u_dir_t0,
 
 /* LBM -> FEM transfer, Sec. 6.2 (ii): bilinear value of the current u at
  * npts points xy[npts][2] given in lattice coordinates.  A point outside
- * [0, nx-1] x [0, ny-1] across a non-periodic side yields NaN. */
+ * [0, nx-1] x [0, ny-1] across a non-periodic side yields NaN.  With xy and
+ * u_out both in device memory the call is asynchronous on the context's
+ * stream; otherwise it waits. */
 lbm_status lbm_interface_trace(lbm_ctx* c, int npts, const double* xy,
                                double* u_out);
 
@@ -280,7 +282,12 @@ void lbm_pair_destroy(lbm_pair* p);
 /* Schwarz rollback (Algorithm 1 restarts every sub-iteration from the state
  * at the start of the coarse step): lbm_state_bytes gives the size of a
  * state blob; lbm_save writes the full state into a caller-owned buffer of
- * at least that size; lbm_restore reads it back into the same context. */
+ * at least that size; lbm_restore reads it back into the same context.
+ * lbm_save into device memory is asynchronous on the context's stream (the
+ * blob is complete when the stream reaches that point); into host memory it
+ * waits.  lbm_restore waits for the stream to read the blob's header (a
+ * blob of another lattice is LBM_ERR_STATE), then queues the copies; from
+ * host memory it waits for them too. */
 lbm_status lbm_state_bytes(lbm_ctx* c, size_t* bytes);
 lbm_status lbm_save(lbm_ctx* c, void* buf, size_t bytes);
 lbm_status lbm_restore(lbm_ctx* c, const void* buf, size_t bytes);
@@ -442,7 +449,9 @@ lbm_status lbm_fem_step(lbm_fem* f, const double* dir_values);
  * xy [npts][2] (physical coordinates; points outside are clamped to the
  * nearest element): the coarse-to-fine transfer of Sec. 5.1 / 6.2 (iii). */
 lbm_status lbm_fem_interpolate(lbm_fem* f, int npts, const double* xy, double* out);
-lbm_status lbm_fem_get(lbm_fem* f, double* d);        /* [(ney+1)(nex+1)] */
+/* d [(ney+1)(nex+1)]: into device memory asynchronous on the solver's
+ * stream, into host memory it waits. */
+lbm_status lbm_fem_get(lbm_fem* f, double* d);
 lbm_status lbm_fem_set(lbm_fem* f, const double* d);  /* e.g. the Schwarz rollback */
 /* Iterations and relative residual of the last solve. */
 lbm_status lbm_fem_solver_info(lbm_fem* f, int* iters, double* rel_resid);

@@ -427,6 +427,7 @@ void free_ctx(lbm_ctx* c) {
                   c->jflux,  c->open_nodes, c->flip_step};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  if (c->pinned) cudaFreeHost(c->pinned);
   ctx_adjoint_free(c);
   delete c;
 }
@@ -581,6 +582,7 @@ lbm_status init_impl(lbm_ctx* c, const uint8_t* solid, const double* vel,
   CK(cudaMemsetAsync(c->counters, 0, 4 * sizeof(long long), c->stream));
   CK(cudaMalloc((void**)&c->status, sizeof(int)));
   CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
+  CK(cudaMallocHost(&c->pinned, 256));
   CK(cudaMalloc((void**)&c->edge, 3 * (size_t)c->nedge * sizeof(double)));
   CK(cudaMemsetAsync(c->edge, 0, 3 * (size_t)c->nedge * sizeof(double), c->stream));
   CK(cudaMalloc((void**)&c->infeasible, (size_t)c->nedge * sizeof(long long)));
@@ -674,9 +676,10 @@ lbm_status check_ctx(const lbm_ctx* c) {
 
 // Reads the device status word (waits for the stream).
 lbm_status check_status(lbm_ctx* c) {
-  int st = 0;
-  CK(cudaMemcpyAsync(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  int* hs = (int*)c->pinned;
+  CK(cudaMemcpyAsync(hs, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
+  const int st = *hs;
   if (st >= lbm::kSiteBase)
     return fail(LBM_ERR_STATE, "index check %d failed (debug-bounds build)", st);
   if (st) return fail(LBM_ERR_TIMEOUT, "a kernel's bounded wait expired (status %d)", st);
@@ -734,6 +737,13 @@ struct BlobHeader {
   int nx, ny, precision, dissolution, nparts, pad;
 };
 const unsigned long long kMagic = 0x4C424D4144453035ull;  // "LBMADE05"
+static_assert(sizeof(BlobHeader) <= 64, "the header fits its pinned read-back slot");
+
+// Write a blob header into device memory byte by byte (any alignment).
+__global__ void k_put_blob_header(unsigned char* dst, const BlobHeader h) {
+  const unsigned char* src = reinterpret_cast<const unsigned char*>(&h);
+  for (int i = threadIdx.x; i < (int)sizeof(BlobHeader); i += blockDim.x) dst[i] = src[i];
+}
 
 // Copy a padded device field out to a caller array (host or device) of
 // `planes` [ny][nx] planes, converting to O.
@@ -1075,6 +1085,8 @@ lbm_status lbm_interface_trace(lbm_ctx* c, int npts, const double* xy, double* u
     CK(cudaStreamSynchronize(c->stream));
   } else if (!xy_dev) {
     CK(cudaStreamSynchronize(c->stream));
+  } else {
+    return LBM_OK;  // device in and out: asynchronous on the stream
   }
   return check_status(c);
 }
@@ -1194,8 +1206,15 @@ lbm_status lbm_save(lbm_ctx* c, void* buf, size_t bytes) {
   const cudaMemcpyKind k = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   TRY(sync_mineral(c));
   BlobHeader h{kMagic, c->steps, c->p.nx, c->p.ny, c->p.precision, c->p.dissolution, c->nparts, 0};
-  CK(cudaMemcpyAsync(buf, &h, sizeof(h), dev ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost,
-                     c->stream));
+  if (dev) {
+    // the header travels as a kernel argument: nothing on this stack frame
+    // is read after the call returns, so a save into device memory need
+    // not wait
+    k_put_blob_header<<<1, 32, 0, c->stream>>>((unsigned char*)buf, h);
+    CK(cudaGetLastError());
+  } else {
+    memcpy(buf, &h, sizeof(h));
+  }
   Section s[16];
   const int n = state_sections(c, s);
   size_t off = align256(sizeof(BlobHeader));
@@ -1203,8 +1222,8 @@ lbm_status lbm_save(lbm_ctx* c, void* buf, size_t bytes) {
     CK(cudaMemcpyAsync((char*)buf + off, s[i].ptr, s[i].bytes, k, c->stream));
     off += align256(s[i].bytes);
   }
-  CK(cudaStreamSynchronize(c->stream));  // the header lives on this stack frame
-  return check_status(c);
+  if (dev) return LBM_OK;
+  return check_status(c);  // waits: the host blob is complete on return
 }
 
 lbm_status lbm_restore(lbm_ctx* c, const void* buf, size_t bytes) {
@@ -1213,9 +1232,15 @@ lbm_status lbm_restore(lbm_ctx* c, const void* buf, size_t bytes) {
   if (!buf || bytes < need) return fail(LBM_ERR_ARG, "lbm_restore: buffer smaller than lbm_state_bytes");
   const bool dev = on_device(buf);
   BlobHeader h;
-  CK(cudaMemcpyAsync(&h, buf, sizeof(h), dev ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost,
-                     c->stream));
-  CK(cudaStreamSynchronize(c->stream));
+  if (dev) {
+    BlobHeader* hh = (BlobHeader*)((char*)c->pinned + 64);
+    CK(cudaMemcpyAsync(hh, buf, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    h = *hh;
+  } else {
+    CK(cudaStreamSynchronize(c->stream));  // the sections below overwrite the state
+    memcpy(&h, buf, sizeof(h));
+  }
   if (h.magic != kMagic || h.nx != c->p.nx || h.ny != c->p.ny ||
       h.precision != c->p.precision || h.dissolution != c->p.dissolution)
     return fail(LBM_ERR_STATE, "lbm_restore: blob does not belong to this lattice");

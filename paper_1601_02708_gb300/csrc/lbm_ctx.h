@@ -61,6 +61,7 @@ struct lbm_ctx {
   int* status = nullptr;          // device error word
   DiagDev* diag = nullptr;
   void* scratch = nullptr;  // staging for host outputs
+  void* pinned = nullptr;   // page-locked host words: status and blob-header read-backs
   size_t scratch_bytes = 0;
   long long steps = 0;
   int nedge = 0;

@@ -374,6 +374,210 @@ __global__ void __launch_bounds__(kThreads) k_bicgstab(const Solve S) {
   }
 }
 
+// ---- the linear solve of a small system in one block -----------------------
+// The same preconditioned BiCGSTAB with its vectors in shared memory, for
+// systems of at most kSmallNodes nodes, run by one block.  One SM then does
+// all the FP64 work, at 1/64 of the FP32 rate on this part (an FP64 warp
+// instruction holds the SM's FP64 pipe for about 16 cycles), so the work
+// that is the same for every thread is done once: each warp folds its
+// threads' partial sums, thread 0 adds the warp sums in warp order and forms
+// the iteration's scalars (alpha, omega, beta), and the others read them
+// from shared memory.  The preconditioned vectors p invd and s invd are
+// formed once an iteration behind a barrier, where the cooperative solve
+// re-forms them at every neighbour to save grid barriers.
+constexpr int kSmallThreads = 256;
+constexpr long long kSmallNodes = 2048;
+constexpr int kSmallVecs = 9;  // x, r, rhat, p, v, s, t, p invd, s invd
+
+// Warp sums of two values into red[0][warp], red[1][warp].
+__device__ __forceinline__ void small_warp_sums(double a, double b, double (*red)[kSmallThreads / 32]) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = a;
+    red[1][threadIdx.x >> 5] = b;
+  }
+}
+
+__global__ void __launch_bounds__(kSmallThreads) k_bicgstab_small(const Solve S) {
+  extern __shared__ double sm[];
+  __shared__ double red[2][kSmallThreads / 32];
+  // broadcast of thread 0's scalars: alpha, omega, beta; and its verdict
+  __shared__ double bc[3];
+  __shared__ int stop;  // 0 go on, 1 converged, 2 broke down
+  constexpr int kW = kSmallThreads / 32;
+  const int n = (int)S.n, nxn = S.nxn, nyn = S.nyn;
+  double* x = sm;
+  double* r = sm + n;
+  double* rh = sm + 2 * n;
+  double* p = sm + 3 * n;
+  double* v = sm + 4 * n;
+  double* s = sm + 5 * n;
+  double* t = sm + 6 * n;
+  double* y = sm + 7 * n;  // p invd (and d^n in the prologue)
+  double* z = sm + 8 * n;  // s invd (and b in the prologue)
+  const int q0 = threadIdx.x;
+  const bool lead = threadIdx.x == 0;
+  // row q of M u for a vector u in shared memory
+  auto row = [&](const double* __restrict__ M, const double* u, int q) {
+    const int i = q % nxn, j = q / nxn;
+    double acc = 0.0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const int ii = i + k % 3 - 1, jj = j + k / 3 - 1;
+      if (ii < 0 || ii >= nxn || jj < 0 || jj >= nyn) continue;
+      acc += __ldg(M + (long long)k * n + q) * u[jj * nxn + ii];
+    }
+    return acc;
+  };
+  for (int q = q0; q < n; q += kSmallThreads) y[q] = S.d[q];
+  __syncthreads();
+  // right-hand side (prescribed rows: their values), initial guess
+  double bb = 0.0;
+  for (int q = q0; q < n; q += kSmallThreads) {
+    const int f = S.fixed_id[q];
+    double bv, xv;
+    if (f >= 0) {
+      bv = S.fixed_val[f];
+      xv = bv;
+    } else if (f == -2) {
+      bv = 0.0;
+      xv = 0.0;
+    } else {
+      bv = row(S.B, y, q);
+      xv = S.warm ? S.w.x[q] : y[q];
+    }
+    z[q] = bv;
+    x[q] = xv;
+    if (f == -1) bb += bv * bv;
+  }
+  __syncthreads();
+  // r = b - A x, rhat = r, p = r, v = 0
+  double rr = 0.0;
+  for (int q = q0; q < n; q += kSmallThreads) {
+    const double rq = z[q] - row(S.A, x, q);
+    r[q] = rq;
+    rh[q] = rq;
+    p[q] = rq;
+    v[q] = 0.0;
+    rr += rq * rq;
+  }
+  small_warp_sums(bb, rr, red);
+  __syncthreads();
+  // thread 0's state: norms, rho and the iteration count
+  double bnorm2 = 0.0, rnorm2 = 0.0, tol2 = 0.0, rho = 0.0;
+  int it = 0;
+  if (lead) {
+    for (int k = 0; k < kW; ++k) {
+      bnorm2 += red[0][k];
+      rnorm2 += red[1][k];
+    }
+    tol2 = S.tol * S.tol * bnorm2;
+    rho = rnorm2;
+    bc[0] = bc[1] = bc[2] = 0.0;
+    stop = rnorm2 <= tol2 ? 1 : 0;
+  }
+  __syncthreads();
+  while (!stop) {
+    const double beta = bc[2], omega_old = bc[1];
+    for (int q = q0; q < n; q += kSmallThreads) {
+      const double pq = r[q] + beta * (p[q] - omega_old * v[q]);
+      p[q] = pq;
+      y[q] = pq * S.invd[q];
+    }
+    __syncthreads();
+    double d0 = 0.0;
+    for (int q = q0; q < n; q += kSmallThreads) {
+      const double vq = row(S.A, y, q);
+      v[q] = vq;
+      d0 += rh[q] * vq;
+    }
+    small_warp_sums(d0, 0.0, red);
+    __syncthreads();
+    if (lead) {
+      double sum = 0.0;
+      for (int k = 0; k < kW; ++k) sum += red[0][k];
+      if (sum == 0.0 || !isfinite(sum))
+        stop = 2;
+      else
+        bc[0] = rho / sum;
+    }
+    __syncthreads();
+    if (stop) break;
+    const double alpha = bc[0];
+    for (int q = q0; q < n; q += kSmallThreads) {
+      const double sq = r[q] - alpha * v[q];
+      s[q] = sq;
+      z[q] = sq * S.invd[q];
+    }
+    __syncthreads();
+    double ts = 0.0, tt = 0.0;
+    for (int q = q0; q < n; q += kSmallThreads) {
+      const double tq = row(S.A, z, q);
+      t[q] = tq;
+      ts += tq * s[q];
+      tt += tq * tq;
+    }
+    small_warp_sums(ts, tt, red);
+    __syncthreads();
+    if (lead) {
+      double a = 0.0, b = 0.0;
+      for (int k = 0; k < kW; ++k) {
+        a += red[0][k];
+        b += red[1][k];
+      }
+      bc[1] = b > 0.0 ? a / b : 0.0;
+    }
+    __syncthreads();
+    const double omega = bc[1];
+    double rhn = 0.0;
+    rr = 0.0;
+    for (int q = q0; q < n; q += kSmallThreads) {
+      x[q] += alpha * y[q] + omega * z[q];
+      const double rq = s[q] - omega * t[q];
+      r[q] = rq;
+      rhn += rh[q] * rq;
+      rr += rq * rq;
+    }
+    small_warp_sums(rhn, rr, red);
+    __syncthreads();
+    if (lead) {
+      double rho_new = 0.0;
+      rnorm2 = 0.0;
+      for (int k = 0; k < kW; ++k) {
+        rho_new += red[0][k];
+        rnorm2 += red[1][k];
+      }
+      ++it;
+      if (rnorm2 <= tol2)
+        stop = 1;
+      else if (rho_new == 0.0 || omega == 0.0 || !isfinite(rho_new))
+        stop = 2;
+      else if (it >= S.max_iter)
+        stop = 3;
+      else
+        bc[2] = (rho_new / rho) * (alpha / omega);
+      rho = rho_new;
+    }
+    __syncthreads();
+  }
+  // the solution, and the warm start of the next solve
+  for (int q = q0; q < n; q += kSmallThreads) {
+    S.d[q] = x[q];
+    S.w.x[q] = x[q];
+  }
+  if (lead) {
+    S.sc->bnorm2 = bnorm2;
+    S.sc->rnorm2 = rnorm2;
+    S.sc->done = stop == 1 ? 1 : 0;
+    S.sc->breakdown = stop == 2 ? 1 : 0;
+    *S.iters = it;
+  }
+}
+
 // FE interpolation (bilinear on the containing element) of d at points
 __global__ void k_interp(const double* __restrict__ d, int nex, int ney, double x0, double y0,
                          double hx, double hy, const double* __restrict__ xy, int npts,
@@ -416,6 +620,8 @@ struct lbm_fem {
   int* status = nullptr;
   int grid = 0;             // blocks of the cooperative solve (all resident)
   double* scratch = nullptr;  // staging of host points / results of lbm_fem_interpolate
+  void* pinned = nullptr;     // page-locked read-back of a solve's outcome
+  bool small = false;         // solved by k_bicgstab_small (n <= kSmallNodes)
   size_t scratch_n = 0;
   int last_iters = 0;
   double last_resid = 0.0;
@@ -434,6 +640,7 @@ void fem_free(lbm_fem* f) {
                   f->sc, f->iters, f->scratch, f->bar, f->status, f->invd};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  if (f->pinned) cudaFreeHost(f->pinned);
   delete f;
 }
 
@@ -589,8 +796,13 @@ lbm_status lbm_fem_init(lbm_fem** out, const lbm_fem_params* p, const uint8_t* e
     long long cap = (long long)sms * (per_sm < 2 ? per_sm : 2);
     if (cap > kFoldCap) cap = kFoldCap;  // partials one fold can take
     f->grid = (int)(need < cap ? need : cap);
+    f->small = n <= kSmallNodes;
+    if (f->small && e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_bicgstab_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(kSmallVecs * kSmallNodes * sizeof(double)));
   }
   al((void**)&f->part, 4 * (size_t)(f->grid > 0 ? f->grid : 1) * sizeof(double));
+  if (e == cudaSuccess) e = cudaMallocHost(&f->pinned, 256);
   al((void**)&f->sc, sizeof(Scal));
   al((void**)&f->iters, sizeof(int));
   al((void**)&f->bar, 2 * sizeof(unsigned));
@@ -639,11 +851,18 @@ lbm_status lbm_fem_step(lbm_fem* f, const double* dir_values) {
   S.max_iter = f->p.max_iter;
   S.warm = f->warm ? 1 : 0;
   void* args[] = {&S};
-  FCK(cudaLaunchCooperativeKernel((const void*)k_bicgstab, dim3(f->grid), dim3(kThreads), args, 0, s));
-  struct {
+  if (f->small)
+    k_bicgstab_small<<<1, kSmallThreads, kSmallVecs * f->n * sizeof(double), s>>>(S);
+  else
+    FCK(cudaLaunchCooperativeKernel((const void*)k_bicgstab, dim3(f->grid), dim3(kThreads), args,
+                                    0, s));
+  FCK(cudaGetLastError());
+  struct Outcome {
     Scal sc;
     int iters, status;
-  } h;
+  };
+  static_assert(sizeof(Outcome) <= 256, "the outcome fits its pinned read-back");
+  Outcome& h = *(Outcome*)f->pinned;
   FCK(cudaMemcpyAsync(&h.sc, f->sc, sizeof(Scal), cudaMemcpyDeviceToHost, s));
   FCK(cudaMemcpyAsync(&h.iters, f->iters, sizeof(int), cudaMemcpyDeviceToHost, s));
   FCK(cudaMemcpyAsync(&h.status, f->status, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -702,7 +921,7 @@ lbm_status lbm_fem_interpolate(lbm_fem* f, int npts, const double* xy, double* o
 lbm_status lbm_fem_get(lbm_fem* f, double* d) {
   if (!f || !d) return ctx_fail(LBM_ERR_ARG, "lbm_fem_get: null argument");
   FCK(cudaMemcpyAsync(d, f->d, f->n * sizeof(double), cudaMemcpyDefault, f->stream));
-  FCK(cudaStreamSynchronize(f->stream));
+  if (!ctx_on_device(d)) FCK(cudaStreamSynchronize(f->stream));
   return LBM_OK;
 }
 

@@ -107,10 +107,14 @@ class Hybrid:
         for it in range(self.max_iter):
             if it > 0:
                 fem.set(self.d_n)
-                for lat, snap in zip(self.lbms, self.snaps):
-                    lat.restore(snap)
+            # the continuum solve waits for its outcome, so the lattices'
+            # restores (which wait to read their blob headers) come after it
+            # and find the stream drained
             fem.step(self.dir_values)
             self.solver_iters.append(fem.solver_info()[0])
+            if it > 0:
+                for lat, snap in zip(self.lbms, self.snaps):
+                    lat.restore(snap)
             for k in range(len(self.lbms)):
                 fem.interpolate(self.points[k], out=self.ub_out[k])
             self._substeps()

@@ -35,11 +35,13 @@ def _oracle_run(layout, n_coarse):
     return fem, lbm
 
 
+# 38 x 12 nodes are solved by one block, 98 x 54 (above 4096 nodes) by the
+# cooperative launch over several blocks
+@pytest.mark.parametrize("nex,ney", [(37, 11), (97, 53)])
 @pytest.mark.parametrize("supg,hole", [(True, False), (False, True)])
-def test_fem_matches_oracle(pkg, oracle_mod, supg, hole):
+def test_fem_matches_oracle(pkg, oracle_mod, supg, hole, nex, ney):
     from oracle.fem import Q1FEM
     from paper_1601_02708_gb300.fem import FEM
-    nex, ney = 37, 11
     rng = np.random.default_rng(7)
     act = None
     if hole:
