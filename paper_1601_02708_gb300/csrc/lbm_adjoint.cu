@@ -34,6 +34,7 @@
 // every step itself and nothing is recomputed.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -263,7 +264,8 @@ lbm_status ensure_work(lbm_ctx* c, int K, int L) {
   ACK(cudaMalloc((void**)&w->gk32, (size_t)c->plane * sizeof(float)));
   ACK(cudaMalloc((void**)&w->ge, 3 * ne * sizeof(double)));
   ACK(cudaMalloc((void**)&w->jn0, (size_t)c->p.ny * sizeof(double)));
-  const size_t parts = (size_t)c->grid.x * c->grid.y;
+  // partials of a 32 x 8 launch or of a step launch, whichever is more
+  const size_t parts = std::max((size_t)c->grid.x * c->grid.y, (size_t)c->sgrid.x * c->sgrid.y);
   ACK(cudaMalloc((void**)&w->part, parts * sizeof(double)));
   ACK(cudaMalloc((void**)&w->jn, (size_t)c->p.ny * sizeof(double)));
   ACK(cudaMalloc((void**)&w->inf, ne * sizeof(long long)));

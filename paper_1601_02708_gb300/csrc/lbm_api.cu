@@ -332,10 +332,10 @@ lbm_status launch_step_kernels(lbm_ctx* c, const lbm::StepArgs<Real>& a, bool fi
     if (final_step) c->nparts = c->tma_grid;
   } else {
     if (final_step)
-      lbm::lbm_step<Real, true, kWalls><<<c->grid, c->block, 0, c->stream>>>(a);
+      lbm::lbm_step<Real, true, kWalls><<<c->sgrid, c->sblock, 0, c->stream>>>(a);
     else
-      lbm::lbm_step<Real, false, kWalls><<<c->grid, c->block, 0, c->stream>>>(a);
-    if (final_step) c->nparts = (int)(c->grid.x * c->grid.y);
+      lbm::lbm_step<Real, false, kWalls><<<c->sgrid, c->sblock, 0, c->stream>>>(a);
+    if (final_step) c->nparts = (int)(c->sgrid.x * c->sgrid.y);
   }
   CK(cudaGetLastError());
   return LBM_OK;
@@ -518,6 +518,11 @@ lbm_status init_impl(lbm_ctx* c, const uint8_t* solid, const double* vel,
   c->nedge = 2 * (p.nx + p.ny);
   c->block = dim3(lbm::kBX, lbm::kBY);
   c->grid = dim3((p.nx + lbm::kBX - 1) / lbm::kBX, (p.ny + lbm::kBY - 1) / lbm::kBY);
+  {
+    const int rows = p.precision == 64 ? lbm::step_rows<double>() : lbm::step_rows<float>();
+    c->sblock = dim3(lbm::kBX, rows);
+    c->sgrid = dim3((p.nx + lbm::kBX - 1) / lbm::kBX, (p.ny + rows - 1) / rows);
+  }
   const size_t plane_b = (size_t)c->plane * c->esize;
   const int per_x = p.edge[0] == LBM_EDGE_PERIODIC;
   CK(cudaGetDevice(&c->device));
@@ -594,7 +599,7 @@ lbm_status init_impl(lbm_ctx* c, const uint8_t* solid, const double* vel,
   {
     // one partial per block of the generic kernel, and enough for a batch's
     // pipelined tiles plus its boundary-warp chunks of 32 nodes
-    const long long generic = (long long)c->grid.x * c->grid.y;
+    const long long generic = (long long)c->sgrid.x * c->sgrid.y;
     const long long tiles = (long long)((p.nx + lbm::kTW - 1) / lbm::kTW) *
                             ((p.ny + lbm::kTH - 1) / lbm::kTH) + (c->n_open + 31) / 32;
     c->partial_cap = (int)((generic > tiles ? generic : tiles) + 1);

@@ -65,7 +65,8 @@ struct lbm_ctx {
   size_t scratch_bytes = 0;
   long long steps = 0;
   int nedge = 0;
-  dim3 grid, block;
+  dim3 grid, block;    // 32 x 8 blocks over the lattice (init, adjoint, read-outs)
+  dim3 sgrid, sblock;  // blocks of the plain step kernel (lbm::step_rows rows)
   int dgrid = 0;  // persistent blocks of the dissolution pass
   bool use_tma = false;  // the FP32 step runs the tile pipeline
   bool kernel_auto = true;  // the library chooses the FP32 step kernel

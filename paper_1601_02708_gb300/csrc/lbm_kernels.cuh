@@ -24,6 +24,17 @@ namespace lbm {
 constexpr int kBX = 32;  // generic kernel: threads along x per block
 constexpr int kBY = 8;   // generic kernel: rows per block
 
+// Rows per block of the plain step kernel (lbm_step).  FP32: 2, so 24
+// blocks of 64 threads share an SM; finer blocks leave fewer slots idle
+// while a block's last warps finish (221 against 225 us a launch at 4096^2
+// with 32 x 8 blocks; 32 x 16 blocks 237 us).  FP64: 8, since its interior
+// blocks pack their updating nodes into the first lanes, which larger
+// blocks do better (1.40 against 1.46 ms at 32 x 4).
+template <typename Real>
+__host__ __device__ constexpr int step_rows() {
+  return sizeof(Real) == 4 ? 2 : 8;
+}
+
 template <typename Real>
 struct StepArgs {
   const Real* __restrict__ fin;  // f* of the previous step
@@ -394,10 +405,12 @@ __device__ __forceinline__ PreSrc<Real> preload(const StepArgs<Real>& a, long lo
 // Generic step: one thread per node, inputs from global memory.  The FP64
 // lattice's step, and the FP32 one on large lattices (lbm_set_kernel).
 template <typename Real, bool kFinal, int kWalls = 0>
-// FP32: six blocks of 256 per SM (40 registers) keep more loads in flight
-// than four; FP64 keeps four (64 registers) for its arithmetic.
-__global__ void __launch_bounds__(kBX * kBY, sizeof(Real) == 4 ? 6 : 4)
+// FP32: 24 blocks of 64 per SM (40 registers, as many threads as six blocks
+// of 256) keep more loads in flight than fewer threads; FP64 keeps four
+// blocks of 256 (64 registers) for its arithmetic.
+__global__ void __launch_bounds__(kBX * step_rows<Real>(), sizeof(Real) == 4 ? 24 : 4)
     lbm_step(const StepArgs<Real> a) {
+  constexpr int kBY = step_rows<Real>();
   __shared__ double red[kBX * kBY / 32];
   const int x = blockIdx.x * kBX + threadIdx.x;
   const int y = blockIdx.y * kBY + threadIdx.y;
