@@ -182,11 +182,16 @@ __device__ __forceinline__ void adjoint_node(const AdjArgs<Real>& a, int x, int 
 }
 
 // One adjoint step (kInit: the gather of lambda^0 and the first collision's
-// rate term only).  One thread per node, 32 x 8 blocks.
+// rate term only).  One thread per node in blocks of one warp (32 x
+// kAdjRows): the reverse step is bound by the latency of its gathers, and
+// one-warp blocks leave no slot waiting for a block's slowest warp.  One
+// 5000-step call at 512^2 took 113, 101, 89 and 84 ms with 8, 4, 2 and 1
+// rows per block.
+constexpr int kAdjRows = 1;
 template <typename Real, bool kInit>
-__global__ void __launch_bounds__(lbm::kBX * lbm::kBY) lbm_adjoint_step(const AdjArgs<Real> a) {
+__global__ void __launch_bounds__(lbm::kBX * kAdjRows) lbm_adjoint_step(const AdjArgs<Real> a) {
   const int x = blockIdx.x * lbm::kBX + threadIdx.x;
-  const int y = blockIdx.y * lbm::kBY + threadIdx.y;
+  const int y = blockIdx.y * kAdjRows + threadIdx.y;
   if (x >= a.nx || y >= a.ny) return;
   const long long n = (long long)(y + lbm::kYO) * a.pitch + (x + lbm::kXO);
   if (lbm::group_is_interior(blockIdx.x * lbm::kBX, y, a.nx, a.ny))
@@ -310,7 +315,8 @@ lbm_status adjoint_impl(lbm_ctx* c, int n, int eta, int L) {
   const size_t pb = w->plane_b, fb = 9 * pb;
   const size_t ne = (size_t)c->nedge;
   cudaStream_t st = c->stream;
-  const dim3 grid = c->grid, block = c->block;
+  const dim3 block(lbm::kBX, kAdjRows);
+  const dim3 grid((c->p.nx + lbm::kBX - 1) / lbm::kBX, (c->p.ny + kAdjRows - 1) / kAdjRows);
 
   // forward, keeping a checkpoint every L steps; with one segment (K = 1)
   // the forward run records u and the Neumann branches of every step itself
