@@ -66,6 +66,31 @@ def test_fem_matches_oracle(pkg, oracle_mod, supg, hole, nex, ney):
     assert np.abs(g.interpolate(pts) - o.interpolate(pts)).max() <= 1e-10
 
 
+@pytest.mark.parametrize("nex,ney", [(37, 11), (97, 53)])
+def test_fem_reports_a_solve_cut_short(pkg, nex, ney):
+    """Both solve paths (one block up to 2048 nodes, the cooperative launch
+    above) report a solve stopped by max_iter before the tolerance as an
+    error, with the iterations it ran; the same system then converges with
+    the default limit."""
+    from paper_1601_02708_gb300.fem import FEM
+    rng = np.random.default_rng(3)
+    nxn = nex + 1
+    kw = dict(nex=nex, ney=ney, x0=0.0, y0=0.0, hx=0.02, hy=0.03, D=1e-3, v=(0.4, -0.15),
+              theta=0.5, dt=0.01, supg=True, dirichlet=[j * nxn for j in range(ney + 1)],
+              d0=rng.uniform(0, 1, nxn * (ney + 1)), tol=1e-14)
+    vals = rng.uniform(0, 2, ney + 1)
+    cut = FEM(max_iter=1, **kw)
+    with pytest.raises(pkg.LBMError):
+        cut.step(vals)
+    assert cut.solver_info()[0] == 1
+    full = FEM(**kw)
+    full.step(vals)
+    it, res = full.solver_info()
+    assert 1 < it < 1000 and res <= 1e-14
+    cut.close()
+    full.close()
+
+
 def test_fem_rejects_bad_input(pkg):
     from paper_1601_02708_gb300.fem import FEM
     with pytest.raises(pkg.LBMError):
