@@ -94,7 +94,8 @@ typedef enum {
 enum { LBM_SIDE_W = 0, LBM_SIDE_E = 1, LBM_SIDE_S = 2, LBM_SIDE_N = 3 };
 
 typedef struct {
-  int nx, ny;        /* lattice nodes, each >= 2 */
+  int nx, ny;        /* lattice nodes, each >= 2; ny <= 65535 (a launch's
+                        block index in y numbers the rows) */
   int precision;     /* 32: FP32 populations and arithmetic (FP64 boundary
                         solves, reaction shares, mineral and sums); 64: FP64
                         throughout */

@@ -886,6 +886,9 @@ namespace {
 
 lbm_status check_params(const lbm_params* p) {
   if (p->nx < 2 || p->ny < 2) return fail(LBM_ERR_ARG, "lbm_init: nx, ny must be >= 2");
+  // launches over the lattice give each row (the adjoint step) or pair of
+  // rows a block index in y, at most 65535
+  if (p->ny > 65535) return fail(LBM_ERR_ARG, "lbm_init: ny must be <= 65535");
   if ((long long)lbm::padded_pitch(p->nx) * lbm::padded_rows(p->ny) > INT_MAX)
     return fail(LBM_ERR_ARG, "lbm_init: lattice too large (padded plane > INT_MAX)");
   if (p->precision != 32 && p->precision != 64)

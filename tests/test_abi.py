@@ -43,6 +43,22 @@ def test_abi_version(lib):
     assert lib.lbm_abi_version() == want
 
 
+def test_init_refuses_bad_sizes_before_touching_the_device(lib):
+    """Size checks come first in lbm_init: rows above 65535 (the y block
+    index of the row launches) and sides under two nodes are LBM_ERR_ARG,
+    with no CUDA call made (this runs without a GPU)."""
+    from paper_1601_02708_gb300._lib import Params
+    for nx, ny in ((64, 65536), (1, 64), (64, 1)):
+        p = Params()
+        p.nx, p.ny, p.precision, p.tau = nx, ny, 32, 0.8
+        for s in range(4):
+            p.edge[s] = 0
+        h = ctypes.c_void_p()
+        lib.lbm_init.restype = ctypes.c_int
+        st = lib.lbm_init(ctypes.byref(h), ctypes.byref(p), None, None, None, None, None, None)
+        assert st == -1 and not h.value
+
+
 def test_product_path_has_no_oracle_dependency():
     """The package never imports or loads the oracle."""
     pkg = os.path.join(ROOT, "paper_1601_02708_gb300")
