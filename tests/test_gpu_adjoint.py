@@ -250,6 +250,25 @@ def test_config4_fp32_against_fp64(pkg, c4, c4_fp64):
         r64["ua"][:ny].sum() + r64["ub"][:ny].sum(), rel=1e-4)
 
 
+def test_config4_fp32_every_outlet_node(pkg, oracle_mod, c4):
+    """FP32 against the oracle's adjoint with the nodes of the last three
+    columns made fluid, so that every outlet node is fed by fluid neighbours
+    and dJ/dq is compared at all of them, with nothing masked (300 steps,
+    seeded nonzero start)."""
+    case, ud, q = c4
+    case = dict(case)
+    solid = case["solid"].copy()
+    solid[:, -3:] = 0
+    case["solid"] = solid
+    rng = np.random.default_rng(9)
+    u0 = rng.uniform(0, 1, (case["ny"], case["nx"]))
+    u0[solid != 0] = 0
+    case["u0"] = u0
+    r = pkg.LBM(precision=32, **case).adjoint(300, 1, ud, ud, q)
+    ref = oracle_mod.LBMOracle(**case).adjoint(300, 1, ud, ud, q)
+    _compare(r, ref, 32)
+
+
 @pytest.mark.parametrize("prec", [64, 32])
 def test_config4_lattice_matches_oracle_adjoint(pkg, oracle_mod, c4, prec):
     """The full 512 x 512 lattice against the oracle's adjoint over 300 steps
@@ -270,7 +289,9 @@ def test_config4_lattice_matches_oracle_adjoint(pkg, oracle_mod, c4, prec):
         # max(S, 0) (root or zero limit).  Where S is within FP32 rounding of
         # 0 the branch taken differs from FP64, and dJ/dq -- a sum of O(J)
         # sensitivities over the steps with the root -- differs with it.
-        # dJ/dq is compared at outlet nodes fed by fluid neighbours.
+        # dJ/dq is compared at outlet nodes fed by fluid neighbours here;
+        # test_config4_fp32_every_outlet_node compares it at every outlet
+        # node of a geometry where all of them are fed.
         ny, nx = case["ny"], case["nx"]
         sol = case["solid"]
         fed = np.array([not (sol[(y - 1) % ny, nx - 2] or sol[y, nx - 2] or sol[(y + 1) % ny, nx - 2])
