@@ -215,13 +215,14 @@ def test_multi_time_step_interpolation(gb, oracle_mod, prec):
 def test_time_interpolated_dirichlet_closed_form(gb, prec):
     """The library on the closed form that pins Eq. "MTS" in the oracle:
     u = a + b t + (b / 2D)(x - xc)^2 at tau = 1 (exact for the scheme), with
-    west/east data interpolated in time over coarse steps of 5 substeps;
-    FP64 to rounding over 300 substeps, FP32 within its bound over 100.
-    (This solution grows by b every step, and FP32 storage rounds each
-    step's increment at about half an ulp of u, so the FP32 deviation grows
-    in proportion to the steps, about 3.5e-8 of u per step here; solutions
-    that do not grow keep the FP32 bound over 10,000 steps, see
-    test_fp32_bound_over_ten_thousand_steps.)"""
+    west/east data interpolated in time over coarse steps of 5 substeps,
+    300 substeps: FP64 to rounding throughout, FP32 within its 1e-5 bound
+    over the first 100.  This solution grows by b every step, and FP32
+    storage rounds each step's increment at about half an ulp of u, so the
+    FP32 deviation grows in proportion to the steps (about 3.5e-8 of u per
+    step here); over all 300 it is held to one storage rounding of u per
+    step, 2^-24 u each.  Solutions that do not grow keep the FP32 bound over
+    10,000 steps (test_fp32_bound_over_ten_thousand_steps)."""
     nx, ny, tau, eta = 33, 4, 1.0, 5
     D = (tau - 0.5) / 3.0
     a, b, xc = 1.0, 1e-3, 16.0
@@ -233,13 +234,18 @@ def test_time_interpolated_dirichlet_closed_form(gb, prec):
     lat = gb.LBM(nx, ny, tau, edges=(1, 1, 0, 0), precision=prec,
                  u0=np.tile(exact(xs, 0.0), (ny, 1)))
     t, worst = 0, 0.0
-    for _ in range(60 if prec == 64 else 20):
+    for _ in range(60):
         ua = inputs.edge_array(nx, ny, W=exact(0.0, t), E=exact(nx - 1.0, t))
         ub = inputs.edge_array(nx, ny, W=exact(0.0, t + eta), E=exact(nx - 1.0, t + eta))
         lat.substeps(eta, eta, ua, ub)
         t += eta
         worst = max(worst, np.abs(lat.concentration() - exact(xs, t)[None, :]).max())
-    assert worst <= TOL[prec] * exact(0.0, t), worst
+        if t == 100:
+            assert worst <= TOL[prec] * exact(0.0, t), worst
+    if prec == 64:
+        assert worst <= TOL[prec] * exact(0.0, t), worst
+    else:
+        assert worst <= t * 2.0 ** -24 * exact(0.0, t), worst
 
 
 def test_neumann_flux_and_interface_trace(gb, oracle_mod):
