@@ -25,11 +25,12 @@ constexpr int kBX = 32;  // generic kernel: threads along x per block
 constexpr int kBY = 8;   // generic kernel: rows per block
 
 // Rows per block of the plain step kernel (lbm_step).  FP32: 2, so 24
-// blocks of 64 threads share an SM; finer blocks leave fewer slots idle
-// while a block's last warps finish (221 against 225 us a launch at 4096^2
-// with 32 x 8 blocks; 32 x 16 blocks 237 us).  FP64: 8, since its interior
-// blocks pack their updating nodes into the first lanes, which larger
-// blocks do better (1.40 against 1.46 ms at 32 x 4).
+// blocks of 64 threads share an SM: measured 221 against 225 us a launch at
+// 4096^2 with 32 x 8 blocks (32 x 16 blocks: 237 us), with the same warps
+// active and the same DRAM bytes but DRAM busier (61 against 59% of peak in
+// a 2048^2 capture).  FP64: 8, since its interior blocks pack their
+// updating nodes into the first lanes, which larger blocks do better (1.40
+// against 1.46 ms at 32 x 4).
 template <typename Real>
 __host__ __device__ constexpr int step_rows() {
   return sizeof(Real) == 4 ? 2 : 8;
